@@ -1,0 +1,210 @@
+/*
+ * libahfgpu - C ABI of the per-halo unbinding stage of AHF
+ * (Knollmann & Knebe 2009, "AHF: Amiga's Halo Finder"), for one GB300 GPU.
+ *
+ * What the library computes, per candidate halo (Sect. 2.1 and Appendix A):
+ *   1. gather: the candidates of the halo inside its gather sphere
+ *      |x - c| <= R, recentred in FP64 (minimum image in a periodic box);
+ *   2. sort the members once by radius (ties by candidate position);
+ *   3. iterate: potential phi_i = -G [M(<r_i)/r_i + sum_{j>=i} m_j/r_j]
+ *      (Appendix A, Eqs. A1-A4 with phi_0 from Eq. A9, the halo truncated at
+ *      its outermost member), escape test |v - v_bulk + H d|^2 > 2|phi|
+ *      (v_esc = sqrt(2|phi|), Appendix A), simultaneous removal of every
+ *      unbound particle, until an iteration removes nothing;
+ *   4. virial radius and mass of the final set: the first outward crossing
+ *      of the mean enclosed density through delta_rho (Sect. 2.1, Eqs. 1-2);
+ *   5. optionally a log-radial profile of the bound set (Sect. 2.1, the
+ *      radially binned halo output).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int: AHF_OK (0), AHF_PENDING (1, polling only),
+ *     or a negative AHF_ERR_* code.  No C++ exception crosses the ABI and no
+ *     call aborts the process.  ahf_last_error() returns a thread-local,
+ *     human-readable message for the last failing call on that thread.
+ *   - Buffers are owned by the caller unless stated otherwise.  "device"
+ *     means memory of the context's GPU (cudaMalloc, torch.cuda, managed);
+ *     "host" means ordinary or pinned CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue their work on it and return; results are
+ *     valid once the stream has reached that point.  A call whose batch
+ *     holds haloes above the on-chip size class synchronises `stream`
+ *     between iterations of that class (convergence is decided on the host).
+ *   - Candidate slots.  Halo h owns the slots [offset, offset + count).
+ *     Without a member list, slot s is particle s; with a member list,
+ *     slot s is particle member_idx[s].  Haloes must not share slots.
+ *     Per-slot outputs (bound_idx, phi, removed_iter) use the same slots:
+ *     halo h writes its k-th bound particle at slot offset + k.
+ */
+#ifndef AHF_H
+#define AHF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define AHF_OK            0
+#define AHF_PENDING       1
+#define AHF_ERR_INVALID   (-1)   /* bad argument, size or layout           */
+#define AHF_ERR_NOMEM     (-2)   /* device allocation failed / above a cap */
+#define AHF_ERR_TIMEOUT   (-3)   /* a bounded device wait gave up          */
+#define AHF_ERR_CUDA      (-4)   /* a CUDA runtime call failed             */
+#define AHF_ERR_FULL      (-5)   /* serving queue full                     */
+#define AHF_ERR_NOT_FOUND (-6)   /* unknown request id                     */
+
+/* ---- per-halo status bits (ahf_result.status) --------------------------- */
+#define AHF_HALO_OK               0
+#define AHF_HALO_NOT_CONVERGED    1  /* max_iter reached while still removing */
+#define AHF_HALO_EMPTY            2  /* no member left                        */
+#define AHF_HALO_RVIR_BEYOND_EDGE 4  /* mean density above delta_rho at the outermost member */
+#define AHF_HALO_RVIR_NONE        8  /* mean density never reaches delta_rho  */
+
+/* ---- coordinate encodings (ahf_particles.coord_type) -------------------- */
+#define AHF_COORD_F64     0  /* double x,y,z,vx,vy,vz,m; any frame           */
+#define AHF_COORD_F32_REL 1  /* float; positions already near the centre    */
+#define AHF_COORD_F32_BOX 2  /* float box coordinates (e.g. [0, box))       */
+
+/* ---- precision modes (ahf_params.precision) ----------------------------- */
+/* MIXED: FP64 recentring, FP32 per-particle arithmetic, and every sum that
+ * needs more than FP32 (M(<r), sum m/r, sum m v, sum m) accumulated exactly
+ * in 64-bit fixed point, which is at least as accurate as FP64 here and
+ * independent of summation order.  FP64: the same with FP64 per-particle
+ * arithmetic (phi and the escape test in double). */
+#define AHF_PREC_MIXED 0
+#define AHF_PREC_FP64  1
+
+typedef struct ahf_params {
+  double G;          /* gravitational constant in the caller's units            */
+  double H;          /* Hubble constant: the escape test uses u = v - v_bulk + H d */
+  double delta_rho;  /* Delta * rho_b of Eq. 1 (mass / length^3)                */
+  double r_soft;     /* radius floor: every r is replaced by max(r, r_soft); with
+                        0, pair terms with max(r_i, r_j) = 0 are dropped        */
+  double box;        /* periodic box size; 0 = not periodic                     */
+  double band;       /* relative half-width of the reported decision band,
+                        |(|u|^2 - 2|phi|) / 2|phi|| < band (default 1e-5)      */
+  int32_t max_iter;  /* iteration cap (>= 1)                                    */
+  int32_t precision; /* AHF_PREC_MIXED or AHF_PREC_FP64                         */
+} ahf_params;
+
+typedef struct ahf_particles {
+  /* Structure-of-arrays particle store, n entries each.  Element type is
+     double for AHF_COORD_F64 and float otherwise.  m may be NULL: every
+     particle then has mass m0. */
+  const void *x, *y, *z, *vx, *vy, *vz, *m;
+  double m0;
+  int64_t n;
+  int32_t coord_type;
+  int32_t reserved;  /* must be 0 */
+} ahf_particles;
+
+typedef struct ahf_halo {
+  double cx, cy, cz; /* centre, same frame as the particle coordinates (FP64) */
+  double radius;     /* gather-sphere radius R; members satisfy |x - c| <= R  */
+  int64_t offset;    /* first candidate slot                                  */
+  int64_t count;     /* number of candidate slots (>= 0)                      */
+} ahf_halo;
+
+typedef struct ahf_result {
+  int64_t n_bound;   /* members left after unbinding                          */
+  int64_t n_member;  /* candidates inside the gather sphere                   */
+  int64_t part_iter; /* sum over iterations of the members tested             */
+  int64_t n_band;    /* sum over iterations of tests inside the band          */
+  int64_t k_vir;     /* index in the sorted bound list of the last particle
+                        inside r_vir, -1 if none                              */
+  int32_t n_iter;    /* iterations run, the last one removing nothing unless
+                        AHF_HALO_NOT_CONVERGED                                */
+  int32_t status;    /* AHF_HALO_* bits                                       */
+  double m_vir;      /* M_vir = M(<= r_vir) (Eq. 2)                           */
+  double r_vir;      /* r_vir with M_vir / (4/3 pi r_vir^3) = delta_rho (Eq. 1) */
+  double vbulk[3];   /* mass-weighted mean velocity of the bound set          */
+} ahf_result;        /* 88 bytes */
+
+typedef struct ahf_ctx ahf_ctx;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int ahf_version(void);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *ahf_last_error(void);
+
+/* Create a context on CUDA device `device`.  The context owns its device
+ * workspace (grown on demand, released by ahf_destroy) and its streams.
+ * Errors: AHF_ERR_INVALID (ctx NULL, bad device), AHF_ERR_CUDA. */
+int ahf_create(ahf_ctx **ctx, int device);
+
+/* Release the context and its workspace; waits for its work to finish.
+ * NULL is accepted. */
+int ahf_destroy(ahf_ctx *ctx);
+
+/* Iterative unbinding of a batch of haloes (Sect. 2.1 and Appendix A).
+ *   p            particle store (device pointers), see ahf_particles
+ *   halos        host array of n_halos descriptors
+ *   member_idx   device int64 slot -> particle index map, or NULL (slot = particle)
+ *   prm          host parameters
+ *   out          device array of n_halos ahf_result records
+ *   bound_idx    device int64 per slot: halo h writes the particle indices of
+ *                its bound set, sorted by (radius, slot), at offset..offset+n_bound-1
+ *   phi          device per slot, nullable: phi of each bound particle, aligned
+ *                with bound_idx (float for MIXED, double for FP64)
+ *   removed_iter device int32 per slot, nullable: -1 outside the gather sphere,
+ *                0 bound, t > 0 removed in iteration t
+ * Slots of a halo beyond offset + n_bound are left unspecified in bound_idx
+ * and phi.  Errors: AHF_ERR_INVALID (NULL pointers, negative sizes, slots out
+ * of range or shared, bad coord_type/precision/max_iter), AHF_ERR_NOMEM,
+ * AHF_ERR_CUDA, AHF_ERR_TIMEOUT.  Outputs are undefined after an error. */
+int ahf_unbind_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
+                     int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
+                     ahf_result *out, int64_t *bound_idx, void *phi,
+                     int32_t *removed_iter, void *stream);
+
+/* The same computation with every pointer in HOST memory (pageable or
+ * pinned): the call stages the inputs on the device, runs ahf_unbind_batch,
+ * copies the outputs back and returns when they are in place (it
+ * synchronises `stream`).  Same arguments, layouts and errors. */
+int ahf_unbind_batch_host(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
+                          int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
+                          ahf_result *out, int64_t *bound_idx, void *phi,
+                          int32_t *removed_iter, void *stream);
+
+/* Plain form of the same stage: one halo at a time, separate kernel launches
+ * for gather, sort and each iteration's scan / test / compaction, and a host
+ * synchronisation on every iteration's change flag.  Same arguments, results
+ * and errors as ahf_unbind_batch; it exists as the one-halo-per-launch
+ * baseline the batched form is measured against. */
+int ahf_unbind_plain(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
+                     int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
+                     ahf_result *out, int64_t *bound_idx, void *phi,
+                     int32_t *removed_iter, void *stream);
+
+/* Log-radial profile of bound sets (Sect. 2.1: the radially binned output).
+ *   p, halos, n_halos, member_idx, prm   as passed to ahf_unbind_batch
+ *   res, bound_idx                       its outputs (device)
+ *   n_bins (1..4096), r_min_frac (0 < f < 1)
+ *   prof  device double [n_halos][n_bins][4]
+ * Bin b of halo h covers (e_b, e_{b+1}] with e_b = r_out f^(1 - b/n_bins),
+ * r_out = r_vir, or the outermost bound radius when r_vir is 0.  Columns:
+ * count, mass within e_{b+1}, mass of the bin / shell volume, circular
+ * velocity sqrt(G M(<= e_{b+1}) / e_{b+1}).  Empty haloes give zero rows.
+ * Errors: AHF_ERR_INVALID, AHF_ERR_NOMEM, AHF_ERR_CUDA. */
+int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
+                      int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
+                      const ahf_result *res, const int64_t *bound_idx, int32_t n_bins,
+                      double r_min_frac, double *prof, void *stream);
+
+/* Tuning and diagnostics knobs (values persist in the context).
+ *   AHF_OPT_ONCHIP_MAX   largest candidate count handled on chip by one CTA
+ *   AHF_OPT_WAIT_LIMIT   spin iterations a bounded device wait may take before
+ *                        it reports AHF_ERR_TIMEOUT (0 = give up at once)
+ * Errors: AHF_ERR_INVALID (unknown option or value). */
+#define AHF_OPT_ONCHIP_MAX 1
+#define AHF_OPT_WAIT_LIMIT 2
+int ahf_set_option(ahf_ctx *ctx, int option, int64_t value);
+int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AHF_H */

@@ -1,0 +1,306 @@
+"""Plain FP64 CPU oracle of AHF's per-halo unbinding stage.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this
+module: only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference legs of ``bench.py`` use it.  It shares no code with the CUDA path;
+the only thing both sides consume is the seeded input generator, which holds
+none of the method's arithmetic.
+
+What it computes (Knollmann & Knebe 2009, "AHF: Amiga's Halo Finder"):
+
+* Particle collection (Sect. 2.1): a halo's initial particle set is the
+  sphere of a given radius around its centre.  Coordinates are recentred in
+  FP64, with the minimum image in a periodic box (the paper's shift test in
+  Sect. 3.2 relies on periodicity).
+* Unbinding (Appendix A): the escape velocity is v_esc = sqrt(2|phi|); phi
+  follows from integrating Poisson's equation for a spherical mass
+  distribution, phi(r) = G int_0^r M(<r')/r'^2 dr' + phi_0, with phi_0 fixed by
+  phi(infinity) = 0 for a halo truncated at its outer edge.  For the step
+  function M(<r) of a particle list sorted by radius this integral is exact:
+
+      phi_i = -G [ M(<r_i) / r_i + sum_{j >= i} m_j / r_j ]
+
+  (integration by parts; the truncation radius drops out as long as it lies
+  at or beyond the outermost particle).  Unbound particles are removed, phi_0
+  and phi are re-evaluated for the new list, and the loop repeats until no
+  particle is removed (Appendix A, last paragraph; Sect. 2.1).
+* Virial radius (Sect. 2.1): mean enclosed density = Delta * rho_b, so
+  M_vir = 4 pi rho_b Delta r_vir^3 / 3.
+
+Readings where the paper is silent (each listed in the design notes):
+
+1. Bulk velocity: mass-weighted mean velocity of the current set, recomputed
+   every iteration; the escape test uses u = v - v_bulk + H d (Hubble flow).
+2. Removal: all unbound particles of an iteration are removed at once.
+3. Truncation: at the current set's outermost particle.
+4. Strict test: a particle is unbound iff |u|^2 > 2|phi|.
+5. r = 0: with r_soft = 0 terms whose max(r_i, r_j) is 0 are dropped;
+   r_soft > 0 replaces every radius r by max(r, r_soft).
+6. r_vir is the first outward crossing: the first k (in the sorted final set,
+   M_k the inclusive mass) with M_k < Delta rho (4 pi/3) r_{k+1}^3, with
+   r_{N+1} = infinity, and r_vir = (3 M_k / (4 pi Delta rho))^(1/3).
+
+Pins: see tests/test_oracle_pins.py (brute force, Appendix A's integral
+evaluated literally, analytic uniform-sphere and truncated-NFW potentials,
+idempotence, the virial identity, invariances, special cases).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Per-halo status bits (mirrors the values documented in the C header; the
+# numbers are part of the interface, not shared code).
+OK = 0
+NOT_CONVERGED = 1
+EMPTY = 2
+RVIR_BEYOND_EDGE = 4
+RVIR_NONE = 8
+
+
+@dataclasses.dataclass
+class Params:
+    G: float = 4.3009e-6
+    H: float = 0.1
+    delta_rho: float = 200.0 * 3.0 * 0.1 * 0.1 / (8.0 * math.pi * 4.3009e-6)
+    r_soft: float = 0.0
+    box: float = 0.0
+    max_iter: int = 100
+    band: float = 1e-5
+
+
+def _f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def recentre(x, y, z, centre, box):
+    """d = x - c in FP64 (inputs promoted exactly), minimum image if box > 0."""
+    d = np.stack([_f64(x) - centre[0], _f64(y) - centre[1], _f64(z) - centre[2]], axis=1)
+    if box > 0.0:
+        half = 0.5 * box
+        d = np.where(d > half, d - box, d)
+        d = np.where(d < -half, d + box, d)
+    return d
+
+
+def gather_sphere(pop, h, member_idx=None):
+    """Candidates of halo h and their recentred phase-space coordinates.
+
+    Returns (pidx, d, v, m, inside): particle indices of the candidate slice,
+    FP64 offsets from the centre, FP64 velocities, FP64 masses and the mask of
+    candidates inside the gather sphere |d| <= R (Sect. 2.1)."""
+    lo = int(pop.offset[h])
+    hi = lo + int(pop.count[h])
+    pidx = np.arange(lo, hi, dtype=np.int64) if member_idx is None else np.asarray(member_idx[lo:hi], np.int64)
+    d = recentre(pop.x[pidx], pop.y[pidx], pop.z[pidx], pop.centre[h], pop.box)
+    v = np.stack([_f64(pop.vx[pidx]), _f64(pop.vy[pidx]), _f64(pop.vz[pidx])], axis=1)
+    m = np.full(pidx.shape[0], float(pop.m0)) if pop.m is None else _f64(pop.m[pidx])
+    r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+    R = float(pop.radius[h])
+    inside = r2 <= R * R
+    return pidx, d, v, m, inside
+
+
+def potential_sorted(r, m, G, r_soft=0.0):
+    """phi of particles sorted by radius (Appendix A, Eq. for phi and phi_0).
+
+    M(<r_i) is the sequential FP64 sum of the masses before i; the outer sum
+    is the sequential FP64 sum of m_j / r_j from the outermost particle in."""
+    rr = np.maximum(r, r_soft)
+    m_inner = np.concatenate([[0.0], np.cumsum(m)[:-1]])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mr = np.where(rr > 0.0, m / rr, 0.0)
+        inner = np.where(rr > 0.0, m_inner / rr, 0.0)
+    outer = np.cumsum(mr[::-1])[::-1]
+    return -G * (inner + outer)
+
+
+def potential_bruteforce(r, m, G, r_soft=0.0):
+    """O(N^2) phi_i = -G sum_j m_j / max(r_i, r_j), zero-radius pairs dropped."""
+    rr = np.maximum(_f64(r), r_soft)
+    mx = np.maximum(rr[:, None], rr[None, :])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(mx > 0.0, m[None, :] / mx, 0.0)
+    return -G * t.sum(axis=1)
+
+
+def virial(r, m, delta_rho):
+    """First outward crossing of the mean enclosed density through delta_rho.
+
+    r, m: the final set sorted by radius.  Returns (r_vir, m_vir, k, status)
+    with k the 0-based index of the last particle inside r_vir."""
+    n = r.shape[0]
+    if n == 0:
+        return 0.0, 0.0, -1, EMPTY
+    mk = np.cumsum(m)
+    r_next = np.concatenate([r[1:], [np.inf]])
+    crit = delta_rho * (4.0 * math.pi / 3.0) * r_next ** 3
+    k = int(np.argmax(mk < crit))          # first True; the last entry is always True
+    m_vir = float(mk[k])
+    r_vir = (3.0 * m_vir / (4.0 * math.pi * delta_rho)) ** (1.0 / 3.0)
+    status = OK
+    if k == n - 1:
+        status |= RVIR_BEYOND_EDGE
+    if m_vir < delta_rho * (4.0 * math.pi / 3.0) * r[k] ** 3:
+        # the mean density never reaches delta_rho around any particle
+        status |= RVIR_NONE
+        return 0.0, 0.0, -1, status
+    return r_vir, m_vir, k, status
+
+
+def unbind_halo(d, v, m, inside, params: Params, forced=None):
+    """Iterative unbinding of one halo (Appendix A; Sect. 2.1).
+
+    d, v, m: FP64 candidates (in candidate order); inside: gather-sphere mask.
+    forced: optional per-candidate removal iteration (0 = never) used only for
+    particles whose escape margin |(|u|^2 - 2|phi|) / 2|phi|| is below
+    params.band (replay of another implementation's in-band decisions).
+
+    Returns a dict with the final set (candidate positions sorted by (r, pos)),
+    phi of the final set, per-candidate removal iteration (-1 outside the
+    sphere, 0 bound, t removed in iteration t) and the iteration statistics."""
+    n_cand = d.shape[0]
+    r = np.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2 + d[:, 2] ** 2)
+    removed_iter = np.where(inside, 0, -1).astype(np.int64)
+    alive = np.nonzero(inside)[0]
+    n_member = int(alive.shape[0])
+    n_iter = 0
+    part_iter = 0
+    n_band = 0
+    status = OK
+    converged = False
+    phi = np.zeros(0)
+    order = alive
+    while alive.shape[0] > 0 and n_iter < params.max_iter:
+        n_iter += 1
+        part_iter += int(alive.shape[0])
+        ma = m[alive]
+        vbulk = (ma[:, None] * v[alive]).sum(axis=0) / ma.sum()
+        # integrate along the radially ordered list (ties by candidate position)
+        order = alive[np.lexsort((alive, r[alive]))]
+        phi = potential_sorted(r[order], m[order], params.G, params.r_soft)
+        u = v[order] - vbulk[None, :] + params.H * d[order]
+        u2 = (u * u).sum(axis=1)
+        two_phi = 2.0 * np.abs(phi)
+        unbound = u2 > two_phi
+        with np.errstate(divide="ignore", invalid="ignore"):
+            margin = np.where(two_phi > 0.0, np.abs(u2 - two_phi) / two_phi, np.inf)
+        in_band = margin < params.band
+        n_band += int(in_band.sum())
+        if forced is not None:
+            fz = np.asarray(forced)[order] == n_iter
+            unbound = np.where(in_band, fz, unbound)
+        if not unbound.any():
+            converged = True
+            break
+        removed_iter[order[unbound]] = n_iter
+        alive = order[~unbound]
+    if alive.shape[0] == 0:
+        status |= EMPTY
+        order = alive
+        phi = np.zeros(0)
+    elif not converged:
+        status |= NOT_CONVERGED
+        order = alive[np.lexsort((alive, r[alive]))]
+        phi = potential_sorted(r[order], m[order], params.G, params.r_soft)
+    if order.shape[0] > 0:
+        mo = m[order]
+        vbulk = (mo[:, None] * v[order]).sum(axis=0) / mo.sum()
+        r_vir, m_vir, k_vir, vst = virial(r[order], mo, params.delta_rho)
+        status |= vst
+    else:
+        vbulk = np.zeros(3)
+        r_vir, m_vir, k_vir = 0.0, 0.0, -1
+    return dict(order=order, phi=phi, r=r[order] if order.shape[0] else np.zeros(0),
+                removed_iter=removed_iter, n_member=n_member, n_iter=n_iter,
+                part_iter=part_iter, n_band=n_band, status=status, vbulk=vbulk,
+                r_vir=r_vir, m_vir=m_vir, k_vir=k_vir)
+
+
+def profile(r_sorted, m_sorted, r_vir, n_bins, r_min_frac, G):
+    """Log-radial profile of a bound set (Sect. 2.1: radially binned output).
+
+    Bin b covers (e_b, e_{b+1}] with e_b = r_out * f^(1 - b/n), r_out = r_vir
+    (or the outermost particle when r_vir is 0).  Columns: particle count,
+    mass within e_{b+1}, density of the bin's shell, circular velocity
+    sqrt(G M(<=e_{b+1}) / e_{b+1})."""
+    out = np.zeros((n_bins, 4))
+    if r_sorted.shape[0] == 0:
+        return out
+    r_out = r_vir if r_vir > 0.0 else float(r_sorted[-1])
+    edges = r_out * r_min_frac ** (1.0 - np.arange(n_bins + 1) / n_bins)
+    edges[-1] = r_out
+    for b in range(n_bins):
+        lo, hi = edges[b], edges[b + 1]
+        sel = (r_sorted > lo) & (r_sorted <= hi)
+        mass_in = float(m_sorted[r_sorted <= hi].sum())
+        out[b, 0] = float(sel.sum())
+        out[b, 1] = mass_in
+        out[b, 2] = float(m_sorted[sel].sum()) / (4.0 * math.pi / 3.0 * (hi ** 3 - lo ** 3))
+        out[b, 3] = math.sqrt(G * mass_in / hi)
+    return out
+
+
+def unbind_population(pop, params: Params, halos=None, member_idx=None,
+                      forced=None, n_bins=0, r_min_frac=0.01):
+    """Run the oracle over haloes of a population (all of them by default).
+
+    forced: optional per-candidate-slot removal iterations (flat, aligned
+    with the candidate slices) for the in-band replay.
+    Returns {h: result dict} with particle indices in 'bound_idx'."""
+    res = {}
+    hs = range(pop.n_halos) if halos is None else halos
+    p = dataclasses.replace(params, box=pop.box)
+    for h in hs:
+        pidx, d, v, m, inside = gather_sphere(pop, h, member_idx)
+        lo = int(pop.offset[h])
+        fz = None if forced is None else np.asarray(forced[lo:lo + pidx.shape[0]])
+        o = unbind_halo(d, v, m, inside, p, fz)
+        o["bound_idx"] = pidx[o["order"]]
+        if n_bins > 0:
+            o["profile"] = profile(o["r"], m[o["order"]], o["r_vir"], n_bins, r_min_frac, p.G)
+        res[h] = o
+    return res
+
+
+def _worker(args):
+    pop, params = args
+    out = unbind_population(pop, params)
+    return [(o["n_iter"], o["part_iter"], o["order"].shape[0]) for _, o in sorted(out.items())]
+
+
+def unbind_population_parallel(pop, params: Params, halos, n_workers):
+    """The oracle over haloes spread across n_workers spawned processes
+    (the i-th listed halo goes to worker i % n_workers).  Returns
+    {h: (n_iter, part_iter, n_bound)}.  Used only to time the oracle as a
+    CPU baseline; the arithmetic is unbind_population's."""
+    import multiprocessing as mp
+    halos = list(halos)
+    chunks = [c for c in (halos[i::n_workers] for i in range(n_workers)) if c]
+    ctx = mp.get_context("spawn")
+    res = {}
+    with ctx.Pool(len(chunks)) as pool:
+        parts = pool.map(_worker, [(_subset(pop, c), params) for c in chunks])
+    for c, part in zip(chunks, parts):
+        for h, stats in zip(c, part):
+            res[h] = stats
+    return res
+
+
+def _subset(pop, halos):
+    """A population holding only the given haloes (renumbered 0..k-1)."""
+    import copy
+    halos = list(halos)
+    idx = np.concatenate([np.arange(pop.offset[h], pop.offset[h] + pop.count[h]) for h in halos])
+    sub = copy.copy(pop)
+    for a in ("x", "y", "z", "vx", "vy", "vz"):
+        setattr(sub, a, getattr(pop, a)[idx])
+    sub.m = None if pop.m is None else pop.m[idx]
+    cnt = pop.count[halos]
+    sub.count = cnt.copy()
+    sub.offset = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)
+    for a in ("centre", "radius", "r200", "conc"):
+        setattr(sub, a, getattr(pop, a)[halos])
+    return sub
