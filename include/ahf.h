@@ -194,6 +194,12 @@ int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halo
                       const ahf_result *res, const int64_t *bound_idx, int32_t n_bins,
                       double r_min_frac, double *prof, void *stream);
 
+/* Wait for the context's enqueued work and report problems the device
+ * found while running it: AHF_ERR_INVALID for an out-of-range member index
+ * or a halo routed to a class it did not fit, AHF_ERR_TIMEOUT when a bounded
+ * device wait gave up.  The device error word is cleared by the call. */
+int ahf_sync(ahf_ctx *ctx);
+
 /* Tuning and diagnostics knobs (values persist in the context).
  *   AHF_OPT_ONCHIP_MAX   largest candidate count handled on chip by one CTA
  *   AHF_OPT_WAIT_LIMIT   spin iterations a bounded device wait may take before

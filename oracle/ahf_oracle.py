@@ -214,6 +214,7 @@ def unbind_halo(d, v, m, inside, params: Params, forced=None):
         vbulk = np.zeros(3)
         r_vir, m_vir, k_vir = 0.0, 0.0, -1
     return dict(order=order, phi=phi, r=r[order] if order.shape[0] else np.zeros(0),
+                m=m[order] if order.shape[0] else np.zeros(0),
                 removed_iter=removed_iter, n_member=n_member, n_iter=n_iter,
                 part_iter=part_iter, n_band=n_band, status=status, vbulk=vbulk,
                 r_vir=r_vir, m_vir=m_vir, k_vir=k_vir)

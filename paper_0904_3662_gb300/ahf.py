@@ -1,0 +1,289 @@
+"""Thin Python binding of libahfgpu (argument marshalling only).
+
+Every step of the unbinding stage runs in the library's CUDA kernels; this
+module only turns torch tensors and numpy descriptors into the C structs of
+include/ahf.h and back.  PyTorch provides device memory and streams.  There
+is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libahfgpu.so")
+
+# status / codes (values from include/ahf.h)
+OK, PENDING = 0, 1
+ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2, -3, -4, -5, -6
+HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
+COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
+PREC_MIXED, PREC_FP64 = 0, 1
+OPT_ONCHIP_MAX, OPT_WAIT_LIMIT = 1, 2
+
+HALO_DTYPE = np.dtype([("cx", "<f8"), ("cy", "<f8"), ("cz", "<f8"), ("radius", "<f8"),
+                       ("offset", "<i8"), ("count", "<i8")])
+RESULT_DTYPE = np.dtype([("n_bound", "<i8"), ("n_member", "<i8"), ("part_iter", "<i8"), ("n_band", "<i8"),
+                         ("k_vir", "<i8"), ("n_iter", "<i4"), ("status", "<i4"), ("m_vir", "<f8"),
+                         ("r_vir", "<f8"), ("vbulk", "<f8", (3,))])
+assert HALO_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 88
+
+# every symbol include/ahf.h declares
+EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_unbind_batch",
+           "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
+           "ahf_get_option", "ahf_sync")
+
+
+class AHFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libahfgpu error {code}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("H", ctypes.c_double), ("delta_rho", ctypes.c_double),
+                ("r_soft", ctypes.c_double), ("box", ctypes.c_double), ("band", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class _Particles(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
+                ("m", ctypes.c_void_p), ("m0", ctypes.c_double), ("n", ctypes.c_int64),
+                ("coord_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libahfgpu.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} not built: run paper_0904_3662_gb300.build_lib.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.ahf_version.restype = ctypes.c_int
+    lib.ahf_last_error.restype = ctypes.c_char_p
+    lib.ahf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.ahf_destroy.argtypes = [vp]
+    sig = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params), vp, vp, vp, vp, vp]
+    for name in ("ahf_unbind_batch", "ahf_unbind_batch_host", "ahf_unbind_plain"):
+        if hasattr(lib, name):
+            getattr(lib, name).argtypes = sig
+    if hasattr(lib, "ahf_profile_batch"):
+        lib.ahf_profile_batch.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
+                                          vp, vp, i32, ctypes.c_double, vp, vp]
+    lib.ahf_set_option.argtypes = [vp, ctypes.c_int, i64]
+    lib.ahf_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
+    lib.ahf_sync.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise AHFError(rc, _lib.ahf_last_error().decode())
+    return rc
+
+
+@dataclasses.dataclass
+class Params:
+    """Mirror of ahf_params (defaults: kpc/h, km/s, Msun/h; Delta = 200 rho_crit)."""
+    G: float = 4.3009e-6
+    H: float = 0.1
+    delta_rho: float = 200.0 * 3.0 * 0.1 * 0.1 / (8.0 * math.pi * 4.3009e-6)
+    r_soft: float = 0.0
+    box: float = 0.0
+    band: float = 1e-5
+    max_iter: int = 100
+    precision: int = PREC_MIXED
+
+    def c(self):
+        return _Params(self.G, self.H, self.delta_rho, self.r_soft, self.box, self.band,
+                       self.max_iter, self.precision)
+
+
+def halo_array(centre, radius, offset, count):
+    """Host halo descriptors as the C struct layout."""
+    n = len(offset)
+    h = np.zeros(n, dtype=HALO_DTYPE)
+    centre = np.asarray(centre, dtype=np.float64).reshape(n, 3)
+    h["cx"], h["cy"], h["cz"] = centre[:, 0], centre[:, 1], centre[:, 2]
+    h["radius"] = np.asarray(radius, dtype=np.float64)
+    h["offset"] = np.asarray(offset, dtype=np.int64)
+    h["count"] = np.asarray(count, dtype=np.int64)
+    return h
+
+
+@dataclasses.dataclass
+class Particles:
+    """Particle store: torch tensors (device) or numpy arrays (host)."""
+    x: object
+    y: object
+    z: object
+    vx: object
+    vy: object
+    vz: object
+    m: object = None
+    m0: float = 0.0
+    coord_type: int = COORD_F32_REL
+
+    @property
+    def n(self):
+        return int(self.x.shape[0])
+
+    def c(self):
+        def ptr(a):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                return a.ctypes.data
+            return a.data_ptr()
+        return _Particles(ptr(self.x), ptr(self.y), ptr(self.z), ptr(self.vx), ptr(self.vy), ptr(self.vz),
+                          ptr(self.m), float(self.m0), self.n, int(self.coord_type), 0)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def n_slots_of(halos, n_particles, member_idx):
+    if member_idx is None:
+        return int(n_particles)
+    return int((halos["offset"] + halos["count"]).max()) if len(halos) else 0
+
+
+class Context:
+    """An ahf_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self._p = ctypes.c_void_p()
+        _check(self.lib.ahf_create(ctypes.byref(self._p), int(device)))
+        self.device = device
+
+    def close(self):
+        if self._p:
+            self.lib.ahf_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, opt, value):
+        _check(self.lib.ahf_set_option(self._p, int(opt), int(value)))
+
+    def get_option(self, opt):
+        v = ctypes.c_int64()
+        _check(self.lib.ahf_get_option(self._p, int(opt), ctypes.byref(v)))
+        return v.value
+
+    def sync(self):
+        _check(self.lib.ahf_sync(self._p))
+
+    def alloc_outputs(self, n_halos, n_slots, with_phi=True, with_removed=True, precision=PREC_MIXED):
+        import torch
+        dev = torch.device("cuda", self.device)
+        out = {
+            "res": torch.empty(n_halos * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+            "bound_idx": torch.empty(max(n_slots, 1), dtype=torch.int64, device=dev),
+            "phi": None, "removed_iter": None,
+        }
+        if with_phi:
+            out["phi"] = torch.empty(max(n_slots, 1), device=dev,
+                                     dtype=torch.float64 if precision == PREC_FP64 else torch.float32)
+        if with_removed:
+            out["removed_iter"] = torch.empty(max(n_slots, 1), dtype=torch.int32, device=dev)
+        return out
+
+    def unbind_batch(self, parts: Particles, halos, params: Params, member_idx=None, out=None,
+                     with_phi=True, with_removed=True, stream=None, plain=False):
+        """Enqueue ahf_unbind_batch (or ahf_unbind_plain) on `stream`."""
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        n_slots = n_slots_of(halos, parts.n, member_idx)
+        if out is None:
+            out = self.alloc_outputs(len(halos), n_slots, with_phi, with_removed, params.precision)
+        pc, prc = parts.c(), params.c()
+        fn = self.lib.ahf_unbind_plain if plain else self.lib.ahf_unbind_batch
+        _check(fn(self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
+                  None if member_idx is None else member_idx.data_ptr(), ctypes.byref(prc),
+                  out["res"].data_ptr(), out["bound_idx"].data_ptr(),
+                  None if out["phi"] is None else out["phi"].data_ptr(),
+                  None if out["removed_iter"] is None else out["removed_iter"].data_ptr(),
+                  _stream_ptr(stream)))
+        return out
+
+    def unbind_batch_host(self, parts: Particles, halos, params: Params, member_idx=None, out=None,
+                          with_phi=True, with_removed=True, stream=None):
+        """ahf_unbind_batch_host: numpy inputs and outputs in host memory."""
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        n_slots = n_slots_of(halos, parts.n, member_idx)
+        if out is None:
+            out = {"res": np.zeros(len(halos), dtype=RESULT_DTYPE),
+                   "bound_idx": np.zeros(max(n_slots, 1), dtype=np.int64),
+                   "phi": np.zeros(max(n_slots, 1), dtype=np.float64 if params.precision == PREC_FP64
+                                   else np.float32) if with_phi else None,
+                   "removed_iter": np.zeros(max(n_slots, 1), dtype=np.int32) if with_removed else None}
+        pc, prc = parts.c(), params.c()
+
+        def p(a):
+            return None if a is None else a.ctypes.data
+        _check(self.lib.ahf_unbind_batch_host(
+            self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
+            None if member_idx is None else member_idx.ctypes.data, ctypes.byref(prc),
+            p(out["res"]), p(out["bound_idx"]), p(out["phi"]), p(out["removed_iter"]), _stream_ptr(stream)))
+        return out
+
+    def profile_batch(self, parts: Particles, halos, params: Params, res_dev, bound_idx, n_bins=32,
+                      r_min_frac=0.01, member_idx=None, prof=None, stream=None):
+        import torch
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        if prof is None:
+            prof = torch.empty((len(halos), n_bins, 4), dtype=torch.float64,
+                               device=torch.device("cuda", self.device))
+        pc, prc = parts.c(), params.c()
+        _check(self.lib.ahf_profile_batch(self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
+                                          None if member_idx is None else member_idx.data_ptr(),
+                                          ctypes.byref(prc), res_dev.data_ptr(), bound_idx.data_ptr(),
+                                          int(n_bins), float(r_min_frac), prof.data_ptr(), _stream_ptr(stream)))
+        return prof
+
+
+def results_to_numpy(res_tensor):
+    """Decode a device result buffer into a numpy structured array."""
+    raw = res_tensor.detach().cpu().numpy()
+    return raw.view(RESULT_DTYPE)
+
+
+def particles_from_population(pop, device="cuda"):
+    """Device copies of a synthetic population's particle arrays."""
+    import torch
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    m = None if pop.m is None else t(pop.m)
+    return Particles(t(pop.x), t(pop.y), t(pop.z), t(pop.vx), t(pop.vy), t(pop.vz), m, float(pop.m0),
+                     int(pop.coord_type))
+
+
+def halos_from_population(pop):
+    return halo_array(pop.centre, pop.radius, pop.offset, pop.count)
+
+
+def params_for(pop, **kw):
+    return Params(box=float(pop.box), **kw)

@@ -1,0 +1,254 @@
+// Device-side building blocks shared by the libahfgpu kernels.
+//
+// Exact sums.  GB300 runs FP64 adds at about 1/70 of the FP32 rate, so the
+// sums the method needs beyond FP32 precision -- M(<r), sum m/r, sum m v and
+// sum m (Appendix A, Sect. 2.1) -- are accumulated in 64-bit fixed point on
+// the integer pipes.  A halo-wide scale 2^s is picked from the largest term's
+// exponent and the member count so that no partial sum can overflow; each
+// term is rounded once when it is converted, after which every addition is
+// exact.  The result therefore does not depend on the order of the additions
+// (tile size, CTA count, batch composition), which a tree of FP64 adds cannot
+// promise.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ahf_internal.h"
+
+namespace ahf {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr uint32_t KEY_NONMEMBER = 0xffffffffu;   // sorts after every r >= 0
+
+// ---- fixed point ------------------------------------------------------------
+
+// Scale exponent s for sums of n terms of magnitude < 2^(emax+1): every
+// partial sum of term * 2^s stays below 2^62.
+__host__ __device__ __forceinline__ int fix_scale(int emax, long long n) {
+  int bits = 0;
+  while (bits < 40 && (1ll << bits) < n) ++bits;
+  return 61 - bits - emax;
+}
+
+// Unbiased exponent of a positive finite float (floor(log2 x)); -127 for 0.
+__device__ __forceinline__ int float_exponent_of_bits(uint32_t bits) {
+  return (int)((bits >> 23) & 0xff) - 127;
+}
+
+// round(x * 2^s) in integer arithmetic (round half away from zero).  The
+// caller guarantees |x| * 2^s < 2^62.
+__device__ __forceinline__ long long fix_from_float(float x, int s) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xff);
+  if (e == 0) return 0;                                   // zero / subnormal
+  const long long mant = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 150 + s;
+  long long v;
+  if (sh >= 0) v = mant << (sh > 39 ? 39 : sh);
+  else if (sh > -25) v = ((mant >> (-sh - 1)) + 1) >> 1;
+  else v = 0;
+  return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long fix_from_double(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = e - 1075 + s;
+  long long v;
+  if (sh >= 0) v = mant << (sh > 10 ? 10 : sh);
+  else if (sh > -54) v = ((mant >> (-sh - 1)) + 1) >> 1;
+  else v = 0;
+  return (b >> 63) ? -v : v;
+}
+
+// f * 2^e for any e (two steps when 2^e is outside the normal float range).
+__device__ __forceinline__ float scale_pow2f(float f, int e) {
+  while (e > 126) { f *= 8.5070592e37f; e -= 126; }          // 2^126
+  while (e < -126) { f *= 1.1754944e-38f; e += 126; }        // 2^-126
+  return f * __int_as_float((e + 127) << 23);
+}
+
+__host__ __device__ __forceinline__ double scale_pow2d(double f, int e) {
+  while (e > 1000) { f *= 1.0715086071862673e301; e -= 1000; }   // 2^1000
+  while (e < -1000) { f *= 9.332636185032189e-302; e += 1000; }  // 2^-1000
+  // 2^e as a double built from its exponent bits
+  union { unsigned long long u; double d; } p;
+  p.u = (unsigned long long)(e + 1023) << 52;
+  return f * p.d;
+}
+
+// int64 -> float using two 32-bit conversions (the 64-bit conversion runs on
+// the slow FP64 path on this part), then * 2^-s.  Error within 1 ulp.
+__device__ __forceinline__ float float_from_fix(long long v, int s) {
+  const float hi = (float)(int)(v >> 32);
+  const float lo = (float)(unsigned)(v & 0xffffffffll);
+  return scale_pow2f(fmaf(hi, 4294967296.0f, lo), -s);
+}
+
+__device__ __forceinline__ double double_from_fix(long long v, int s) {
+  const double hi = (double)(int)(v >> 32);
+  const double lo = (double)(unsigned)(v & 0xffffffffll);
+  return scale_pow2d(fma(hi, 4294967296.0, lo), -s);
+}
+
+// ---- recentring (Sect. 2.1: the sphere around the candidate centre) -----------
+
+// Coordinates are moved to 64-bit fixed point with `frac` fractional bits
+// (a float or double below 2^(62-frac) in magnitude converts exactly up to
+// bits finer than 2^-frac), the centre is subtracted as an integer, the
+// result wrapped to the minimum image and rounded once to float.  This is
+// the FP64-accurate recentring of large box coordinates without FP64 adds.
+__device__ __forceinline__ long long fixcoord_from_float(float x, int frac) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xff);
+  if (e == 0) return 0;
+  const long long mant = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 150 + frac;
+  long long v;
+  if (sh >= 0) v = mant << (sh > 39 ? 39 : sh);
+  else if (sh > -25) v = mant >> (-sh);
+  else v = 0;
+  return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long fixcoord_from_double(double x, int frac) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = e - 1075 + frac;
+  long long v;
+  if (sh >= 0) v = mant << (sh > 9 ? 9 : sh);
+  else if (sh > -54) v = mant >> (-sh);
+  else v = 0;
+  return (b >> 63) ? -v : v;
+}
+
+__device__ __forceinline__ long long wrap_fix(long long d, long long box) {
+  if (box > 0) {
+    const long long half = box >> 1;
+    if (d > half) d -= box;
+    else if (d < -half) d += box;
+  }
+  return d;
+}
+
+// Round an int64 to the nearest float (ties to even) with integer
+// operations only.
+__device__ __forceinline__ float f32_from_i64_rn(long long v) {
+  if (v == 0) return 0.0f;
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  int msb = 63 - __clzll((long long)a);
+  unsigned long long m;
+  if (msb <= 23) {
+    m = a << (23 - msb);
+  } else {
+    const int sh = msb - 23;
+    m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      m += 1ull;
+      if (m == (1ull << 24)) { m >>= 1; msb += 1; }
+    }
+  }
+  uint32_t bits = ((uint32_t)m & 0x7fffffu) | ((uint32_t)(msb + 127) << 23);
+  if (v < 0) bits |= 0x80000000u;
+  return __uint_as_float(bits);
+}
+
+// Fixed-point offset of one candidate from the halo centre (per axis).
+template <int CT>
+__device__ __forceinline__ void load_offset_fix(const ParticlesDev& p, long long i, const long long cfix[3],
+                                                long long boxfix, int frac, long long f[3]) {
+  if (CT == AHF_COORD_F64) {
+    f[0] = wrap_fix(fixcoord_from_double(__ldg((const double*)p.x + i), frac) - cfix[0], boxfix);
+    f[1] = wrap_fix(fixcoord_from_double(__ldg((const double*)p.y + i), frac) - cfix[1], boxfix);
+    f[2] = wrap_fix(fixcoord_from_double(__ldg((const double*)p.z + i), frac) - cfix[2], boxfix);
+  } else {
+    f[0] = wrap_fix(fixcoord_from_float(__ldg((const float*)p.x + i), frac) - cfix[0], boxfix);
+    f[1] = wrap_fix(fixcoord_from_float(__ldg((const float*)p.y + i), frac) - cfix[1], boxfix);
+    f[2] = wrap_fix(fixcoord_from_float(__ldg((const float*)p.z + i), frac) - cfix[2], boxfix);
+  }
+}
+
+// f * 2^-frac rounded to float (exact scaling of the correctly rounded integer).
+__device__ __forceinline__ float f32_from_fixcoord(long long f, int frac) {
+  return scale_pow2f(f32_from_i64_rn(f), -frac);
+}
+
+template <int CT>
+__device__ __forceinline__ void load_velocity(const ParticlesDev& p, long long i, float v[3]) {
+  if (CT == AHF_COORD_F64) {
+    v[0] = (float)__ldg((const double*)p.vx + i);
+    v[1] = (float)__ldg((const double*)p.vy + i);
+    v[2] = (float)__ldg((const double*)p.vz + i);
+  } else {
+    v[0] = __ldg((const float*)p.vx + i);
+    v[1] = __ldg((const float*)p.vy + i);
+    v[2] = __ldg((const float*)p.vz + i);
+  }
+}
+
+template <int CT>
+__device__ __forceinline__ float load_mass(const ParticlesDev& p, long long i) {
+  if (p.m == nullptr) return p.m0f;
+  if (CT == AHF_COORD_F64) return (float)__ldg((const double*)p.m + i);
+  return __ldg((const float*)p.m + i);
+}
+
+// Member of the gather sphere: |d| <= R decided in FP64 arithmetic.  The
+// float test settles all but the candidates within ~1e-6 of the surface.
+__device__ __forceinline__ bool inside_sphere(const long long f[3], const float df[3], int frac, double R2,
+                                              float R2lo, float R2hi) {
+  const float r2f = fmaf(df[2], df[2], fmaf(df[1], df[1], df[0] * df[0]));
+  if (r2f < R2lo) return true;
+  if (r2f > R2hi) return false;
+  double dd[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dd[k] = scale_pow2d((double)f[k], -frac);
+  const double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+  return r2 <= R2;
+}
+
+__device__ __forceinline__ float radius_of(const float df[3]) {
+  return sqrtf(fmaf(df[2], df[2], fmaf(df[1], df[1], df[0] * df[0])));
+}
+
+// m / max(r, r_soft) as the method's per-particle outer-sum term, and the
+// reciprocal radius it uses.  r' = 0 contributes nothing (pairs at zero
+// separation are dropped).
+__device__ __forceinline__ float rinv_of(float r, float r_soft) {
+  const float rr = fmaxf(r, r_soft);
+  return rr > 0.0f ? __frcp_rn(rr) : 0.0f;
+}
+
+// ---- warp / block scans ---------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+  return x;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace ahf

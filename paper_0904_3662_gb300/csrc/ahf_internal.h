@@ -1,0 +1,160 @@
+// Internal structures shared by the host scheduler and the kernels of
+// libahfgpu (not part of the public C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ahf.h"
+
+namespace ahf {
+
+// Device-side view of the caller's particle store.
+struct ParticlesDev {
+  const void *x, *y, *z, *vx, *vy, *vz, *m;
+  double m0;
+  float m0f;
+  int coord_type;
+  long long n;
+};
+
+// Per-halo descriptor prepared on the host.  Haloes are reordered by size
+// class and size; `index` is the caller's position (for the result record).
+struct HaloDev {
+  long long cfix[3];   // centre in 2^-frac units (mixed precision recentring)
+  double c[3];         // centre (FP64 recentring)
+  double R2;           // gather radius squared
+  float R2lo, R2hi;    // float bounds of R^2 that settle membership without FP64
+  long long offset;    // first candidate slot
+  long long count;     // candidate slots
+  long long gbase;     // first position in the multi-CTA class's flat arrays
+  int index;           // caller's halo index
+  int pad;
+};
+
+struct FrameDev {
+  long long boxfix;    // periodic box in 2^-frac units (0 = none)
+  double box;
+  int frac;            // fractional bits of the fixed-point coordinates
+};
+
+struct ParamsDev {
+  double G, H, delta_rho, r_soft, band;
+  float Gf, Hf, r_soft_f, band_f;
+  float crit_f;        // delta_rho * 4 pi / 3 as float
+  double crit;         // delta_rho * 4 pi / 3
+  int max_iter;
+  int precision;
+};
+
+struct OutputsDev {
+  ahf_result *res;
+  long long *bound_idx;
+  void *phi;
+  int *removed_iter;
+  const long long *member_idx;
+  long long n_slots;
+  int *err;            // device error word (bit flags, see ERR_*)
+};
+
+// Device error bits reported back through the error word.
+constexpr int ERR_BAD_INDEX = 1;     // a member index was out of range
+constexpr int ERR_TIMEOUT = 2;       // a bounded wait gave up
+constexpr int ERR_CAPACITY = 4;      // a halo exceeded its class capacity
+
+// Per-halo state of the multi-CTA class, kept in the context's workspace.
+struct GridHaloState {
+  unsigned long long mass_max_bits;  // float bits of the largest member mass
+  unsigned long long mr_max_bits;    // float bits of the largest m/r
+  unsigned long long mv_max_bits;    // float bits of the largest |m v_k|
+  long long n_member;
+  long long n_alive;
+  long long m_tot;                   // exact sum of member masses (fixed point)
+  long long mv[3];                   // exact sum of m v (fixed point)
+  long long t_tot;                   // exact sum of m/r (fixed point)
+  long long removed;                 // removed in the current iteration
+  long long band;                    // band tests so far
+  long long part_iter;
+  long long k_first;                 // first virial crossing (compacted index)
+  int n_iter;
+  int status;
+  int active;
+  int s_m, s_mr, s_mv;               // fixed-point scales
+  float vbulk[3];
+};
+
+// ---- launchers (defined in the .cu files) -----------------------------------
+
+struct OnchipLaunch {
+  ParticlesDev p;
+  FrameDev frame;
+  ParamsDev prm;
+  OutputsDev out;
+  const HaloDev *halos;  // this class's haloes, largest first
+  int n_halos;
+  int *queue;            // work counter (zeroed by the launcher)
+};
+
+// Largest candidate count the on-chip class accepts for a given variant.
+int onchip_capacity(int variant);
+// Launch the on-chip class (variant chosen by the scheduler).
+cudaError_t launch_onchip(const OnchipLaunch &L, int variant, int grid, cudaStream_t s);
+int onchip_max_grid(int variant, int device);
+
+struct GridLaunch {
+  ParticlesDev p;
+  FrameDev frame;
+  ParamsDev prm;
+  OutputsDev out;
+  HaloDev *halos;          // device copy of the class's haloes
+  int n_halos;
+  long long n_flat;        // sum of candidate counts of the class
+  GridHaloState *state;    // n_halos
+  // flat arrays (n_flat each unless noted)
+  uint32_t *key_a, *key_b, *val_a, *val_b;
+  float4 *wm;              // (w.x, w.y, w.z, m) with m's sign bit = removed
+  float *r;
+  long long *mc;           // compacted inclusive mass (final pass)
+  float *rc;               // compacted radius (final pass)
+  // tiles
+  int n_tiles;
+  int2 *tile_range;        // (first flat index, length)
+  int *tile_halo;
+  int *halo_tile0;         // first tile of each halo (n_halos + 1)
+  uint32_t *tile_hist;     // n_tiles * 256
+  long long *tile_agg;     // n_tiles * 3
+  long long *tile_pre;     // n_tiles * 3
+  int *any_active;         // device flag read by the host loop
+  uint32_t *key_or_and;    // 2 words
+};
+
+constexpr int GRID_TILE = 2048;
+constexpr int GRID_THREADS = 256;
+
+cudaError_t grid_prepare(const GridLaunch &L, cudaStream_t s);
+cudaError_t grid_sort(GridLaunch &L, cudaStream_t s, uint32_t or_bits, uint32_t and_bits);
+cudaError_t grid_fill(const GridLaunch &L, cudaStream_t s);
+cudaError_t grid_iterate(const GridLaunch &L, cudaStream_t s);
+cudaError_t grid_finish(const GridLaunch &L, cudaStream_t s);
+
+struct ProfileLaunch {
+  ParticlesDev p;
+  FrameDev frame;
+  ParamsDev prm;
+  OutputsDev out;
+  const HaloDev *halos;    // all haloes (caller order)
+  int n_halos;
+  const ahf_result *res;
+  const long long *bound_idx;
+  int n_bins;
+  double r_min_frac;
+  double *prof;
+  long long *chunk_acc;    // workspace: per chunk per bin (count, mass bits)
+  int *chunk_halo;         // chunk -> halo
+  long long *chunk_start;  // chunk -> first bound index position (slot)
+  int n_chunks;
+};
+constexpr int PROFILE_CHUNK = 4096;
+cudaError_t launch_profile(const ProfileLaunch &L, cudaStream_t s);
+
+}  // namespace ahf
