@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the batched unbinding stage (libahfgpu) on GB300.
+
+One step = one pass of the whole stage over one synthetic batch: gather +
+recentre + radial sort + iterated potential / escape test / removal +
+virial radius (ahf_unbind_batch) and the log-radial profile
+(ahf_profile_batch).  Metric: particle-iterations per second, where a
+particle-iteration is one member tested in one unbinding iteration (the
+count every implementation of the method performs; the library reports it
+per halo).
+
+Default workload: 2,000 NFW haloes, N_p ~ N^-1.9 on [100, 1e5] plus 15 %
+contaminants, float32 positions relative to each centre (about 1.8e6
+particles).  Inputs (~45 MB) are smaller than L2, so a 256 MiB buffer is
+written between timed steps to flush it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun each rank runs its own batch (seed +
+rank): haloes are independent, there is no collective on the data path,
+and the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-iterations/s"
+N_BINS = 32
+R_MIN_FRAC = 0.01
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ahf", "reference"], default="ahf")
+    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep"], default="batch")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, rank):
+    from paper_0904_3662_gb300 import synth
+    if name == "batch":
+        pop = synth.halo_batch(seed=synth.SEED_BASE + 2 + 1000 * rank)
+        desc = "2000 NFW haloes, N_p ~ N^-1.9 on [1e2, 1e5] + 15% contaminants, float32 relative SoA"
+    elif name == "single":
+        pop = synth.single_halo(seed=synth.SEED_BASE + 1 + 1000 * rank)
+        desc = "one NFW halo (1e4 particles, c=10, M=1e12) + 1e3 background, float64"
+    elif name == "tail":
+        pop = synth.large_tail(seed=synth.SEED_BASE + 3 + 1000 * rank)
+        desc = "64 hosts of 1e6-1e7 particles + 20 subhaloes each, float32 box coordinates, 500 Mpc/h box"
+    else:
+        pop = synth.precision_sweep(seed=synth.SEED_BASE + 4 + 1000 * rank)
+        desc = "1e5 NFW haloes, N_p ~ N^-1.9 on [1e2, 1e5] + 10% background, float64"
+    return pop, desc
+
+
+# ---- distributed plumbing (barrier + max over ranks only) -------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- clocks ------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- algorithmic bytes per phase (see the design notes) --------------------------------
+
+def class_of(counts, onchip_max=8192):
+    caps = [1024, 4096, min(8192, onchip_max)]
+    cls = np.full(counts.shape[0], 3)
+    for v in (2, 1, 0):
+        cls = np.where(counts <= caps[v], v, cls)
+    return cls
+
+
+def phase_bytes(pop, res, cls):
+    """Algorithmic HBM bytes of each phase for one step."""
+    es = 8 if pop.coord_type == 0 else 4
+    in_b = 6 * es + (es if pop.m is not None else 0)
+    cand = pop.count.astype(np.float64)
+    nb = res["n_bound"].astype(np.float64)
+    nm = res["n_member"].astype(np.float64)
+    pit = res["part_iter"].astype(np.float64)
+    out = np.zeros(7)
+    for v in range(3):
+        s = cls == v
+        # read the candidates once, write bound list + phi + the record
+        out[v] = in_b * cand[s].sum() + 12.0 * nb[s].sum() + 88.0 * s.sum()
+    g = cls == 3
+    out[3] = in_b * cand[g].sum() + 24.0 * nm[g].sum()           # inputs in, sorted SoA out
+    out[4] = 20.0 * pit[g].sum()                                  # (w, m) + r per particle-iteration
+    out[5] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
+    pos_b = 3 * es + (es if pop.m is not None else 0)
+    out[6] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)    # gather bound particles, write rows
+    return out
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+PHASE_SOURCES = {0: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 1: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 2: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 3: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 4: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 5: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
+                 6: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]}
+
+
+def measured_traffic(phase, workload):
+    """DRAM bytes per launch of a phase from the committed ncu summary, or
+    None when there is none or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    e = t.get(f"{workload}:{phase}")
+    if not e or e.get("source_hash") != source_hash(PHASE_SOURCES[phase]):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---- the CPU oracle as a baseline -----------------------------------------------------
+
+def cpu_baseline(pop, sample_desc=None, budget_s=30.0):
+    from oracle import ahf_oracle as O
+    from paper_0904_3662_gb300 import ahf
+    prm = ahf.params_for(pop)
+    op = O.Params(G=prm.G, H=prm.H, delta_rho=prm.delta_rho, r_soft=prm.r_soft, box=prm.box,
+                  max_iter=prm.max_iter, band=prm.band)
+    # a bounded sample: haloes in input order until the budget is spent
+    t0 = time.perf_counter()
+    units = 0
+    done = 0
+    for h in range(pop.n_halos):
+        r = O.unbind_population(pop, op, halos=[h], n_bins=N_BINS, r_min_frac=R_MIN_FRAC)[h]
+        units += r["part_iter"]
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": sample_desc or f"first {done} of {pop.n_halos} haloes of the same workload "
+                                     f"({units} particle-iterations, unbinding + profile), one process"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        barrier(world)
+        return 0
+    pop, desc = make_workload(args.workload, 0)
+    cb = []
+    # each step: the oracle over a bounded sample of the workload
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        cpu_baseline(pop, budget_s=budget)
+    vals = [cpu_baseline(pop, budget_s=budget) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "halos": pop.n_halos, "particles": pop.n_particles},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    barrier(world)
+    return 0
+
+
+# ---- the GPU arm -----------------------------------------------------------------------
+
+def run_ahf(args):
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_0904_3662_gb300 import ahf, build_lib
+    build_lib.build()
+    pop, desc = make_workload(args.workload, rank)
+    ctx = ahf.Context(local)
+    parts = ahf.particles_from_population(pop)
+    hal = ahf.halos_from_population(pop)
+    prm = ahf.params_for(pop)
+    n_slots = pop.n_particles
+    out = ctx.alloc_outputs(pop.n_halos, n_slots, with_phi=True, with_removed=False)
+    prof = torch.empty((pop.n_halos, N_BINS, 4), dtype=torch.float64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx.set_option(ahf.OPT_TIMING, 1)
+
+    def step():
+        ctx.unbind_batch(parts, hal, prm, out=out, stream=stream)
+        ctx.profile_batch(parts, hal, prm, out["res"], out["bound_idx"], n_bins=N_BINS, r_min_frac=R_MIN_FRAC,
+                          prof=prof, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.sync()
+    res = ahf.results_to_numpy(out["res"])
+    units = float(res["part_iter"].sum())
+    cls = class_of(pop.count)
+    pbytes = phase_bytes(pop, res, cls)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase_ms = np.zeros(7)
+    phase_n = np.zeros(7)
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()                         # L2 flush, outside the timed events
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+            st = ctx.stats()                      # waits for this step's phase events
+            launches += st["launches"]
+            for k in range(7):
+                if st["phase_ms"][k] >= 0:
+                    phase_ms[k] += st["phase_ms"][k]
+                    phase_n[k] += 1
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    ms_max = reduce_max(world, ms)
+    total_units = reduce_sum(world, units)
+    value = total_units / (ms_max / 1e3)
+
+    # roofline of the dominant phase (device time per launch of that phase)
+    avg = np.where(phase_n > 0, phase_ms / np.maximum(phase_n, 1), 0.0)
+    dom = int(np.argmax(avg))
+    peak, peak_kind = peaks()
+    achieved = pbytes[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
+    traffic = measured_traffic(dom, args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": ahf.PHASE_NAMES[dom], "algorithmic_bytes": float(pbytes[dom]),
+                "ms_per_launch": float(avg[dom]), "peak_source": peak_kind,
+                "phases_ms": {ahf.PHASE_NAMES[k]: round(float(avg[k]), 4) for k in range(7) if phase_n[k] > 0}}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+            "config": {"workload": desc, "halos": pop.n_halos, "particles": pop.n_particles,
+                       "particle_iterations_per_step": units, "l2": "flushed (256 MiB write) between steps",
+                       "parallelism": f"replicas x{world}, haloes independent, no collective"},
+            "gpu_launches": launches, "roofline": roofline,
+            "timed_wall_s": t_wall}
+    clocks = clk.summary()
+    line["clocks"] = clocks
+
+    if rank == 0 and not args.no_plain:
+        line["plain"] = time_plain(ctx, parts, hal, prm, out, stream, units, flush)
+        line["plain"]["batched_speedup"] = (units / (ms / 1e3)) / line["plain"]["value"]
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = time_e2e(ctx, pop, hal, prm, units, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pop)
+    if rank == 0:
+        print(json.dumps(line))
+    barrier(world)
+    return 0
+
+
+def time_plain(ctx, parts, hal, prm, out, stream, units, flush, steps=2):
+    """The plain one-halo-per-launch form on the same inputs (fewer steps: it
+    is slow by design)."""
+    import torch
+    ctx.unbind_batch(parts, hal, prm, out=out, stream=stream, plain=True)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.unbind_batch(parts, hal, prm, out=out, stream=stream, plain=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    return {"value": units / (ms / 1e3), "unit": METRIC, "ms_per_step": ms, "steps": steps,
+            "what": "ahf_unbind_plain: one halo at a time, separate launches per step, host sync per iteration "
+                    "(unbinding only, no profile)"}
+
+
+def time_e2e(ctx, pop, hal, prm, units, args):
+    """The same step through ahf_unbind_batch_host: pinned host inputs in,
+    results back in host memory, copies inside the timed region."""
+    import torch
+    from paper_0904_3662_gb300 import ahf
+
+    def pinned(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a)
+        t = torch.from_numpy(a.reshape(-1).view(np.uint8)).pin_memory()
+        return t.numpy().view(a.dtype).reshape(a.shape)
+    hp = ahf.Particles(pinned(pop.x), pinned(pop.y), pinned(pop.z), pinned(pop.vx), pinned(pop.vy),
+                       pinned(pop.vz), pinned(pop.m), pop.m0, pop.coord_type)
+    n = pop.n_particles
+    out = {"res": pinned(np.zeros(pop.n_halos, dtype=ahf.RESULT_DTYPE)),
+           "bound_idx": pinned(np.zeros(n, dtype=np.int64)), "phi": pinned(np.zeros(n, dtype=np.float32)),
+           "removed_iter": None, "prof": pinned(np.zeros((pop.n_halos, N_BINS, 4)))}
+    es = hp.x.dtype.itemsize
+    h2d = 6 * n * es + (n * es if pop.m is not None else 0) + hal.nbytes
+    d2h = out["res"].nbytes + out["bound_idx"].nbytes + out["phi"].nbytes + out["prof"].nbytes
+    for _ in range(max(1, args.warmup)):
+        ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
+    ts = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
+        ts.append(time.perf_counter() - t0)
+    s = float(np.mean(ts))
+    return {"value": units / s, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": s * 1e3, "api": "ahf_unbind_batch_host (unbinding + profile, host buffers)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ahf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

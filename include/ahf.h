@@ -161,13 +161,16 @@ int ahf_unbind_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos
                      int32_t *removed_iter, void *stream);
 
 /* The same computation with every pointer in HOST memory (pageable or
- * pinned): the call stages the inputs on the device, runs ahf_unbind_batch,
- * copies the outputs back and returns when they are in place (it
- * synchronises `stream`).  Same arguments, layouts and errors. */
+ * pinned): the call stages the inputs on the device, runs ahf_unbind_batch
+ * and, when n_bins > 0, ahf_profile_batch into `prof` (host double
+ * [n_halos][n_bins][4], may be NULL when n_bins is 0), copies the outputs
+ * back and returns when they are in place (it synchronises `stream`).
+ * Same arguments, layouts and errors as the two device entry points. */
 int ahf_unbind_batch_host(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
                           int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
                           ahf_result *out, int64_t *bound_idx, void *phi,
-                          int32_t *removed_iter, void *stream);
+                          int32_t *removed_iter, int32_t n_bins, double r_min_frac,
+                          double *prof, void *stream);
 
 /* Plain form of the same stage: one halo at a time, separate kernel launches
  * for gather, sort and each iteration's scan / test / compaction, and a host
@@ -204,9 +207,33 @@ int ahf_sync(ahf_ctx *ctx);
  *   AHF_OPT_ONCHIP_MAX   largest candidate count handled on chip by one CTA
  *   AHF_OPT_WAIT_LIMIT   spin iterations a bounded device wait may take before
  *                        it reports AHF_ERR_TIMEOUT (0 = give up at once)
+ *   AHF_OPT_TIMING       1 = record CUDA events around every phase of the
+ *                        following calls (read with ahf_get_stats), 0 = off
  * Errors: AHF_ERR_INVALID (unknown option or value). */
 #define AHF_OPT_ONCHIP_MAX 1
 #define AHF_OPT_WAIT_LIMIT 2
+#define AHF_OPT_TIMING     3
+
+/* Per-call statistics of the most recent unbinding or profile call.
+ * Phases: 0-2 the on-chip variants (1k / 4k / 8k slots), 3 the multi-CTA
+ * class's gather + sort + fill, 4 its iterations, 5 its final pass, 6 the
+ * profile.  phase_ms is device time between events recorded on the stream
+ * the phase ran on (valid only with AHF_OPT_TIMING on; -1 otherwise);
+ * phase_halos / phase_candidates count the haloes and candidate slots each
+ * phase covered. */
+#define AHF_N_PHASES 7
+typedef struct ahf_stats {
+  int64_t launches;                    /* kernels launched by the call        */
+  int64_t host_syncs;                  /* host synchronisations in the call   */
+  int64_t grid_iterations;             /* multi-CTA iterations launched       */
+  int64_t phase_halos[AHF_N_PHASES];
+  int64_t phase_candidates[AHF_N_PHASES];
+  double phase_ms[AHF_N_PHASES];
+} ahf_stats;
+
+/* Copy the statistics of the context's last call (waits for its device work
+ * when timing is on).  Errors: AHF_ERR_INVALID (NULL), AHF_ERR_CUDA. */
+int ahf_get_stats(ahf_ctx *ctx, ahf_stats *out);
 int ahf_set_option(ahf_ctx *ctx, int option, int64_t value);
 int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
 

@@ -23,7 +23,10 @@ ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2,
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
-OPT_ONCHIP_MAX, OPT_WAIT_LIMIT = 1, 2
+OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING = 1, 2, 3
+N_PHASES = 7
+PHASE_NAMES = ("onchip_1k", "onchip_4k", "onchip_8k", "grid_gather_sort", "grid_iterate", "grid_finish",
+               "profile")
 
 HALO_DTYPE = np.dtype([("cx", "<f8"), ("cy", "<f8"), ("cz", "<f8"), ("radius", "<f8"),
                        ("offset", "<i8"), ("count", "<i8")])
@@ -35,7 +38,7 @@ assert HALO_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 88
 # every symbol include/ahf.h declares
 EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_unbind_batch",
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
-           "ahf_get_option", "ahf_sync")
+           "ahf_get_option", "ahf_sync", "ahf_get_stats")
 
 
 class AHFError(RuntimeError):
@@ -57,6 +60,13 @@ class _Particles(ctypes.Structure):
                 ("coord_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("host_syncs", ctypes.c_int64),
+                ("grid_iterations", ctypes.c_int64),
+                ("phase_halos", ctypes.c_int64 * N_PHASES), ("phase_candidates", ctypes.c_int64 * N_PHASES),
+                ("phase_ms", ctypes.c_double * N_PHASES)]
+
+
 _lib = None
 
 
@@ -74,9 +84,10 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     lib.ahf_destroy.argtypes = [vp]
     sig = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params), vp, vp, vp, vp, vp]
-    for name in ("ahf_unbind_batch", "ahf_unbind_batch_host", "ahf_unbind_plain"):
-        if hasattr(lib, name):
-            getattr(lib, name).argtypes = sig
+    for name in ("ahf_unbind_batch", "ahf_unbind_plain"):
+        getattr(lib, name).argtypes = sig
+    lib.ahf_unbind_batch_host.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
+    lib.ahf_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     if hasattr(lib, "ahf_profile_batch"):
         lib.ahf_profile_batch.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
                                           vp, vp, i32, ctypes.c_double, vp, vp]
@@ -196,6 +207,13 @@ class Context:
     def sync(self):
         _check(self.lib.ahf_sync(self._p))
 
+    def stats(self):
+        st = _Stats()
+        _check(self.lib.ahf_get_stats(self._p, ctypes.byref(st)))
+        return {"launches": st.launches, "host_syncs": st.host_syncs, "grid_iterations": st.grid_iterations,
+                "phase_halos": list(st.phase_halos), "phase_candidates": list(st.phase_candidates),
+                "phase_ms": list(st.phase_ms)}
+
     def alloc_outputs(self, n_halos, n_slots, with_phi=True, with_removed=True, precision=PREC_MIXED):
         import torch
         dev = torch.device("cuda", self.device)
@@ -229,8 +247,9 @@ class Context:
         return out
 
     def unbind_batch_host(self, parts: Particles, halos, params: Params, member_idx=None, out=None,
-                          with_phi=True, with_removed=True, stream=None):
-        """ahf_unbind_batch_host: numpy inputs and outputs in host memory."""
+                          with_phi=True, with_removed=True, n_bins=0, r_min_frac=0.01, stream=None):
+        """ahf_unbind_batch_host: numpy inputs and outputs in host memory
+        (profile too when n_bins > 0)."""
         halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
         n_slots = n_slots_of(halos, parts.n, member_idx)
         if out is None:
@@ -238,7 +257,8 @@ class Context:
                    "bound_idx": np.zeros(max(n_slots, 1), dtype=np.int64),
                    "phi": np.zeros(max(n_slots, 1), dtype=np.float64 if params.precision == PREC_FP64
                                    else np.float32) if with_phi else None,
-                   "removed_iter": np.zeros(max(n_slots, 1), dtype=np.int32) if with_removed else None}
+                   "removed_iter": np.zeros(max(n_slots, 1), dtype=np.int32) if with_removed else None,
+                   "prof": np.zeros((len(halos), n_bins, 4)) if n_bins > 0 else None}
         pc, prc = parts.c(), params.c()
 
         def p(a):
@@ -246,7 +266,8 @@ class Context:
         _check(self.lib.ahf_unbind_batch_host(
             self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
             None if member_idx is None else member_idx.ctypes.data, ctypes.byref(prc),
-            p(out["res"]), p(out["bound_idx"]), p(out["phi"]), p(out["removed_iter"]), _stream_ptr(stream)))
+            p(out["res"]), p(out["bound_idx"]), p(out["phi"]), p(out["removed_iter"]),
+            int(n_bins), float(r_min_frac), p(out.get("prof")), _stream_ptr(stream)))
         return out
 
     def profile_batch(self, parts: Particles, halos, params: Params, res_dev, bound_idx, n_bins=32,

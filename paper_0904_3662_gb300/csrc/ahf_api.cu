@@ -74,22 +74,57 @@ struct ahf_ctx {
   int64_t onchip_max = 8192;
   int64_t wait_limit = 1 << 22;
   std::mutex mu;
-  // pinned staging for host descriptors
-  void* pin = nullptr;
-  size_t pin_bytes = 0;
+  // pinned staging for host descriptors: a ring of slots, each released by
+  // an event after the copies that read it, so a call never waits for the
+  // previous call's kernels just to reuse staging memory
+  static constexpr int NPIN = 4;
+  void* pin[NPIN] = {};
+  size_t pin_bytes[NPIN] = {};
+  cudaEvent_t pin_ev[NPIN] = {};
+  bool pin_ev_valid[NPIN] = {};
+  int pin_next = 0;
+  int pin_cur = -1;
+  int* flag_host = nullptr;      // pinned readback of small device words
+  char* stage = nullptr;         // device staging of the host-memory entry point
+  size_t stage_bytes = 0;
+  // per-call statistics and optional phase timing
+  bool timing = false;
+  ahf_stats stats{};
+  bool phase_used[AHF_N_PHASES] = {};
+  cudaEvent_t ev0[AHF_N_PHASES] = {}, ev1[AHF_N_PHASES] = {};
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // on-chip variants
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
 
-int ensure_pinned(ahf_ctx* c, size_t bytes) {
-  if (bytes <= c->pin_bytes) return AHF_OK;
-  if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
-  if (c->pin) cudaFreeHost(c->pin);
-  c->pin = nullptr;
-  c->pin_bytes = 0;
-  size_t want = std::max(bytes, (size_t)1 << 20);
-  if (cudaMallocHost(&c->pin, want) != cudaSuccess) return fail(AHF_ERR_NOMEM, "pinned staging of %zu bytes", want);
-  c->pin_bytes = want;
+// Take the next staging slot (waiting only for that slot's own copies) with
+// at least `bytes` of pinned memory; release with pin_release after the
+// copies are enqueued.
+int pin_acquire(ahf_ctx* c, size_t bytes, char** out) {
+  const int k = c->pin_next;
+  c->pin_next = (k + 1) % ahf_ctx::NPIN;
+  if (c->pin_ev_valid[k]) AHF_CUDA(cudaEventSynchronize(c->pin_ev[k]));
+  if (bytes > c->pin_bytes[k]) {
+    if (c->pin[k]) cudaFreeHost(c->pin[k]);
+    c->pin[k] = nullptr;
+    c->pin_bytes[k] = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    if (cudaMallocHost(&c->pin[k], want) != cudaSuccess) return fail(AHF_ERR_NOMEM, "pinned staging of %zu bytes", want);
+    c->pin_bytes[k] = want;
+  }
+  c->pin_cur = k;
+  *out = (char*)c->pin[k];
+  return AHF_OK;
+}
+
+int pin_release(ahf_ctx* c, cudaStream_t s) {
+  const int k = c->pin_cur;
+  if (k < 0) return AHF_OK;
+  AHF_CUDA(cudaEventRecord(c->pin_ev[k], s));
+  c->pin_ev_valid[k] = true;
+  c->pin_cur = -1;
   return AHF_OK;
 }
 
@@ -105,6 +140,27 @@ int ensure_workspace(ahf_ctx* c, size_t bytes) {
     return fail(AHF_ERR_NOMEM, "device workspace of %zu bytes", want);
   }
   c->ws_bytes = want;
+  return AHF_OK;
+}
+
+void reset_stats(ahf_ctx* c) {
+  c->stats = ahf_stats{};
+  for (int k = 0; k < AHF_N_PHASES; ++k) {
+    c->stats.phase_ms[k] = -1.0;
+    c->phase_used[k] = false;
+  }
+}
+
+int phase_begin(ahf_ctx* c, int ph, cudaStream_t s, long long halos, long long cands) {
+  c->phase_used[ph] = true;
+  c->stats.phase_halos[ph] += halos;
+  c->stats.phase_candidates[ph] += cands;
+  if (c->timing) AHF_CUDA(cudaEventRecord(c->ev0[ph], s));
+  return AHF_OK;
+}
+
+int phase_end(ahf_ctx* c, int ph, cudaStream_t s) {
+  if (c->timing) AHF_CUDA(cudaEventRecord(c->ev1[ph], s));
   return AHF_OK;
 }
 
@@ -159,7 +215,7 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
                   (long long)H.offset, (long long)(H.offset + H.count), (long long)n_slots);
     if (!(std::isfinite(H.cx) && std::isfinite(H.cy) && std::isfinite(H.cz)))
       return fail(AHF_ERR_INVALID, "halo %lld: centre not finite", (long long)h);
-    if (std::isnan(H.radius)) return fail(AHF_ERR_INVALID, "halo %lld: radius is NaN", (long long)h);
+    if (!std::isfinite(H.radius)) return fail(AHF_ERR_INVALID, "halo %lld: radius must be finite", (long long)h);
     if (H.count > 0) iv.emplace_back(H.offset, H.offset + H.count);
   }
   std::sort(iv.begin(), iv.end());
@@ -170,22 +226,7 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
 
 int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const ahf_params* prm,
               Plan& P) {
-  // fixed-point frame: every member coordinate and centre stays below 2^(61-frac)
-  double maxabs = prm->box;
-  for (int64_t h = 0; h < n_halos; ++h) {
-    const ahf_halo& H = halos[h];
-    const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
-    const double rad = std::isfinite(H.radius) ? std::fabs(H.radius) : 0.0;
-    maxabs = std::max(maxabs, cm + rad);
-  }
-  if (p->coord_type == AHF_COORD_F32_REL) maxabs = std::max(maxabs, 1.0);
-  int frac = 60 - ceil_log2(maxabs + 1.0);
-  if (frac > 200) frac = 200;
-  if (frac < -200) frac = -200;
-  P.frame.frac = frac;
   P.frame.box = prm->box;
-  P.frame.boxfix = prm->box > 0.0 ? (long long)std::llround(std::ldexp(prm->box, frac)) : 0;
-
   const int cap0 = onchip_capacity(0), cap1 = onchip_capacity(1);
   const int cap2 = (int)std::min<int64_t>(c->onchip_max, onchip_capacity(2));
   std::vector<int> cls((size_t)n_halos);
@@ -209,16 +250,24 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     const ahf_halo& H = halos[h];
     HaloDev& d = P.hd[k];
     d.c[0] = H.cx; d.c[1] = H.cy; d.c[2] = H.cz;
+    // fixed-point frame of this halo alone (so a halo's result does not
+    // depend on the rest of the batch): its centre, every member and the
+    // box stay below 2^(60-frac)
+    const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
+    double span = std::max(cm + std::fabs(H.radius), prm->box);
+    if (p->coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
+    int frac = 60 - ceil_log2(span + 1.0);
+    frac = std::max(-200, std::min(200, frac));
+    d.frac = frac;
+    d.boxfix = prm->box > 0.0 ? (long long)std::llround(std::ldexp(prm->box, frac)) : 0;
     for (int a = 0; a < 3; ++a) d.cfix[a] = (long long)std::llround(std::ldexp(d.c[a], frac));
     const double R = H.radius;
-    d.R2 = std::isinf(R) ? INFINITY : R * R;
+    d.R2 = R * R;
     d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
     d.R2hi = (float)(d.R2 * (1.0 + 4e-6));
-    if (std::isinf(d.R2)) { d.R2lo = INFINITY; d.R2hi = INFINITY; }
     d.offset = H.offset;
     d.count = H.count;
     d.index = h;
-    d.pad = 0;
     d.gbase = 0;
     if (cls[h] == 3) { d.gbase = gbase; gbase += H.count; }
   }
@@ -256,6 +305,59 @@ int end_call(ahf_ctx* c, cudaStream_t s) {
   return AHF_OK;
 }
 
+// Sort, fill, iterate (convergence read back on the host) and finish the
+// multi-CTA class; phases 3 (to the end of fill), 4 and 5.
+int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
+  int rc;
+  AHF_CUDA(cudaMemcpyAsync(c->flag_host, G.key_or_and, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AHF_CUDA(cudaStreamSynchronize(s));
+  c->stats.host_syncs += 1;
+  const uint32_t orb = (uint32_t)c->flag_host[0], andb = (uint32_t)c->flag_host[1];
+  AHF_CUDA(grid_sort(G, s, orb, andb));
+  c->stats.launches += 3 * G.sort_passes;
+  AHF_CUDA(grid_fill(G, s));
+  c->stats.launches += 1;
+  if ((rc = phase_end(c, 3, s))) return rc;
+  if ((rc = phase_begin(c, 4, s, G.n_halos, G.n_flat))) return rc;
+  for (int it = 1; it <= prm->max_iter; ++it) {
+    AHF_CUDA(cudaMemsetAsync(G.any_active, 0, sizeof(int), s));
+    AHF_CUDA(grid_iterate(G, it, s));
+    c->stats.launches += 4;
+    c->stats.grid_iterations += 1;
+    AHF_CUDA(cudaMemcpyAsync(c->flag_host + 2, G.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AHF_CUDA(cudaStreamSynchronize(s));
+    c->stats.host_syncs += 1;
+    if (c->flag_host[2] == 0) break;
+  }
+  if ((rc = phase_end(c, 4, s))) return rc;
+  if ((rc = phase_begin(c, 5, s, G.n_halos, G.n_flat))) return rc;
+  AHF_CUDA(grid_finish(G, s));
+  c->stats.launches += 5;
+  return phase_end(c, 5, s);
+}
+
+struct GridTables {
+  std::vector<int2> tile_range;
+  std::vector<int> tile_halo;
+  std::vector<int> halo_tile0;
+};
+
+void build_tiles(const Plan& P, int first, int n, GridTables& T) {
+  T.tile_range.clear();
+  T.tile_halo.clear();
+  T.halo_tile0.assign((size_t)n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    const HaloDev& d = P.hd[(size_t)first + k];
+    T.halo_tile0[k] = (int)T.tile_range.size();
+    for (long long o = 0; o < d.count; o += GRID_TILE) {
+      const long long len = std::min<long long>(GRID_TILE, d.count - o);
+      T.tile_range.push_back(make_int2((int)(d.gbase + o), (int)len));
+      T.tile_halo.push_back(k);
+    }
+  }
+  T.halo_tile0[n] = (int)T.tile_range.size();
+}
+
 int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                 const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
                 int32_t* removed_iter, cudaStream_t s) {
@@ -270,21 +372,66 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if (n_halos == 0) return AHF_OK;
   Plan P;
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
-  if (P.n_class[3] > 0)
-    return fail(AHF_ERR_INVALID, "haloes above %lld candidates need the multi-CTA class", (long long)c->onchip_max);
+  reset_stats(c);
+  const int n_onchip = P.n_class[0] + P.n_class[1] + P.n_class[2];
+  const int n_grid = P.n_class[3];
+  if (P.grid_flat >= (1ll << 31)) return fail(AHF_ERR_INVALID, "multi-CTA class above 2^31 candidates");
+  GridTables T;
+  if (n_grid) build_tiles(P, n_onchip, n_grid, T);
+  const int n_tiles = (int)T.tile_range.size();
+  const size_t nf = (size_t)P.grid_flat;
 
-  // workspace
-  size_t need = align_up(sizeof(HaloDev) * (size_t)n_halos, 256) + 4096;
-  if ((rc = ensure_workspace(c, need))) return rc;
-  if ((rc = ensure_pinned(c, sizeof(HaloDev) * (size_t)n_halos + 256))) return rc;
+  // workspace layout (must match the Bump sequence below)
+  auto layout = [&](Bump& B, GridLaunch* G) {
+    HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
+    int* queues = B.take<int>(16);
+    if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (uint32_t*)(queues + 10); }
+    if (n_grid) {
+      GridHaloState* st = B.take<GridHaloState>((size_t)n_grid);
+      uint32_t* ka = B.take<uint32_t>(nf);
+      uint32_t* kb = B.take<uint32_t>(nf);
+      uint32_t* va = B.take<uint32_t>(nf);
+      uint32_t* vb = B.take<uint32_t>(nf);
+      float4* wm = B.take<float4>(nf);
+      float* r = B.take<float>(nf);
+      long long* mc = B.take<long long>(nf);
+      float* rcp = B.take<float>(nf);
+      int2* trg = B.take<int2>((size_t)n_tiles);
+      int* th = B.take<int>((size_t)n_tiles);
+      int* ht0 = B.take<int>((size_t)n_grid + 1);
+      uint32_t* hist = B.take<uint32_t>((size_t)n_tiles * 256);
+      long long* agg = B.take<long long>((size_t)n_tiles * 3);
+      long long* pre = B.take<long long>((size_t)n_tiles * 3);
+      if (G) {
+        G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
+        G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
+        G->tile_hist = hist; G->tile_agg = agg; G->tile_pre = pre;
+      }
+    }
+    return hd;
+  };
+  Bump sizing{nullptr, 0, 0};
+  layout(sizing, nullptr);
+  if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
+  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 +
+                          (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
-  HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
-  int* queues = B.take<int>(16);
-  // the pinned staging buffer is reused by later calls: wait for its last copy
-  if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
-  std::memcpy(c->pin, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos);
-  AHF_CUDA(cudaMemcpyAsync(hd, c->pin, sizeof(HaloDev) * (size_t)n_halos, cudaMemcpyHostToDevice, s));
+  GridLaunch G{};
+  HaloDev* hd = layout(B, &G);
+  int* queues = reinterpret_cast<int*>(reinterpret_cast<char*>(hd) + align_up(sizeof(HaloDev) * (size_t)n_halos, 256));
+  char* pin = nullptr;
+  if ((rc = pin_acquire(c, pin_need, &pin))) return rc;
+  size_t po = 0;
+  auto stage = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    po = align_up(po, 256);
+    std::memcpy(pin + po, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, pin + po, bytes, cudaMemcpyHostToDevice, s);
+    po += bytes;
+    return e;
+  };
+  AHF_CUDA(stage(hd, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos));
   AHF_CUDA(cudaMemsetAsync(queues, 0, 16 * sizeof(int), s));
 
   OutputsDev O;
@@ -292,7 +439,26 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   O.member_idx = (const long long*)member_idx; O.n_slots = n_slots; O.err = c->err_dev;
   const ParticlesDev pd = to_dev(p);
   const ParamsDev prd = to_dev(prm);
+
+  if (n_grid) {
+    AHF_CUDA(stage(G.tile_range, T.tile_range.data(), sizeof(int2) * (size_t)n_tiles));
+    AHF_CUDA(stage(G.tile_halo, T.tile_halo.data(), sizeof(int) * (size_t)n_tiles));
+    AHF_CUDA(stage(G.halo_tile0, T.halo_tile0.data(), sizeof(int) * ((size_t)n_grid + 1)));
+    AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState) * (size_t)n_grid, s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(uint32_t), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
+    G.p = pd; G.frame = P.frame; G.prm = prd; G.out = O;
+    G.n_halos = n_grid; G.n_flat = (long long)nf; G.n_tiles = n_tiles;
+    if ((rc = phase_begin(c, 3, s, n_grid, (long long)nf))) return rc;
+    AHF_CUDA(grid_prepare(G, s));
+    c->stats.launches += 2;
+  }
+  if ((rc = pin_release(c, s))) return rc;
+  // the on-chip variants run on side streams, largest first, concurrently
+  // with the multi-CTA class on the caller's stream
+  AHF_CUDA(cudaEventRecord(c->fork, s));
   int first = 0;
+  int used_side[3] = {0, 0, 0};
   for (int v = 0; v < 3; ++v) {
     const int n = P.n_class[v];
     if (n > 0) {
@@ -300,11 +466,288 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       L.p = pd; L.frame = P.frame; L.prm = prd; L.out = O;
       L.halos = hd + first; L.n_halos = n; L.queue = queues + v;
       const int grid = std::min(n, onchip_max_grid(v, c->device));
-      AHF_CUDA(launch_onchip(L, v, grid, s));
+      long long cands = 0;
+      for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first + k].count;
+      AHF_CUDA(cudaStreamWaitEvent(c->side[2 - v], c->fork, 0));
+      if ((rc = phase_begin(c, v, c->side[2 - v], n, cands))) return rc;
+      AHF_CUDA(launch_onchip(L, v, grid, c->side[2 - v]));
+      c->stats.launches += 1;
+      if ((rc = phase_end(c, v, c->side[2 - v]))) return rc;
+      AHF_CUDA(cudaEventRecord(c->join[2 - v], c->side[2 - v]));
+      used_side[2 - v] = 1;
     }
     first += n;
   }
+  if (n_grid) {
+    if ((rc = run_grid(c, G, prm, s))) return rc;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (used_side[k]) AHF_CUDA(cudaStreamWaitEvent(s, c->join[k], 0));
   return end_call(c, s);
+}
+
+
+int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                 const int64_t* member_idx, const ahf_params* prm, const ahf_result* res, const int64_t* bound_idx,
+                 int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s) {
+  int rc = validate(p, halos, n_halos, prm, res, bound_idx);
+  if (rc) return rc;
+  if (n_halos > 0 && !prof) return fail(AHF_ERR_INVALID, "prof must not be NULL");
+  if (n_bins < 1 || n_bins > profile_max_bins()) return fail(AHF_ERR_INVALID, "n_bins must be in [1, %d]", profile_max_bins());
+  if (!(r_min_frac > 0.0 && r_min_frac < 1.0)) return fail(AHF_ERR_INVALID, "r_min_frac must be in (0, 1)");
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  if ((rc = validate_slots(halos, n_halos, n_slots, member_idx != nullptr))) return rc;
+  if (n_halos == 0) return AHF_OK;
+  Plan P;
+  if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
+  // descriptors in the caller's order (make_plan reorders by class)
+  std::vector<HaloDev> hd((size_t)n_halos);
+  for (const HaloDev& d : P.hd) hd[(size_t)d.index] = d;
+  std::vector<int> chunk_halo, halo_chunk0((size_t)n_halos + 1);
+  std::vector<long long> chunk_start;
+  for (int64_t h = 0; h < n_halos; ++h) {
+    halo_chunk0[(size_t)h] = (int)chunk_halo.size();
+    for (long long o = 0; o < halos[h].count; o += PROFILE_CHUNK) {
+      chunk_halo.push_back((int)h);
+      chunk_start.push_back(o);
+    }
+  }
+  halo_chunk0[(size_t)n_halos] = (int)chunk_halo.size();
+  const int n_chunks = (int)chunk_halo.size();
+  auto layout = [&](Bump& B, ProfileLaunch* L, int** h0) {
+    HaloDev* d = B.take<HaloDev>((size_t)n_halos);
+    int* ch = B.take<int>((size_t)n_chunks + 1);
+    long long* cs = B.take<long long>((size_t)n_chunks + 1);
+    int* hc0 = B.take<int>((size_t)n_halos + 1);
+    long long* acc = B.take<long long>((size_t)n_chunks * (1 + 2 * (size_t)n_bins) + 1);
+    if (L) { L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0; }
+  };
+  Bump sizing{nullptr, 0, 0};
+  layout(sizing, nullptr, nullptr);
+  if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
+  if ((rc = begin_call(c, s))) return rc;
+  Bump B{c->ws, 0, c->ws_bytes};
+  ProfileLaunch L{};
+  int* hc0 = nullptr;
+  layout(B, &L, &hc0);
+  char* pin = nullptr;
+  if ((rc = pin_acquire(c, sizing.used + 4096, &pin))) return rc;
+  size_t po = 0;
+  auto stage = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    po = align_up(po, 256);
+    std::memcpy(pin + po, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, pin + po, bytes, cudaMemcpyHostToDevice, s);
+    po += bytes;
+    return e;
+  };
+  AHF_CUDA(stage((void*)L.halos, hd.data(), sizeof(HaloDev) * (size_t)n_halos));
+  AHF_CUDA(stage(L.chunk_halo, chunk_halo.data(), sizeof(int) * (size_t)n_chunks));
+  AHF_CUDA(stage(L.chunk_start, chunk_start.data(), sizeof(long long) * (size_t)n_chunks));
+  AHF_CUDA(stage(hc0, halo_chunk0.data(), sizeof(int) * ((size_t)n_halos + 1)));
+  if ((rc = pin_release(c, s))) return rc;
+  L.p = to_dev(p);
+  L.frame = P.frame;
+  L.prm = to_dev(prm);
+  L.out.err = c->err_dev;
+  L.out.member_idx = (const long long*)member_idx;
+  L.n_halos = (int)n_halos;
+  L.res = res;
+  L.bound_idx = (const long long*)bound_idx;
+  L.n_bins = n_bins;
+  L.r_min_frac = r_min_frac;
+  L.prof = prof;
+  L.n_chunks = n_chunks;
+  for (int k = 0; k < AHF_N_PHASES; ++k) c->phase_used[k] = false;
+  c->stats.phase_ms[6] = -1.0;
+  c->stats.phase_halos[6] = 0;
+  c->stats.phase_candidates[6] = 0;
+  if ((rc = phase_begin(c, 6, s, n_halos, (long long)n_chunks * PROFILE_CHUNK))) return rc;
+  AHF_CUDA(launch_profile(L, hc0, s));
+  c->stats.launches += n_chunks > 0 ? 2 : 1;
+  if ((rc = phase_end(c, 6, s))) return rc;
+  return end_call(c, s);
+}
+
+// One halo at a time: the multi-CTA kernels on a single halo, with a host
+// synchronisation on every iteration's change flag (the plain launch form).
+int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+               const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
+               int32_t* removed_iter, cudaStream_t s) {
+  int rc = validate(p, halos, n_halos, prm, out, bound_idx);
+  if (rc) return rc;
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  if ((rc = validate_slots(halos, n_halos, n_slots, member_idx != nullptr))) return rc;
+  if (n_halos == 0) return AHF_OK;
+  Plan P;
+  if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
+  long long maxc = 1;
+  for (const HaloDev& d : P.hd) maxc = std::max(maxc, d.count);
+  const size_t nf = (size_t)maxc;
+  const int max_tiles = (int)((maxc + GRID_TILE - 1) / GRID_TILE);
+  auto layout = [&](Bump& B, GridLaunch* G) {
+    HaloDev* hd = B.take<HaloDev>(1);
+    int* words = B.take<int>(16);
+    GridHaloState* st = B.take<GridHaloState>(1);
+    uint32_t* ka = B.take<uint32_t>(nf);
+    uint32_t* kb = B.take<uint32_t>(nf);
+    uint32_t* va = B.take<uint32_t>(nf);
+    uint32_t* vb = B.take<uint32_t>(nf);
+    float4* wm = B.take<float4>(nf);
+    float* r = B.take<float>(nf);
+    long long* mc = B.take<long long>(nf);
+    float* rcp = B.take<float>(nf);
+    int2* trg = B.take<int2>((size_t)max_tiles);
+    int* th = B.take<int>((size_t)max_tiles);
+    int* ht0 = B.take<int>(2);
+    uint32_t* hist = B.take<uint32_t>((size_t)max_tiles * 256);
+    long long* agg = B.take<long long>((size_t)max_tiles * 3);
+    long long* pre = B.take<long long>((size_t)max_tiles * 3);
+    if (G) {
+      G->halos = hd; G->any_active = words + 8; G->key_or_and = (uint32_t*)(words + 10);
+      G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
+      G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
+      G->tile_hist = hist; G->tile_agg = agg; G->tile_pre = pre;
+    }
+  };
+  Bump sizing{nullptr, 0, 0};
+  layout(sizing, nullptr);
+  if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
+  const size_t pin_need = sizeof(HaloDev) + (sizeof(int2) + sizeof(int)) * (size_t)max_tiles + 1024;
+  if ((rc = begin_call(c, s))) return rc;
+  Bump B{c->ws, 0, c->ws_bytes};
+  GridLaunch G{};
+  layout(B, &G);
+  OutputsDev O;
+  O.res = out; O.bound_idx = (long long*)bound_idx; O.phi = phi; O.removed_iter = removed_iter;
+  O.member_idx = (const long long*)member_idx; O.n_slots = n_slots; O.err = c->err_dev;
+  G.p = to_dev(p); G.frame = P.frame; G.prm = to_dev(prm); G.out = O; G.n_halos = 1;
+  reset_stats(c);
+  for (const HaloDev& d0 : P.hd) {
+    HaloDev d = d0;
+    d.gbase = 0;
+    // one halo: tile table
+    std::vector<int2> tr;
+    std::vector<int> th;
+    for (long long o = 0; o < d.count; o += GRID_TILE) {
+      tr.push_back(make_int2((int)o, (int)std::min<long long>(GRID_TILE, d.count - o)));
+      th.push_back(0);
+    }
+    const int ht0[2] = {0, (int)tr.size()};
+    G.n_tiles = (int)tr.size();
+    G.n_flat = d.count;
+    char* pin = nullptr;
+    if ((rc = pin_acquire(c, pin_need, &pin))) return rc;
+    size_t po = 0;
+    auto stage = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      if (bytes == 0) return cudaSuccess;
+      po = align_up(po, 256);
+      std::memcpy(pin + po, src, bytes);
+      cudaError_t e = cudaMemcpyAsync(dst, pin + po, bytes, cudaMemcpyHostToDevice, s);
+      po += bytes;
+      return e;
+    };
+    AHF_CUDA(stage(G.halos, &d, sizeof(HaloDev)));
+    AHF_CUDA(stage(G.tile_range, tr.data(), sizeof(int2) * tr.size()));
+    AHF_CUDA(stage(G.tile_halo, th.data(), sizeof(int) * th.size()));
+    AHF_CUDA(stage(G.halo_tile0, ht0, sizeof(ht0)));
+    if ((rc = pin_release(c, s))) return rc;
+    AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(uint32_t), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
+    if (G.n_tiles == 0) {
+      // no candidates: an empty record
+      ahf_result R{};
+      R.status = AHF_HALO_EMPTY;
+      R.k_vir = -1;
+      AHF_CUDA(cudaMemcpyAsync(out + d.index, &R, sizeof(R), cudaMemcpyHostToDevice, s));
+      AHF_CUDA(cudaStreamSynchronize(s));
+      continue;
+    }
+    if ((rc = phase_begin(c, 3, s, 1, d.count))) return rc;
+    AHF_CUDA(grid_prepare(G, s));
+    c->stats.launches += 2;
+    if ((rc = run_grid(c, G, prm, s))) return rc;
+  }
+  return end_call(c, s);
+}
+
+// Host-memory form: stage the inputs in a device buffer, run, copy back.
+int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+              const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
+              int32_t* removed_iter, int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s) {
+  int rc = validate(p, halos, n_halos, prm, out, bound_idx);
+  if (rc) return rc;
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  const size_t es = p->coord_type == AHF_COORD_F64 ? 8 : 4;
+  const size_t n = (size_t)p->n;
+  const size_t ps = prm->precision == AHF_PREC_FP64 ? 8 : 4;
+  const size_t bytes = align_up(6 * n * es, 256) * 1 + align_up(p->m ? n * es : 0, 256) +
+                       align_up(member_idx ? (size_t)n_slots * 8 : 0, 256) + align_up(sizeof(ahf_result) * (size_t)n_halos, 256) +
+                       align_up((size_t)n_slots * 8, 256) + align_up(phi ? (size_t)n_slots * ps : 0, 256) +
+                       align_up(removed_iter ? (size_t)n_slots * 4 : 0, 256) +
+                       align_up(n_bins > 0 ? (size_t)n_halos * n_bins * 32 : 0, 256) + 8 * 256 + 4096;
+  if (n_bins < 0 || (n_bins > 0 && n_halos > 0 && !prof)) return fail(AHF_ERR_INVALID, "profile output missing");
+  if (bytes > c->stage_bytes) {
+    if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    if (cudaMalloc(&c->stage, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AHF_ERR_NOMEM, "device staging of %zu bytes", bytes);
+    }
+    c->stage_bytes = bytes;
+  }
+  AHF_CUDA(cudaSetDevice(c->device));
+  if (c->last_valid) AHF_CUDA(cudaStreamWaitEvent(s, c->last, 0));
+  Bump B{c->stage, 0, c->stage_bytes};
+  ahf_particles dp = *p;
+  const void* src[7] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m};
+  const void** dst[7] = {&dp.x, &dp.y, &dp.z, &dp.vx, &dp.vy, &dp.vz, &dp.m};
+  for (int k = 0; k < 7; ++k) {
+    if (!src[k]) continue;
+    char* d = B.take<char>(n * es);
+    if (n) AHF_CUDA(cudaMemcpyAsync(d, src[k], n * es, cudaMemcpyHostToDevice, s));
+    *dst[k] = d;
+  }
+  int64_t* dmi = nullptr;
+  if (member_idx) {
+    dmi = B.take<int64_t>((size_t)n_slots);
+    if (n_slots) AHF_CUDA(cudaMemcpyAsync(dmi, member_idx, (size_t)n_slots * 8, cudaMemcpyHostToDevice, s));
+  }
+  ahf_result* dout = B.take<ahf_result>((size_t)n_halos);
+  int64_t* dbi = B.take<int64_t>((size_t)std::max<int64_t>(n_slots, 1));
+  void* dphi = phi ? (void*)B.take<char>((size_t)std::max<int64_t>(n_slots, 1) * ps) : nullptr;
+  int32_t* dri = removed_iter ? B.take<int32_t>((size_t)std::max<int64_t>(n_slots, 1)) : nullptr;
+  double* dprof = n_bins > 0 ? B.take<double>((size_t)n_halos * n_bins * 4 + 1) : nullptr;
+  if ((rc = unbind_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, dphi, dri, s))) return rc;
+  if (n_bins > 0 &&
+      (rc = profile_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, n_bins, r_min_frac, dprof, s)))
+    return rc;
+  if (n_halos) AHF_CUDA(cudaMemcpyAsync(out, dout, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
+  if (n_bins > 0 && n_halos)
+    AHF_CUDA(cudaMemcpyAsync(prof, dprof, sizeof(double) * (size_t)n_halos * n_bins * 4, cudaMemcpyDeviceToHost, s));
+  if (n_slots) {
+    AHF_CUDA(cudaMemcpyAsync(bound_idx, dbi, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, s));
+    if (phi) AHF_CUDA(cudaMemcpyAsync(phi, dphi, (size_t)n_slots * ps, cudaMemcpyDeviceToHost, s));
+    if (removed_iter) AHF_CUDA(cudaMemcpyAsync(removed_iter, dri, (size_t)n_slots * 4, cudaMemcpyDeviceToHost, s));
+  }
+  AHF_CUDA(cudaEventRecord(c->last, s));
+  AHF_CUDA(cudaStreamSynchronize(s));
+  return AHF_OK;
 }
 
 }  // namespace
@@ -333,10 +776,25 @@ int ahf_create(ahf_ctx** ctx, int device) {
     if (cudaMalloc(&c->err_dev, sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "error word"); break; }
     if (cudaMemset(c->err_dev, 0, sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_CUDA, "memset"); break; }
     if (cudaMallocHost(&c->err_host, sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "pinned word"); break; }
-    if (cudaEventCreateWithFlags(&c->last, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&c->last, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) {
       rc = fail(AHF_ERR_CUDA, "event");
       break;
     }
+    if (cudaMallocHost(&c->flag_host, 16 * sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "pinned flags"); break; }
+    for (int k = 0; k < 3 && rc == AHF_OK; ++k) {
+      if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AHF_ERR_CUDA, "side stream");
+    }
+    for (int k = 0; k < AHF_N_PHASES && rc == AHF_OK; ++k) {
+      if (cudaEventCreate(&c->ev0[k]) != cudaSuccess || cudaEventCreate(&c->ev1[k]) != cudaSuccess)
+        rc = fail(AHF_ERR_CUDA, "phase events");
+    }
+    for (int k = 0; k < ahf_ctx::NPIN && rc == AHF_OK; ++k)
+      if (cudaEventCreateWithFlags(&c->pin_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AHF_ERR_CUDA, "staging events");
+    if (rc != AHF_OK) break;
   } while (0);
   if (rc != AHF_OK) {
     cudaGetLastError();
@@ -352,10 +810,24 @@ int ahf_destroy(ahf_ctx* c) {
   cudaSetDevice(c->device);
   if (c->last_valid) cudaEventSynchronize(c->last);
   if (c->ws) cudaFree(c->ws);
+  if (c->stage) cudaFree(c->stage);
   if (c->err_dev) cudaFree(c->err_dev);
   if (c->err_host) cudaFreeHost(c->err_host);
-  if (c->pin) cudaFreeHost(c->pin);
+  for (int k = 0; k < ahf_ctx::NPIN; ++k) {
+    if (c->pin[k]) cudaFreeHost(c->pin[k]);
+    if (c->pin_ev[k]) cudaEventDestroy(c->pin_ev[k]);
+  }
   if (c->last) cudaEventDestroy(c->last);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->flag_host) cudaFreeHost(c->flag_host);
+  for (int k = 0; k < 3; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->join[k]) cudaEventDestroy(c->join[k]);
+  }
+  for (int k = 0; k < AHF_N_PHASES; ++k) {
+    if (c->ev0[k]) cudaEventDestroy(c->ev0[k]);
+    if (c->ev1[k]) cudaEventDestroy(c->ev1[k]);
+  }
   delete c;
   return AHF_OK;
 }
@@ -372,6 +844,10 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value < 0) return fail(AHF_ERR_INVALID, "wait limit < 0");
       c->wait_limit = value;
       return AHF_OK;
+    case AHF_OPT_TIMING:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "timing is 0 or 1");
+      c->timing = value == 1;
+      return AHF_OK;
     default:
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
@@ -382,6 +858,7 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
   switch (option) {
     case AHF_OPT_ONCHIP_MAX: *value = c->onchip_max; return AHF_OK;
     case AHF_OPT_WAIT_LIMIT: *value = c->wait_limit; return AHF_OK;
+    case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
     default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }
@@ -407,6 +884,54 @@ int ahf_unbind_batch(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, 
   std::lock_guard<std::mutex> g(c->mu);
   return unbind_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter,
                      (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int ahf_unbind_batch_host(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                          const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx,
+                          void* phi, int32_t* removed_iter, int32_t n_bins, double r_min_frac, double* prof,
+                          void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return host_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, n_bins, r_min_frac,
+                   prof, (cudaStream_t)stream);
+}
+
+int ahf_get_stats(ahf_ctx* c, ahf_stats* out) {
+  if (!c || !out) return fail(AHF_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->timing) {
+    AHF_CUDA(cudaSetDevice(c->device));
+    for (int k = 0; k < AHF_N_PHASES; ++k) {
+      if (!c->phase_used[k]) continue;
+      AHF_CUDA(cudaEventSynchronize(c->ev1[k]));
+      float ms = 0.0f;
+      AHF_CUDA(cudaEventElapsedTime(&ms, c->ev0[k], c->ev1[k]));
+      c->stats.phase_ms[k] = ms;
+    }
+  }
+  *out = c->stats;
+  return AHF_OK;
+}
+
+int ahf_unbind_plain(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                     const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx,
+                     void* phi, int32_t* removed_iter, void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return plain_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, (cudaStream_t)stream);
+}
+
+int ahf_profile_batch(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                      const int64_t* member_idx, const ahf_params* prm, const ahf_result* res,
+                      const int64_t* bound_idx, int32_t n_bins, double r_min_frac, double* prof, void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return profile_impl(c, p, halos, n_halos, member_idx, prm, res, bound_idx, n_bins, r_min_frac, prof,
+                      (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -98,9 +98,10 @@ __device__ __forceinline__ double double_from_fix(long long v, int s) {
 
 // Coordinates are moved to 64-bit fixed point with `frac` fractional bits
 // (a float or double below 2^(62-frac) in magnitude converts exactly up to
-// bits finer than 2^-frac), the centre is subtracted as an integer, the
-// result wrapped to the minimum image and rounded once to float.  This is
-// the FP64-accurate recentring of large box coordinates without FP64 adds.
+// bits finer than 2^-frac; anything larger saturates far outside the
+// halo), the centre is subtracted as an integer, the result wrapped to the
+// minimum image and rounded once to float.  This is the FP64-accurate
+// recentring of large box coordinates without FP64 adds.
 __device__ __forceinline__ long long fixcoord_from_float(float x, int frac) {
   const uint32_t b = __float_as_uint(x);
   const int e = (int)((b >> 23) & 0xff);
@@ -108,7 +109,8 @@ __device__ __forceinline__ long long fixcoord_from_float(float x, int frac) {
   const long long mant = (long long)((b & 0x7fffffu) | 0x800000u);
   const int sh = e - 150 + frac;
   long long v;
-  if (sh >= 0) v = mant << (sh > 39 ? 39 : sh);
+  if (sh > 38) v = 1ll << 62;            // far outside every frame: saturate
+  else if (sh >= 0) v = mant << sh;
   else if (sh > -25) v = mant >> (-sh);
   else v = 0;
   return (b >> 31) ? -v : v;
@@ -121,7 +123,8 @@ __device__ __forceinline__ long long fixcoord_from_double(double x, int frac) {
   const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
   const int sh = e - 1075 + frac;
   long long v;
-  if (sh >= 0) v = mant << (sh > 9 ? 9 : sh);
+  if (sh > 8) v = 1ll << 62;             // far outside every frame: saturate
+  else if (sh >= 0) v = mant << sh;
   else if (sh > -54) v = mant >> (-sh);
   else v = 0;
   return (b >> 63) ? -v : v;

@@ -25,8 +25,6 @@ constexpr int TILE = GRID_TILE;         // 2048
 constexpr int IPT = TILE / T;           // 8 elements per thread
 constexpr int NWARP = T / 32;
 
-__device__ __forceinline__ int scale_m(const GridHaloState& s) { return s.s_m; }
-
 // ---- prepare ---------------------------------------------------------------------
 
 template <int CT>
@@ -51,11 +49,11 @@ __global__ void __launch_bounds__(T) g_prepare(GridLaunch L) {
     uint32_t key = KEY_NONMEMBER;
     if (ok) {
       long long f[3];
-      load_offset_fix<CT>(L.p, pi, H.cfix, L.frame.boxfix, L.frame.frac, f);
+      load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
       float df[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) df[a] = f32_from_fixcoord(f[a], L.frame.frac);
-      if (inside_sphere(f, df, L.frame.frac, H.R2, H.R2lo, H.R2hi)) {
+      for (int a = 0; a < 3; ++a) df[a] = f32_from_fixcoord(f[a], H.frac);
+      if (inside_sphere(f, df, H.frac, H.R2, H.R2lo, H.R2hi)) {
         const float r = radius_of(df);
         key = __float_as_uint(r);
         const float m = load_mass<CT>(L.p, pi);
@@ -107,6 +105,7 @@ __global__ void g_scales(GridLaunch L) {
   s.band = 0;
   s.removed = 0;
   s.mv[0] = s.mv[1] = s.mv[2] = 0;
+  s.k_first = 0x7fffffffffffffffll;
 }
 
 // ---- segmented radix sort ------------------------------------------------------------
@@ -225,14 +224,14 @@ __global__ void __launch_bounds__(T) g_fill(GridLaunch L, const uint32_t* __rest
       const long long slot = H.offset + val[g];
       const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
       long long f[3];
-      load_offset_fix<CT>(L.p, pi, H.cfix, L.frame.boxfix, L.frame.frac, f);
+      load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
       float v[3];
       load_velocity<CT>(L.p, pi, v);
       const float m = load_mass<CT>(L.p, pi);
       float4 w;
-      w.x = fmaf(L.prm.Hf, f32_from_fixcoord(f[0], L.frame.frac), v[0]);
-      w.y = fmaf(L.prm.Hf, f32_from_fixcoord(f[1], L.frame.frac), v[1]);
-      w.z = fmaf(L.prm.Hf, f32_from_fixcoord(f[2], L.frame.frac), v[2]);
+      w.x = fmaf(L.prm.Hf, f32_from_fixcoord(f[0], H.frac), v[0]);
+      w.y = fmaf(L.prm.Hf, f32_from_fixcoord(f[1], H.frac), v[1]);
+      w.z = fmaf(L.prm.Hf, f32_from_fixcoord(f[2], H.frac), v[2]);
       w.w = m;
       L.wm[g] = w;
       L.r[g] = __uint_as_float(key[g]);
@@ -599,8 +598,10 @@ cudaError_t grid_prepare(const GridLaunch& L, cudaStream_t s) {
 cudaError_t grid_sort(GridLaunch& L, cudaStream_t s, uint32_t or_bits, uint32_t and_bits) {
   const uint32_t diff = or_bits ^ and_bits;
   uint32_t *ki = L.key_a, *vi = L.val_a, *ko = L.key_b, *vo = L.val_b;
+  L.sort_passes = 0;
   for (int d = 0; d < 4; ++d) {
     if (!((diff >> (8 * d)) & 0xffu)) continue;
+    ++L.sort_passes;
     const int shift = 8 * d;
     g_hist<<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_hist, shift);
     g_offsets<<<L.n_halos, 256, 0, s>>>(L.tile_hist, L.halo_tile0);

@@ -28,14 +28,13 @@ struct HaloDev {
   long long offset;    // first candidate slot
   long long count;     // candidate slots
   long long gbase;     // first position in the multi-CTA class's flat arrays
+  long long boxfix;    // periodic box in this halo's 2^-frac units (0 = none)
+  int frac;            // fractional bits of this halo's fixed-point offsets
   int index;           // caller's halo index
-  int pad;
 };
 
 struct FrameDev {
-  long long boxfix;    // periodic box in 2^-frac units (0 = none)
-  double box;
-  int frac;            // fractional bits of the fixed-point coordinates
+  double box;          // periodic box (0 = none)
 };
 
 struct ParamsDev {
@@ -69,10 +68,13 @@ struct GridHaloState {
   unsigned long long mv_max_bits;    // float bits of the largest |m v_k|
   long long n_member;
   long long n_alive;
-  long long m_tot;                   // exact sum of member masses (fixed point)
-  long long mv[3];                   // exact sum of m v (fixed point)
-  long long t_tot;                   // exact sum of m/r (fixed point)
+  long long m_tot;                   // exact sum of alive masses (fixed point)
+  long long mv[3];                   // exact sum of m v of the alive set
+  long long t_tot;                   // exact sum of m/r of the alive set
   long long removed;                 // removed in the current iteration
+  long long rem_m;                   // exact mass removed in the current iteration
+  long long rem_mv[3];               // exact m v removed in the current iteration
+  long long band_iter;               // band tests in the current iteration
   long long band;                    // band tests so far
   long long part_iter;
   long long k_first;                 // first virial crossing (compacted index)
@@ -112,6 +114,7 @@ struct GridLaunch {
   GridHaloState *state;    // n_halos
   // flat arrays (n_flat each unless noted)
   uint32_t *key_a, *key_b, *val_a, *val_b;
+  uint32_t *key_x, *val_x;  // the sorted pair (one of a / b)
   float4 *wm;              // (w.x, w.y, w.z, m) with m's sign bit = removed
   float *r;
   long long *mc;           // compacted inclusive mass (final pass)
@@ -126,6 +129,7 @@ struct GridLaunch {
   long long *tile_pre;     // n_tiles * 3
   int *any_active;         // device flag read by the host loop
   uint32_t *key_or_and;    // 2 words
+  int sort_passes;         // radix passes the last grid_sort launched
 };
 
 constexpr int GRID_TILE = 2048;
@@ -134,7 +138,7 @@ constexpr int GRID_THREADS = 256;
 cudaError_t grid_prepare(const GridLaunch &L, cudaStream_t s);
 cudaError_t grid_sort(GridLaunch &L, cudaStream_t s, uint32_t or_bits, uint32_t and_bits);
 cudaError_t grid_fill(const GridLaunch &L, cudaStream_t s);
-cudaError_t grid_iterate(const GridLaunch &L, cudaStream_t s);
+cudaError_t grid_iterate(const GridLaunch &L, int iter, cudaStream_t s);
 cudaError_t grid_finish(const GridLaunch &L, cudaStream_t s);
 
 struct ProfileLaunch {
@@ -149,12 +153,13 @@ struct ProfileLaunch {
   int n_bins;
   double r_min_frac;
   double *prof;
-  long long *chunk_acc;    // workspace: per chunk per bin (count, mass bits)
+  long long *chunk_acc;    // workspace: per chunk (inner mass, per bin count and mass)
   int *chunk_halo;         // chunk -> halo
-  long long *chunk_start;  // chunk -> first bound index position (slot)
+  long long *chunk_start;  // chunk -> first position in the halo's bound list
   int n_chunks;
 };
 constexpr int PROFILE_CHUNK = 4096;
-cudaError_t launch_profile(const ProfileLaunch &L, cudaStream_t s);
+int profile_max_bins();
+cudaError_t launch_profile(const ProfileLaunch &L, const int *halo_chunk0, cudaStream_t s);
 
 }  // namespace ahf

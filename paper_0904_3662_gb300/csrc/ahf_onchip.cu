@@ -226,11 +226,11 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
         uint32_t key = KEY_NONMEMBER;
         if (ok) {
           long long f[3];
-          load_offset_fix<CT>(L.p, pi, H.cfix, L.frame.boxfix, L.frame.frac, f);
+          load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
           float df[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) df[k] = f32_from_fixcoord(f[k], L.frame.frac);
-          if (inside_sphere(f, df, L.frame.frac, H.R2, H.R2lo, H.R2hi)) {
+          for (int k = 0; k < 3; ++k) df[k] = f32_from_fixcoord(f[k], H.frac);
+          if (inside_sphere(f, df, H.frac, H.R2, H.R2lo, H.R2hi)) {
             const float r = radius_of(df);
             key = __float_as_uint(r);
             const float m = load_mass<CT>(L.p, pi);
@@ -292,14 +292,14 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
         const long long slot = H.offset + j;
         const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
         long long f[3];
-        load_offset_fix<CT>(L.p, pi, H.cfix, L.frame.boxfix, L.frame.frac, f);
+        load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
         float v[3];
         load_velocity<CT>(L.p, pi, v);
         const float m = load_mass<CT>(L.p, pi);
         mm[q] = m;
-        wx[q] = fmaf(P.Hf, f32_from_fixcoord(f[0], L.frame.frac), v[0]);
-        wy[q] = fmaf(P.Hf, f32_from_fixcoord(f[1], L.frame.frac), v[1]);
-        wz[q] = fmaf(P.Hf, f32_from_fixcoord(f[2], L.frame.frac), v[2]);
+        wx[q] = fmaf(P.Hf, f32_from_fixcoord(f[0], H.frac), v[0]);
+        wy[q] = fmaf(P.Hf, f32_from_fixcoord(f[1], H.frac), v[1]);
+        wz[q] = fmaf(P.Hf, f32_from_fixcoord(f[2], H.frac), v[2]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) smv[k] += fix_from_float(__fmul_rn(m, v[k]), s_v);
       }

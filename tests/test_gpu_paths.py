@@ -1,0 +1,264 @@
+"""GPU: every entry point of the C ABI against the oracle, plus the edge cases
+of the method (empty, ragged, degenerate haloes)."""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ahf_oracle as O
+from paper_0904_3662_gb300 import synth
+from tests.gpu_util import require_gpu, run_gpu
+from tests.parity import compare, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _pop_from_arrays(pos_list, vel_list, centres, radii, coord_type=synth.COORD_F32_REL, masses=None, m0=1e9,
+                     box=0.0):
+    """A population from explicit per-halo arrays (candidates back to back)."""
+    counts = np.array([p.shape[0] for p in pos_list], dtype=np.int64)
+    offset = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    pos = np.concatenate(pos_list) if counts.sum() else np.zeros((0, 3))
+    vel = np.concatenate(vel_list) if counts.sum() else np.zeros((0, 3))
+    dt = np.float64 if coord_type == synth.COORD_F64 else np.float32
+    m = None if masses is None else np.concatenate(masses).astype(dt)
+    return synth.Population(
+        name="custom", coord_type=coord_type,
+        x=pos[:, 0].astype(dt), y=pos[:, 1].astype(dt), z=pos[:, 2].astype(dt),
+        vx=vel[:, 0].astype(dt), vy=vel[:, 1].astype(dt), vz=vel[:, 2].astype(dt),
+        m=m, m0=m0, box=box, centre=np.asarray(centres, dtype=np.float64).reshape(-1, 3),
+        radius=np.asarray(radii, dtype=np.float64), offset=offset, count=counts,
+        r200=np.zeros(len(counts)), conc=np.zeros(len(counts)))
+
+
+def _check_all(pop, ctx=None, **kw):
+    out, prm, ctx, dev = run_gpu(pop, ctx=ctx, **kw)
+    s = compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+    return out, prm, ctx, dev, s
+
+
+def test_edge_cases_small():
+    rng = np.random.default_rng(1)
+    pl, vl, cs, rs = [], [], [], []
+    # 0: empty halo
+    pl.append(np.zeros((0, 3))); vl.append(np.zeros((0, 3))); cs.append([0, 0, 0]); rs.append(10.0)
+    # 1: single particle (Hubble flow unbinds it)
+    pl.append(np.array([[3.0, 0, 0]])); vl.append(np.array([[10.0, 0, 0]])); cs.append([0, 0, 0]); rs.append(10.0)
+    # 2: nobody inside the gather sphere
+    pl.append(rng.uniform(50, 60, (20, 3))); vl.append(np.zeros((20, 3))); cs.append([0, 0, 0]); rs.append(1.0)
+    # 3: a particle exactly at the centre plus a bound cloud
+    p, v = synth.sample_uniform_sphere(rng, 300, 5.0, 20.0)
+    p[0] = 0.0
+    pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(10.0)
+    # 4: duplicate positions (radius ties)
+    p, v = synth.sample_uniform_sphere(rng, 200, 5.0, 20.0)
+    p[100:150] = p[0:50]
+    pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(10.0)
+    # 5: every particle at 10 v_esc: all removed (EMPTY)
+    p, _ = synth.sample_uniform_sphere(rng, 500, 5.0, 0.0)
+    d = rng.standard_normal((500, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    vl.append(d * 3000.0); pl.append(p); cs.append([0, 0, 0]); rs.append(10.0)
+    # 6: cold sphere moving with the bulk (nothing removed without Hubble flow in its frame)
+    p, _ = synth.sample_uniform_sphere(rng, 700, 5.0, 0.0)
+    pl.append(p); vl.append(np.tile([[300.0, -200.0, 50.0]], (700, 1))); cs.append([0, 0, 0]); rs.append(10.0)
+    # 7: ragged sizes just around the class boundaries
+    for n in (1023, 1024, 1025, 4095, 4097, 8191, 8192):
+        p, v = synth.sample_nfw(rng, n, 10.0, 60.0)
+        pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(120.0)
+    pop = _pop_from_arrays(pl, vl, cs, rs, m0=1e9)
+    out, prm, ctx, dev, s = _check_all(pop)
+    res = out["res"]
+    assert res[0]["status"] & O.EMPTY and res[0]["n_iter"] == 0
+    assert res[2]["n_member"] == 0 and res[2]["status"] & O.EMPTY
+    assert res[5]["status"] & O.EMPTY
+    assert (out["removed_iter"][int(pop.offset[2]):int(pop.offset[2]) + 20] == -1).all()
+
+
+def test_edge_cases_multi_cta():
+    # the same degenerate haloes through the multi-CTA class
+    from paper_0904_3662_gb300 import ahf
+    require_gpu()
+    rng = np.random.default_rng(2)
+    pl, vl, cs, rs = [], [], [], []
+    pl.append(np.zeros((0, 3))); vl.append(np.zeros((0, 3))); cs.append([0, 0, 0]); rs.append(10.0)
+    pl.append(np.array([[3.0, 0, 0]])); vl.append(np.array([[10.0, 0, 0]])); cs.append([0, 0, 0]); rs.append(10.0)
+    pl.append(rng.uniform(50, 60, (20, 3))); vl.append(np.zeros((20, 3))); cs.append([0, 0, 0]); rs.append(1.0)
+    p, v = synth.sample_uniform_sphere(rng, 3000, 5.0, 20.0)
+    p[0] = 0.0
+    p[1500:2000] = p[0:500]
+    pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(10.0)
+    p, _ = synth.sample_uniform_sphere(rng, 2500, 5.0, 0.0)
+    d = rng.standard_normal((2500, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pl.append(p); vl.append(d * 3000.0); cs.append([0, 0, 0]); rs.append(10.0)
+    for n in (2047, 2048, 2049, 6000):
+        p, v = synth.sample_nfw(rng, n, 10.0, 60.0)
+        pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(120.0)
+    pop = _pop_from_arrays(pl, vl, cs, rs, m0=1e9)
+    ctx = ahf.Context(0)
+    ctx.set_option(ahf.OPT_ONCHIP_MAX, 0)
+    _check_all(pop, ctx=ctx)
+
+
+def test_member_index_list_and_gather_radius():
+    # candidates given through a permuted member list; gather radius cuts
+    # part of each halo
+    pop = synth.halo_batch(seed=11, n_halos=15, n_lo=200, n_hi=12000)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(pop.n_particles).astype(np.int64)
+    # member slots: halo h's slice lists its particles in shuffled order
+    member = np.empty(pop.n_particles, dtype=np.int64)
+    for h in range(pop.n_halos):
+        lo, n = int(pop.offset[h]), int(pop.count[h])
+        member[lo:lo + n] = lo + rng.permutation(n)
+    q = copy.copy(pop)
+    q.radius = pop.radius * 0.6
+    out, prm, _, _ = run_gpu(q, member_idx=member)
+    compare(q, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"], member_idx=member)
+
+
+@pytest.mark.parametrize("n_lo,n_hi", [(1500, 6000), (20_000, 40_000)])
+def test_periodic_box_float32_coordinates(n_lo, n_hi):
+    # haloes straddling the edges of a periodic box, float32 box coordinates
+    # (on-chip and multi-CTA classes)
+    pop = synth.large_tail(seed=5, n_halos=3, n_lo=n_lo, n_hi=n_hi, n_sub=5, box=5e5)
+    pop.centre[0] = [10.0, 499_990.0, 250_000.0]
+    pop.centre[1] = [499_999.0, 5.0, 3.0]
+    # rebuild coordinates around the moved centres
+    src = synth.large_tail(seed=5, n_halos=3, n_lo=n_lo, n_hi=n_hi, n_sub=5, box=5e5)
+    for h in range(2):
+        s = slice(int(pop.offset[h]), int(pop.offset[h] + pop.count[h]))
+        for a, k in enumerate("xyz"):
+            rel = getattr(src, k)[s].astype(np.float64) - src.centre[h, a]
+            rel = (rel + 2.5e5) % 5e5 - 2.5e5
+            getattr(pop, k)[s] = np.mod(rel + pop.centre[h, a], 5e5).astype(np.float32)
+    out, prm, _, _ = run_gpu(pop)
+    s = compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+    assert all(out["res"][h]["n_bound"] > 0.5 * pop.count[h] for h in range(3))
+
+
+def test_not_converged_and_softening():
+    pop = synth.halo_batch(seed=12, n_halos=10, n_lo=300, n_hi=20000)
+    from paper_0904_3662_gb300 import ahf
+    prm = ahf.params_for(pop, max_iter=1, r_soft=0.5)
+    out, prm, _, _ = run_gpu(pop, params=prm)
+    compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+    assert any(r["status"] & O.NOT_CONVERGED for r in out["res"])
+
+
+def test_plain_path_matches_batched():
+    pop = synth.halo_batch(seed=13, n_halos=12, n_lo=100, n_hi=15000)
+    a, prm, ctx, _ = run_gpu(pop)
+    b, _, _, _ = run_gpu(pop, plain=True, ctx=ctx)
+    compare(pop, prm, b["res"], b["bound_idx"], b["phi"], b["removed_iter"])
+    for h in range(pop.n_halos):
+        nb = int(a["res"][h]["n_bound"])
+        lo = int(pop.offset[h])
+        assert int(b["res"][h]["n_bound"]) == nb
+        np.testing.assert_array_equal(np.sort(a["bound_idx"][lo:lo + nb]), np.sort(b["bound_idx"][lo:lo + nb]))
+
+
+def test_host_entry_point_with_profile():
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=14, n_halos=20, n_lo=100, n_hi=12000)
+    ctx = ahf.Context(0)
+    parts = ahf.Particles(pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz, None, pop.m0, pop.coord_type)
+    prm = ahf.params_for(pop)
+    out = ctx.unbind_batch_host(parts, ahf.halos_from_population(pop), prm, n_bins=16, r_min_frac=0.02)
+    compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+    _check_profiles(pop, prm, out["res"], out["prof"], 16, 0.02)
+
+
+def _check_profiles(pop, prm, res, prof, n_bins, f):
+    ref = O.unbind_population(pop, oracle_params(prm), forced=None, n_bins=n_bins, r_min_frac=f)
+    for h in range(pop.n_halos):
+        o = ref[h]
+        gp = prof[h]
+        if o["order"].shape[0] == 0:
+            assert np.all(gp == 0.0)
+            continue
+        r_out = float(res[h]["r_vir"]) if res[h]["r_vir"] > 0 else float(o["r"][-1])
+        edges = r_out * f ** (1.0 - np.arange(n_bins + 1) / n_bins)
+        edges[-1] = r_out
+        near = np.zeros(n_bins, dtype=np.int64)
+        for b in range(n_bins):
+            for e in (edges[b], edges[b + 1]):
+                near[b] += int(np.sum(np.abs(o["r"] / e - 1.0) < 2e-5))
+        # counts may move between neighbouring bins only for particles on an edge
+        assert np.all(np.abs(gp[:, 0] - o["profile"][:, 0]) <= near), (h, gp[:, 0], o["profile"][:, 0])
+        mp = float(o["m"].max())
+        cum_near = np.cumsum(near)
+        assert np.all(np.abs(gp[:, 1] - o["profile"][:, 1]) <= cum_near * mp + 1e-9 * o["profile"][:, 1] + 1e-6)
+        ok = near == 0
+        np.testing.assert_allclose(gp[ok, 2], o["profile"][ok, 2], rtol=1e-5)
+        np.testing.assert_allclose(gp[ok, 3], o["profile"][ok, 3], rtol=1e-5)
+
+
+def test_profile_batch_device():
+    torch = require_gpu()
+    pop = synth.halo_batch(seed=15, n_halos=30, n_lo=100, n_hi=20000, with_masses=True)
+    out, prm, ctx, dev = run_gpu(pop)
+    from paper_0904_3662_gb300 import ahf
+    parts = ahf.particles_from_population(pop)
+    prof = ctx.profile_batch(parts, ahf.halos_from_population(pop), prm, dev["res"], dev["bound_idx"], n_bins=24,
+                             r_min_frac=0.01)
+    torch.cuda.synchronize()
+    _check_profiles(pop, prm, out["res"], prof.cpu().numpy(), 24, 0.01)
+
+
+def test_bitwise_repeatable_and_batch_independent():
+    # exact sums: identical outputs run to run and alone vs in a batch
+    torch = require_gpu()
+    pop = synth.halo_batch(seed=16, n_halos=40, n_lo=100, n_hi=20000)
+    a, prm, ctx, _ = run_gpu(pop)
+    b, _, _, _ = run_gpu(pop, ctx=ctx)
+    np.testing.assert_array_equal(a["removed_iter"], b["removed_iter"])
+    np.testing.assert_array_equal(a["res"].view(np.uint8), b["res"].view(np.uint8))
+    for h in range(pop.n_halos):          # slots past n_bound are unspecified
+        lo, nb = int(pop.offset[h]), int(a["res"][h]["n_bound"])
+        np.testing.assert_array_equal(a["bound_idx"][lo:lo + nb], b["bound_idx"][lo:lo + nb])
+        np.testing.assert_array_equal(a["phi"][lo:lo + nb], b["phi"][lo:lo + nb])
+    # halo 3 alone
+    h = 3
+    one = copy.copy(pop)
+    for k in ("centre", "radius", "offset", "count", "r200", "conc"):
+        setattr(one, k, getattr(pop, k)[h:h + 1])
+    c, _, _, _ = run_gpu(one, ctx=ctx)
+    lo, nb = int(pop.offset[h]), int(a["res"][h]["n_bound"])
+    np.testing.assert_array_equal(c["bound_idx"][lo:lo + nb], a["bound_idx"][lo:lo + nb])
+    np.testing.assert_array_equal(c["phi"][lo:lo + nb], a["phi"][lo:lo + nb])
+    assert c["res"][0].tobytes() == a["res"][h].tobytes()
+
+
+def test_invalid_arguments_are_rejected():
+    require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=17, n_halos=3, n_lo=100, n_hi=500)
+    ctx = ahf.Context(0)
+    parts = ahf.particles_from_population(pop)
+    hal = ahf.halos_from_population(pop)
+    bad = hal.copy()
+    bad["offset"][1] = bad["offset"][0]          # shared slots
+    with pytest.raises(ahf.AHFError) as e:
+        ctx.unbind_batch(parts, bad, ahf.params_for(pop))
+    assert e.value.code == ahf.ERR_INVALID
+    bad = hal.copy()
+    bad["count"][2] += 10 ** 9                   # beyond the particle store
+    with pytest.raises(ahf.AHFError):
+        ctx.unbind_batch(parts, bad, ahf.params_for(pop))
+    with pytest.raises(ahf.AHFError):
+        ctx.unbind_batch(parts, hal, ahf.params_for(pop, max_iter=0))
+    with pytest.raises(ahf.AHFError):
+        ctx.set_option(ahf.OPT_ONCHIP_MAX, 10 ** 7)
+    # out-of-range member index: reported by ahf_sync, no fault
+    import torch
+    member = torch.arange(pop.n_particles, dtype=torch.int64, device="cuda")
+    member[5] = 10 ** 12
+    ctx.unbind_batch(parts, hal, ahf.params_for(pop), member_idx=member)
+    with pytest.raises(ahf.AHFError) as e:
+        ctx.sync()
+    assert e.value.code == ahf.ERR_INVALID
+    ctx.sync()                                    # cleared
