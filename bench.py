@@ -44,6 +44,10 @@ R_MIN_FRAC = 0.01
 FLUSH_BYTES = 256 << 20
 
 
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,7 +302,9 @@ def run_ahf(args):
     torch.cuda.set_device(local)
     from paper_0904_3662_gb300 import ahf, build_lib
     build_lib.build()
+    t0 = time.perf_counter()
     pop, desc = make_workload(args.workload, rank)
+    log(f"workload {pop.n_halos} haloes / {pop.n_particles} particles in {time.perf_counter() - t0:.1f} s")
     ctx = ahf.Context(local)
     parts = ahf.particles_from_population(pop)
     hal = ahf.halos_from_population(pop)
@@ -376,13 +382,17 @@ def run_ahf(args):
     clocks = clk.summary()
     line["clocks"] = clocks
 
+    log(f"timed {args.steps} steps: {ms:.3f} ms/step, {value:.4g} {METRIC}")
     if rank == 0 and not args.no_plain:
         line["plain"] = time_plain(ctx, parts, hal, prm, out, stream, units, flush)
         line["plain"]["batched_speedup"] = (units / (ms / 1e3)) / line["plain"]["value"]
+        log(f"plain path {line['plain']['ms_per_step']:.1f} ms/step")
     if rank == 0 and not args.no_e2e:
         line["e2e"] = time_e2e(ctx, pop, hal, prm, units, args)
+        log(f"e2e {line['e2e']['ms_per_step']:.2f} ms/step")
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pop)
+        log(f"cpu baseline {line['cpu_baseline']['value']:.4g} {METRIC}")
     if rank == 0:
         print(json.dumps(line))
     barrier(world)

@@ -562,7 +562,7 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   L.r_min_frac = r_min_frac;
   L.prof = prof;
   L.n_chunks = n_chunks;
-  for (int k = 0; k < AHF_N_PHASES; ++k) c->phase_used[k] = false;
+  c->phase_used[6] = false;
   c->stats.phase_ms[6] = -1.0;
   c->stats.phase_halos[6] = 0;
   c->stats.phase_candidates[6] = 0;
