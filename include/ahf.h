@@ -237,6 +237,41 @@ int ahf_get_stats(ahf_ctx *ctx, ahf_stats *out);
 int ahf_set_option(ahf_ctx *ctx, int option, int64_t value);
 int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
 
+/* Allocation-free unbinding for callers that cannot let a library allocate.
+ *
+ * Which callers: applications that have given all device memory to their own
+ * allocator (a framework's caching allocator, a serving engine's fixed pool)
+ * and loops that must never block in cudaMalloc / cudaFree, which
+ * synchronise the whole device.  This entry point needs no context and
+ * allocates nothing, on the device or on the host.  It computes exactly what
+ * ahf_unbind_batch computes (same arguments, layouts and results) for
+ * batches whose haloes all fit the on-chip class.  The paper has no
+ * counterpart: it is an interface choice of this library.
+ *
+ * Limits: n_halos <= AHF_STATIC_MAX_HALOS and every halo's count <=
+ * AHF_STATIC_MAX_COUNT; larger requests return AHF_ERR_INVALID before any
+ * work is enqueued.  Only AHF_PREC_MIXED.
+ *
+ * Scratch: the halo descriptors and work counters live in one fixed array
+ * in device memory (about 3.3 MiB) that every GPU loading the library holds
+ * until the process exits.  All calls on a device share it and it keeps the
+ * last call's contents; each call clears the counters it uses.  Calls whose
+ * device work overlaps (different streams with no ordering between them)
+ * race on the array and give undefined results: serialise them.
+ *
+ * Set-up: the first call on a device (the current device, cudaGetDevice)
+ * looks up the array's device address with cudaGetSymbolAddress; make that
+ * first call before any stream capture.  The call runs on `stream` and
+ * returns without waiting.  An out-of-range member index makes that
+ * candidate a non-member and is not reported here (ahf_sync needs a
+ * context).  Errors: AHF_ERR_INVALID, AHF_ERR_CUDA; ahf_last_error() has
+ * the message. */
+#define AHF_STATIC_MAX_HALOS 32768
+#define AHF_STATIC_MAX_COUNT 8192
+int ahf_unbind_batch_static(const ahf_particles *p, const ahf_halo *halos, int64_t n_halos,
+                            const int64_t *member_idx, const ahf_params *prm, ahf_result *out,
+                            int64_t *bound_idx, void *phi, int32_t *removed_iter, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

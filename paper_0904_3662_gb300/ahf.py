@@ -38,7 +38,8 @@ assert HALO_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 88
 # every symbol include/ahf.h declares
 EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_unbind_batch",
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
-           "ahf_get_option", "ahf_sync", "ahf_get_stats")
+           "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static")
+STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
 
 
 class AHFError(RuntimeError):
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = sig
     lib.ahf_unbind_batch_host.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     lib.ahf_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.ahf_unbind_batch_static.argtypes = sig[1:]
     if hasattr(lib, "ahf_profile_batch"):
         lib.ahf_profile_batch.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
                                           vp, vp, i32, ctypes.c_double, vp, vp]

@@ -26,6 +26,7 @@ using namespace ahf;
 namespace {
 
 thread_local std::string g_last_error;
+thread_local const char* g_last_ptr = "";
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -34,6 +35,7 @@ int fail(int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_last_error = buf;
+  g_last_ptr = g_last_error.c_str();
   return code;
 }
 
@@ -61,6 +63,8 @@ struct Bump {
 };
 
 }  // namespace
+
+void ahf::set_last_error_static(const char* msg) { g_last_ptr = msg; }
 
 struct ahf_ctx {
   int device = 0;
@@ -756,7 +760,7 @@ extern "C" {
 
 int ahf_version(void) { return 100; }
 
-const char* ahf_last_error(void) { return g_last_error.c_str(); }
+const char* ahf_last_error(void) { return g_last_ptr; }
 
 int ahf_create(ahf_ctx** ctx, int device) {
   if (!ctx) return fail(AHF_ERR_INVALID, "ctx is NULL");

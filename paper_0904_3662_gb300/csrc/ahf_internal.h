@@ -85,6 +85,9 @@ struct GridHaloState {
   float vbulk[3];
 };
 
+// Record a static message as the thread's last error (no allocation).
+void set_last_error_static(const char *msg);
+
 // ---- launchers (defined in the .cu files) -----------------------------------
 
 struct OnchipLaunch {
