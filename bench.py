@@ -175,11 +175,16 @@ class ClockSampler:
 
 # ---- algorithmic bytes per phase (see the design notes) --------------------------------
 
-def class_of(counts, onchip_max=8192):
-    caps = [1024, 4096, min(8192, onchip_max)]
-    cls = np.full(counts.shape[0], 3)
-    for v in (2, 1, 0):
-        cls = np.where(counts <= caps[v], v, cls)
+CAPS = [1024, 4096, 8192, 4 * 8192, 8 * 8192, 16 * 8192]
+
+
+def class_of(counts):
+    """Size class of each halo as the library's scheduler assigns it:
+    0-2 single-CTA shared-memory variants, 3-5 clusters of 4/8/16 CTAs,
+    6 the multi-CTA class."""
+    cls = np.full(counts.shape[0], 6)
+    for v in range(5, -1, -1):
+        cls = np.where(counts <= CAPS[v], v, cls)
     return cls
 
 
@@ -191,17 +196,17 @@ def phase_bytes(pop, res, cls):
     nb = res["n_bound"].astype(np.float64)
     nm = res["n_member"].astype(np.float64)
     pit = res["part_iter"].astype(np.float64)
-    out = np.zeros(7)
-    for v in range(3):
+    out = np.zeros(10)
+    for v in range(6):
         s = cls == v
         # read the candidates once, write bound list + phi + the record
         out[v] = in_b * cand[s].sum() + 12.0 * nb[s].sum() + 88.0 * s.sum()
-    g = cls == 3
-    out[3] = in_b * cand[g].sum() + 24.0 * nm[g].sum()           # inputs in, sorted SoA out
-    out[4] = 20.0 * pit[g].sum()                                  # (w, m) + r per particle-iteration
-    out[5] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
+    g = cls == 6
+    out[6] = in_b * cand[g].sum() + 24.0 * nm[g].sum()           # inputs in, sorted SoA out
+    out[7] = 20.0 * pit[g].sum()                                  # (w, m) + r per particle-iteration
+    out[8] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
     pos_b = 3 * es + (es if pop.m is not None else 0)
-    out[6] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)    # gather bound particles, write rows
+    out[9] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)    # gather bound particles, write rows
     return out
 
 
@@ -213,13 +218,10 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-PHASE_SOURCES = {0: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 1: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 2: ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 3: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 4: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 5: ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"],
-                 6: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]}
+_ONCHIP = ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]
+_GRID = ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]
+PHASE_SOURCES = {0: _ONCHIP, 1: _ONCHIP, 2: _ONCHIP, 3: _ONCHIP, 4: _ONCHIP, 5: _ONCHIP, 6: _GRID, 7: _GRID,
+                 8: _GRID, 9: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]}
 
 
 def measured_traffic(phase, workload):
@@ -333,8 +335,8 @@ def run_ahf(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    phase_ms = np.zeros(7)
-    phase_n = np.zeros(7)
+    phase_ms = np.zeros(ahf.N_PHASES)
+    phase_n = np.zeros(ahf.N_PHASES)
     launches = 0
     barrier(world)
     torch.cuda.synchronize()
@@ -347,7 +349,7 @@ def run_ahf(args):
             ends[i].record(stream)
             st = ctx.stats()                      # waits for this step's phase events
             launches += st["launches"]
-            for k in range(7):
+            for k in range(ahf.N_PHASES):
                 if st["phase_ms"][k] >= 0:
                     phase_ms[k] += st["phase_ms"][k]
                     phase_n[k] += 1
@@ -369,7 +371,8 @@ def run_ahf(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": ahf.PHASE_NAMES[dom], "algorithmic_bytes": float(pbytes[dom]),
                 "ms_per_launch": float(avg[dom]), "peak_source": peak_kind,
-                "phases_ms": {ahf.PHASE_NAMES[k]: round(float(avg[k]), 4) for k in range(7) if phase_n[k] > 0}}
+                "phases_ms": {ahf.PHASE_NAMES[k]: round(float(avg[k]), 4) for k in range(ahf.N_PHASES)
+                              if phase_n[k] > 0}}
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

@@ -204,7 +204,9 @@ int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halo
 int ahf_sync(ahf_ctx *ctx);
 
 /* Tuning and diagnostics knobs (values persist in the context).
- *   AHF_OPT_ONCHIP_MAX   largest candidate count handled on chip by one CTA
+ *   AHF_OPT_ONCHIP_MAX   largest candidate count handled in shared memory (by one
+ *                        CTA or one thread-block cluster); larger haloes take the
+ *                        multi-CTA class (default and maximum 131072)
  *   AHF_OPT_WAIT_LIMIT   spin iterations a bounded device wait may take before
  *                        it reports AHF_ERR_TIMEOUT (0 = give up at once)
  *   AHF_OPT_TIMING       1 = record CUDA events around every phase of the
@@ -215,13 +217,14 @@ int ahf_sync(ahf_ctx *ctx);
 #define AHF_OPT_TIMING     3
 
 /* Per-call statistics of the most recent unbinding or profile call.
- * Phases: 0-2 the on-chip variants (1k / 4k / 8k slots), 3 the multi-CTA
- * class's gather + sort + fill, 4 its iterations, 5 its final pass, 6 the
- * profile.  phase_ms is device time between events recorded on the stream
+ * Phases: 0-2 the single-CTA shared-memory variants (1k / 4k / 8k slots),
+ * 3-5 the cluster variants (4 / 8 / 16 CTAs, 32k / 64k / 128k slots), 6 the
+ * multi-CTA class's gather + sort + fill, 7 its iterations, 8 its final
+ * pass, 9 the profile.  phase_ms is device time between events recorded on the stream
  * the phase ran on (valid only with AHF_OPT_TIMING on; -1 otherwise);
  * phase_halos / phase_candidates count the haloes and candidate slots each
  * phase covered. */
-#define AHF_N_PHASES 7
+#define AHF_N_PHASES 10
 typedef struct ahf_stats {
   int64_t launches;                    /* kernels launched by the call        */
   int64_t host_syncs;                  /* host synchronisations in the call   */

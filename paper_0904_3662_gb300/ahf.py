@@ -24,9 +24,9 @@ HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE =
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
 OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING = 1, 2, 3
-N_PHASES = 7
-PHASE_NAMES = ("onchip_1k", "onchip_4k", "onchip_8k", "grid_gather_sort", "grid_iterate", "grid_finish",
-               "profile")
+N_PHASES = 10
+PHASE_NAMES = ("onchip_1k", "onchip_4k", "onchip_8k", "cluster4_32k", "cluster8_64k", "cluster16_128k",
+               "grid_gather_sort", "grid_iterate", "grid_finish", "profile")
 
 HALO_DTYPE = np.dtype([("cx", "<f8"), ("cy", "<f8"), ("cz", "<f8"), ("radius", "<f8"),
                        ("offset", "<i8"), ("count", "<i8")])

@@ -75,7 +75,7 @@ struct ahf_ctx {
   int* err_host = nullptr;       // pinned mirror
   cudaEvent_t last = nullptr;    // end of the previous call's device work
   bool last_valid = false;
-  int64_t onchip_max = 8192;
+  int64_t onchip_max = 16 * 8192;    // largest candidate count of the shared-memory classes
   int64_t wait_limit = 1 << 22;
   std::mutex mu;
   // pinned staging for host descriptors: a ring of slots, each released by
@@ -96,9 +96,10 @@ struct ahf_ctx {
   ahf_stats stats{};
   bool phase_used[AHF_N_PHASES] = {};
   cudaEvent_t ev0[AHF_N_PHASES] = {}, ev1[AHF_N_PHASES] = {};
-  cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // on-chip variants
+  cudaStream_t side[6] = {};     // one stream per on-chip / cluster variant
   cudaEvent_t fork = nullptr;
-  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t join[6] = {};
+  int variant_grid[6] = {-1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
 };
 
 namespace {
@@ -176,7 +177,7 @@ int ceil_log2(double x) {
 
 struct Plan {
   std::vector<HaloDev> hd;     // reordered: class 0, 1, 2 (on-chip), then grid class
-  int n_class[4] = {0, 0, 0, 0};
+  int n_class[7] = {0, 0, 0, 0, 0, 0, 0};   // 0-5 shared-memory variants, 6 multi-CTA
   long long grid_flat = 0;
   FrameDev frame;
 };
@@ -231,15 +232,21 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
 int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const ahf_params* prm,
               Plan& P) {
   P.frame.box = prm->box;
-  const int cap0 = onchip_capacity(0), cap1 = onchip_capacity(1);
-  const int cap2 = (int)std::min<int64_t>(c->onchip_max, onchip_capacity(2));
+  // the smallest shared-memory variant that holds the halo and can run on
+  // this device, else the multi-CTA class
+  int caps[6];
+  for (int v = 0; v < 6; ++v) {
+    if (c->variant_grid[v] < 0) c->variant_grid[v] = onchip_max_grid(v, c->device);
+    caps[v] = c->variant_grid[v] > 0 ? (int)std::min<int64_t>(onchip_capacity(v), c->onchip_max) : 0;
+  }
   std::vector<int> cls((size_t)n_halos);
   for (int64_t h = 0; h < n_halos; ++h) {
     const int64_t n = halos[h].count;
-    cls[h] = n <= std::min<int64_t>(cap0, c->onchip_max) ? 0
-             : n <= std::min<int64_t>(cap1, c->onchip_max) ? 1
-             : n <= cap2 ? 2 : 3;
-    P.n_class[cls[h]]++;
+    int k = 6;
+    for (int v = 0; v < 6; ++v)
+      if (n <= caps[v]) { k = v; break; }
+    cls[h] = k;
+    P.n_class[k]++;
   }
   std::vector<int> order((size_t)n_halos);
   std::iota(order.begin(), order.end(), 0);
@@ -273,7 +280,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     d.count = H.count;
     d.index = h;
     d.gbase = 0;
-    if (cls[h] == 3) { d.gbase = gbase; gbase += H.count; }
+    if (cls[h] == 6) { d.gbase = gbase; gbase += H.count; }
   }
   P.grid_flat = gbase;
   return AHF_OK;
@@ -318,11 +325,11 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
   c->stats.host_syncs += 1;
   const uint32_t orb = (uint32_t)c->flag_host[0], andb = (uint32_t)c->flag_host[1];
   AHF_CUDA(grid_sort(G, s, orb, andb));
-  c->stats.launches += 3 * G.sort_passes;
+  c->stats.launches += 4 * G.sort_passes;
   AHF_CUDA(grid_fill(G, s));
   c->stats.launches += 1;
-  if ((rc = phase_end(c, 3, s))) return rc;
-  if ((rc = phase_begin(c, 4, s, G.n_halos, G.n_flat))) return rc;
+  if ((rc = phase_end(c, 6, s))) return rc;
+  if ((rc = phase_begin(c, 7, s, G.n_halos, G.n_flat))) return rc;
   for (int it = 1; it <= prm->max_iter; ++it) {
     AHF_CUDA(cudaMemsetAsync(G.any_active, 0, sizeof(int), s));
     AHF_CUDA(grid_iterate(G, it, s));
@@ -333,11 +340,11 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
     c->stats.host_syncs += 1;
     if (c->flag_host[2] == 0) break;
   }
-  if ((rc = phase_end(c, 4, s))) return rc;
-  if ((rc = phase_begin(c, 5, s, G.n_halos, G.n_flat))) return rc;
+  if ((rc = phase_end(c, 7, s))) return rc;
+  if ((rc = phase_begin(c, 8, s, G.n_halos, G.n_flat))) return rc;
   AHF_CUDA(grid_finish(G, s));
   c->stats.launches += 5;
-  return phase_end(c, 5, s);
+  return phase_end(c, 8, s);
 }
 
 struct GridTables {
@@ -377,8 +384,9 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Plan P;
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
   reset_stats(c);
-  const int n_onchip = P.n_class[0] + P.n_class[1] + P.n_class[2];
-  const int n_grid = P.n_class[3];
+  int n_onchip = 0;
+  for (int v = 0; v < 6; ++v) n_onchip += P.n_class[v];
+  const int n_grid = P.n_class[6];
   if (P.grid_flat >= (1ll << 31)) return fail(AHF_ERR_INVALID, "multi-CTA class above 2^31 candidates");
   GridTables T;
   if (n_grid) build_tiles(P, n_onchip, n_grid, T);
@@ -404,12 +412,13 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       int* th = B.take<int>((size_t)n_tiles);
       int* ht0 = B.take<int>((size_t)n_grid + 1);
       uint32_t* hist = B.take<uint32_t>((size_t)n_tiles * 256);
+      uint32_t* dbase = B.take<uint32_t>((size_t)n_grid * 256);
       long long* agg = B.take<long long>((size_t)n_tiles * 3);
       long long* pre = B.take<long long>((size_t)n_tiles * 3);
       if (G) {
         G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
         G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
-        G->tile_hist = hist; G->tile_agg = agg; G->tile_pre = pre;
+        G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
       }
     }
     return hd;
@@ -453,7 +462,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
     G.p = pd; G.frame = P.frame; G.prm = prd; G.out = O;
     G.n_halos = n_grid; G.n_flat = (long long)nf; G.n_tiles = n_tiles;
-    if ((rc = phase_begin(c, 3, s, n_grid, (long long)nf))) return rc;
+    if ((rc = phase_begin(c, 6, s, n_grid, (long long)nf))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
   }
@@ -462,30 +471,32 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   // with the multi-CTA class on the caller's stream
   AHF_CUDA(cudaEventRecord(c->fork, s));
   int first = 0;
-  int used_side[3] = {0, 0, 0};
-  for (int v = 0; v < 3; ++v) {
+  int used_side[6] = {0, 0, 0, 0, 0, 0};
+  // clusters (the largest haloes) first, then the single-CTA variants
+  int first_of[6];
+  for (int v = 0, f = 0; v < 6; ++v) { first_of[v] = f; f += P.n_class[v]; }
+  for (int v = 5; v >= 0; --v) {
     const int n = P.n_class[v];
-    if (n > 0) {
-      OnchipLaunch L;
-      L.p = pd; L.frame = P.frame; L.prm = prd; L.out = O;
-      L.halos = hd + first; L.n_halos = n; L.queue = queues + v;
-      const int grid = std::min(n, onchip_max_grid(v, c->device));
-      long long cands = 0;
-      for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first + k].count;
-      AHF_CUDA(cudaStreamWaitEvent(c->side[2 - v], c->fork, 0));
-      if ((rc = phase_begin(c, v, c->side[2 - v], n, cands))) return rc;
-      AHF_CUDA(launch_onchip(L, v, grid, c->side[2 - v]));
-      c->stats.launches += 1;
-      if ((rc = phase_end(c, v, c->side[2 - v]))) return rc;
-      AHF_CUDA(cudaEventRecord(c->join[2 - v], c->side[2 - v]));
-      used_side[2 - v] = 1;
-    }
-    first += n;
+    if (n == 0) continue;
+    OnchipLaunch L;
+    L.p = pd; L.frame = P.frame; L.prm = prd; L.out = O;
+    L.halos = hd + first_of[v]; L.n_halos = n; L.queue = queues + v;
+    long long cands = 0;
+    for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first_of[v] + k].count;
+    const int cs = onchip_cluster_size(v);
+    const int grid = (int)std::min<long long>((long long)n * cs, c->variant_grid[v]);
+    AHF_CUDA(cudaStreamWaitEvent(c->side[v], c->fork, 0));
+    if ((rc = phase_begin(c, v, c->side[v], n, cands))) return rc;
+    AHF_CUDA(launch_onchip(L, v, grid, c->side[v]));
+    c->stats.launches += 1;
+    if ((rc = phase_end(c, v, c->side[v]))) return rc;
+    AHF_CUDA(cudaEventRecord(c->join[v], c->side[v]));
+    used_side[v] = 1;
   }
   if (n_grid) {
     if ((rc = run_grid(c, G, prm, s))) return rc;
   }
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 6; ++k)
     if (used_side[k]) AHF_CUDA(cudaStreamWaitEvent(s, c->join[k], 0));
   return end_call(c, s);
 }
@@ -522,13 +533,19 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   }
   halo_chunk0[(size_t)n_halos] = (int)chunk_halo.size();
   const int n_chunks = (int)chunk_halo.size();
+  int n_multi = 0;
+  for (int64_t h = 0; h < n_halos; ++h) n_multi += halo_chunk0[(size_t)h + 1] - halo_chunk0[(size_t)h] > 1;
+  std::vector<double> factor((size_t)n_bins);
+  for (int b = 0; b < n_bins; ++b) factor[(size_t)b] = std::pow(r_min_frac, 1.0 - (double)b / (double)n_bins);
+  double* dfac = nullptr;
   auto layout = [&](Bump& B, ProfileLaunch* L, int** h0) {
     HaloDev* d = B.take<HaloDev>((size_t)n_halos);
     int* ch = B.take<int>((size_t)n_chunks + 1);
     long long* cs = B.take<long long>((size_t)n_chunks + 1);
     int* hc0 = B.take<int>((size_t)n_halos + 1);
-    long long* acc = B.take<long long>((size_t)n_chunks * (1 + 2 * (size_t)n_bins) + 1);
-    if (L) { L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0; }
+    double* fac = B.take<double>((size_t)n_bins);
+    long long* acc = B.take<long long>((size_t)n_chunks * (2 + 2 * (size_t)n_bins) + 1);
+    if (L) { L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0; dfac = fac; }
   };
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr, nullptr);
@@ -553,7 +570,10 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   AHF_CUDA(stage(L.chunk_halo, chunk_halo.data(), sizeof(int) * (size_t)n_chunks));
   AHF_CUDA(stage(L.chunk_start, chunk_start.data(), sizeof(long long) * (size_t)n_chunks));
   AHF_CUDA(stage(hc0, halo_chunk0.data(), sizeof(int) * ((size_t)n_halos + 1)));
+  AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * (size_t)n_bins));
   if ((rc = pin_release(c, s))) return rc;
+  L.edge_factor = dfac;
+  L.n_multi = n_multi;
   L.p = to_dev(p);
   L.frame = P.frame;
   L.prm = to_dev(prm);
@@ -566,14 +586,14 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   L.r_min_frac = r_min_frac;
   L.prof = prof;
   L.n_chunks = n_chunks;
-  c->phase_used[6] = false;
-  c->stats.phase_ms[6] = -1.0;
-  c->stats.phase_halos[6] = 0;
-  c->stats.phase_candidates[6] = 0;
-  if ((rc = phase_begin(c, 6, s, n_halos, (long long)n_chunks * PROFILE_CHUNK))) return rc;
+  c->phase_used[9] = false;
+  c->stats.phase_ms[9] = -1.0;
+  c->stats.phase_halos[9] = 0;
+  c->stats.phase_candidates[9] = 0;
+  if ((rc = phase_begin(c, 9, s, n_halos, (long long)n_chunks * PROFILE_CHUNK))) return rc;
   AHF_CUDA(launch_profile(L, hc0, s));
-  c->stats.launches += n_chunks > 0 ? 2 : 1;
-  if ((rc = phase_end(c, 6, s))) return rc;
+  c->stats.launches += (n_chunks > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0);
+  if ((rc = phase_end(c, 9, s))) return rc;
   return end_call(c, s);
 }
 
@@ -613,13 +633,14 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     int* th = B.take<int>((size_t)max_tiles);
     int* ht0 = B.take<int>(2);
     uint32_t* hist = B.take<uint32_t>((size_t)max_tiles * 256);
+    uint32_t* dbase = B.take<uint32_t>(256);
     long long* agg = B.take<long long>((size_t)max_tiles * 3);
     long long* pre = B.take<long long>((size_t)max_tiles * 3);
     if (G) {
       G->halos = hd; G->any_active = words + 8; G->key_or_and = (uint32_t*)(words + 10);
       G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
       G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
-      G->tile_hist = hist; G->tile_agg = agg; G->tile_pre = pre;
+      G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
     }
   };
   Bump sizing{nullptr, 0, 0};
@@ -676,7 +697,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
       AHF_CUDA(cudaStreamSynchronize(s));
       continue;
     }
-    if ((rc = phase_begin(c, 3, s, 1, d.count))) return rc;
+    if ((rc = phase_begin(c, 6, s, 1, d.count))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
     if ((rc = run_grid(c, G, prm, s))) return rc;
@@ -786,7 +807,7 @@ int ahf_create(ahf_ctx** ctx, int device) {
       break;
     }
     if (cudaMallocHost(&c->flag_host, 16 * sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "pinned flags"); break; }
-    for (int k = 0; k < 3 && rc == AHF_OK; ++k) {
+    for (int k = 0; k < 6 && rc == AHF_OK; ++k) {
       if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) != cudaSuccess)
         rc = fail(AHF_ERR_CUDA, "side stream");
@@ -824,7 +845,7 @@ int ahf_destroy(ahf_ctx* c) {
   if (c->last) cudaEventDestroy(c->last);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->flag_host) cudaFreeHost(c->flag_host);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 6; ++k) {
     if (c->side[k]) cudaStreamDestroy(c->side[k]);
     if (c->join[k]) cudaEventDestroy(c->join[k]);
   }
@@ -841,7 +862,7 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
   std::lock_guard<std::mutex> g(c->mu);
   switch (option) {
     case AHF_OPT_ONCHIP_MAX:
-      if (value < 0 || value > onchip_capacity(2)) return fail(AHF_ERR_INVALID, "onchip max out of range");
+      if (value < 0 || value > onchip_capacity(5)) return fail(AHF_ERR_INVALID, "onchip max out of range");
       c->onchip_max = value;
       return AHF_OK;
     case AHF_OPT_WAIT_LIMIT:

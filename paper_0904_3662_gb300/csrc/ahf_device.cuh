@@ -229,6 +229,13 @@ __device__ __forceinline__ float rinv_of(float r, float r_soft) {
   return rr > 0.0f ? __frcp_rn(rr) : 0.0f;
 }
 
+// phi_i = -G [M(<r_i) / r_i + sum_{j>=i} m_j / r_j] (Appendix A) from the
+// float values of the inner mass, 1/r and the outer sum, rounded the same
+// way in every kernel (explicit FMA: no compiler contraction choices).
+__device__ __forceinline__ float phi_of(float m_inner, float rinv, float outer, float G) {
+  return __fmul_rn(-G, __fmaf_rn(m_inner, rinv, outer));
+}
+
 // ---- warp / block scans ---------------------------------------------------------
 
 template <typename T>

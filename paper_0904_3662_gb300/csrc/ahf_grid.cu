@@ -6,7 +6,8 @@
 // each a grid-wide kernel:
 //   prepare   recentre, sphere test, radius key, exponent maxima
 //   sort      segmented stable LSD radix sort (per pass: tile histograms,
-//             per-halo digit offsets, stable tile scatter)
+//             per-(halo, digit) scans over tiles, per-halo digit bases,
+//             stable tile scatter)
 //   fill      sorted SoA (w.x, w.y, w.z, m) + radius, exact sum m v
 //   iterate   tile sums -> per-halo tile scan -> phi / escape test / removal
 //             -> per-halo bookkeeping, repeated while any halo changes
@@ -110,50 +111,78 @@ __global__ void g_scales(GridLaunch L) {
 
 // ---- segmented radix sort ------------------------------------------------------------
 
+// Tile histograms, stored per halo digit-major: the count of digit d in the
+// halo's tile i (i = t - t0) sits at hist[256 t0 + d T_h + i], T_h the halo's
+// tile count, so each digit's column over the halo's tiles is contiguous.
 __global__ void __launch_bounds__(T) g_hist(const uint32_t* __restrict__ key, const int2* __restrict__ tile_range,
+                                            const int* __restrict__ tile_halo, const int* __restrict__ halo_tile0,
                                             uint32_t* __restrict__ tile_hist, int shift) {
   __shared__ uint32_t h[256];
   const int t = blockIdx.x;
   const int2 tr = tile_range[t];
+  const int k = tile_halo[t];
+  const int t0 = halo_tile0[k], th = halo_tile0[k + 1] - t0;
   h[threadIdx.x] = 0;
   __syncthreads();
   for (int e = threadIdx.x; e < tr.y; e += T) atomicAdd(&h[(key[tr.x + e] >> shift) & 0xffu], 1u);
   __syncthreads();
-  tile_hist[(size_t)t * 256 + threadIdx.x] = h[threadIdx.x];
+  tile_hist[(size_t)t0 * 256 + (size_t)threadIdx.x * th + (t - t0)] = h[threadIdx.x];
 }
 
-// One CTA per halo: tile_hist[t][d] <- first destination (relative to the
-// halo) of tile t's digit-d elements: all smaller digits of the halo, then
-// digit d of the halo's earlier tiles.
-__global__ void __launch_bounds__(256) g_offsets(uint32_t* __restrict__ tile_hist, const int* __restrict__ halo_tile0) {
+// One CTA per (halo, digit): exclusive prefix of the digit's counts over the
+// halo's tiles (in place) and the digit's total.
+__global__ void __launch_bounds__(256) g_digit_scan(uint32_t* __restrict__ tile_hist, const int* __restrict__ halo_tile0,
+                                                    uint32_t* __restrict__ digit_base) {
   __shared__ uint32_t wt[8];
-  const int k = blockIdx.x;
-  const int t0 = halo_tile0[k], t1 = halo_tile0[k + 1];
-  const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
-  uint32_t tot = 0;
-  for (int t = t0; t < t1; ++t) {
-    const uint32_t c = tile_hist[(size_t)t * 256 + d];
-    tile_hist[(size_t)t * 256 + d] = tot;
-    tot += c;
+  __shared__ uint32_t carry;
+  const int k = blockIdx.x >> 8, d = blockIdx.x & 255;
+  const int t0 = halo_tile0[k], th = halo_tile0[k + 1] - t0;
+  uint32_t* col = tile_hist + (size_t)t0 * 256 + (size_t)d * th;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b = 0; b < th; b += 256) {
+    const int i = b + threadIdx.x;
+    const uint32_t v = i < th ? col[i] : 0u;
+    const uint32_t inc = warp_inclusive_scan(v, lane);
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    uint32_t base = carry;
+    for (int w = 0; w < warp; ++w) base += wt[w];
+    if (i < th) col[i] = base + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 255) carry = base + inc;
+    __syncthreads();
   }
-  const uint32_t inc = warp_inclusive_scan(tot, lane);
+  if (threadIdx.x == 0) digit_base[(size_t)k * 256 + d] = carry;
+}
+
+// One CTA per halo: digit totals -> first destination of each digit.
+__global__ void __launch_bounds__(256) g_digit_base(uint32_t* __restrict__ digit_base) {
+  __shared__ uint32_t wt[8];
+  const int k = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
+  const uint32_t v = digit_base[(size_t)k * 256 + d];
+  const uint32_t inc = warp_inclusive_scan(v, lane);
   if (lane == 31) wt[warp] = inc;
   __syncthreads();
-  uint32_t base = inc - tot;
+  uint32_t base = inc - v;
   for (int w = 0; w < warp; ++w) base += wt[w];
-  for (int t = t0; t < t1; ++t) tile_hist[(size_t)t * 256 + d] += base;
+  digit_base[(size_t)k * 256 + d] = base;
 }
 
 __global__ void __launch_bounds__(T) g_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                const int2* __restrict__ tile_range, const int* __restrict__ tile_halo,
-                                               const HaloDev* __restrict__ halos,
-                                               const uint32_t* __restrict__ tile_off, int shift) {
+                                               const int* __restrict__ halo_tile0, const HaloDev* __restrict__ halos,
+                                               const uint32_t* __restrict__ tile_off,
+                                               const uint32_t* __restrict__ digit_base, int shift) {
   __shared__ uint16_t hist[NWARP * 256];
   __shared__ uint32_t doff[256];
   const int t = blockIdx.x;
   const int2 tr = tile_range[t];
-  const long long gb = halos[tile_halo[t]].gbase;
+  const int kh = tile_halo[t];
+  const long long gb = halos[kh].gbase;
+  const int t0 = halo_tile0[kh], th = halo_tile0[kh + 1] - t0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < NWARP * 256; i += T) hist[i] = 0;
   __syncthreads();
@@ -189,7 +218,7 @@ __global__ void __launch_bounds__(T) g_scatter(const uint32_t* __restrict__ kin,
       hist[w * 256 + d] = (uint16_t)run;
       run += c;
     }
-    doff[d] = tile_off[(size_t)t * 256 + d];
+    doff[d] = digit_base[(size_t)kh * 256 + d] + tile_off[(size_t)t0 * 256 + (size_t)d * th + (t - t0)];
   }
   __syncthreads();
 #pragma unroll
@@ -393,9 +422,7 @@ __global__ void __launch_bounds__(T) g_apply(GridLaunch L, int iter) {
       const float ri = rinv_of(rv[q], P.r_soft_f);
       const long long mfix = fix_from_float(m, s_m);
       const long long rfix = fix_from_float(m * ri, s_r);
-      const float inner = float_from_fix(M, s_m) * ri;
-      const float outer = float_from_fix(Ttot - Pp, s_r);
-      const float phi = -P.Gf * (inner + outer);
+      const float phi = phi_of(float_from_fix(M, s_m), ri, float_from_fix(Ttot - Pp, s_r), P.Gf);
       const float ux = wmv[q].x - vb0, uy = wmv[q].y - vb1, uz = wmv[q].z - vb2;
       const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
       const float two_phi = -2.0f * phi;
@@ -493,9 +520,7 @@ __global__ void __launch_bounds__(T) g_emit(GridLaunch L) {
       const long long g = g0 + q;
       const float ri = rinv_of(rq[q], P.r_soft_f);
       const long long mfix = fix_from_float(m, s_m);
-      const float inner = float_from_fix(M, s_m) * ri;
-      const float outer = float_from_fix(Ttot - Pp, s_r);
-      const float phi = -P.Gf * (inner + outer);
+      const float phi = phi_of(float_from_fix(M, s_m), ri, float_from_fix(Ttot - Pp, s_r), P.Gf);
       const long long slot = H.offset + L.val_x[g];
       const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
       const long long dst = H.offset + C;
@@ -603,9 +628,11 @@ cudaError_t grid_sort(GridLaunch& L, cudaStream_t s, uint32_t or_bits, uint32_t 
     if (!((diff >> (8 * d)) & 0xffu)) continue;
     ++L.sort_passes;
     const int shift = 8 * d;
-    g_hist<<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_hist, shift);
-    g_offsets<<<L.n_halos, 256, 0, s>>>(L.tile_hist, L.halo_tile0);
-    g_scatter<<<L.n_tiles, T, 0, s>>>(ki, vi, ko, vo, L.tile_range, L.tile_halo, L.halos, L.tile_hist, shift);
+    g_hist<<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_halo, L.halo_tile0, L.tile_hist, shift);
+    g_digit_scan<<<L.n_halos * 256, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.digit_base);
+    g_digit_base<<<L.n_halos, 256, 0, s>>>(L.digit_base);
+    g_scatter<<<L.n_tiles, T, 0, s>>>(ki, vi, ko, vo, L.tile_range, L.tile_halo, L.halo_tile0, L.halos,
+                                      L.tile_hist, L.digit_base, shift);
     uint32_t* x;
     x = ki; ki = ko; ko = x;
     x = vi; vi = vo; vo = x;

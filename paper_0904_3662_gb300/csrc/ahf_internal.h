@@ -100,8 +100,9 @@ struct OnchipLaunch {
   int *queue;            // work counter (zeroed by the launcher)
 };
 
-// Largest candidate count the on-chip class accepts for a given variant.
+// Shared-memory variants 0..5: candidate capacity, CTAs per cluster.
 int onchip_capacity(int variant);
+int onchip_cluster_size(int variant);
 // Launch the on-chip class (variant chosen by the scheduler).
 cudaError_t launch_onchip(const OnchipLaunch &L, int variant, int grid, cudaStream_t s);
 int onchip_max_grid(int variant, int device);
@@ -127,7 +128,8 @@ struct GridLaunch {
   int2 *tile_range;        // (first flat index, length)
   int *tile_halo;
   int *halo_tile0;         // first tile of each halo (n_halos + 1)
-  uint32_t *tile_hist;     // n_tiles * 256
+  uint32_t *tile_hist;     // n_tiles * 256, per halo digit-major
+  uint32_t *digit_base;    // n_halos * 256
   long long *tile_agg;     // n_tiles * 3
   long long *tile_pre;     // n_tiles * 3
   int *any_active;         // device flag read by the host loop
@@ -156,10 +158,12 @@ struct ProfileLaunch {
   int n_bins;
   double r_min_frac;
   double *prof;
-  long long *chunk_acc;    // workspace: per chunk (inner mass, per bin count and mass)
+  long long *chunk_acc;    // workspace: per chunk (inner mass, inner count, per bin count and mass)
   int *chunk_halo;         // chunk -> halo
   long long *chunk_start;  // chunk -> first position in the halo's bound list
+  const double *edge_factor;  // f^(1 - b/n), b = 0..n-1
   int n_chunks;
+  int n_multi;             // haloes held by more than one chunk
 };
 constexpr int PROFILE_CHUNK = 4096;
 int profile_max_bins();

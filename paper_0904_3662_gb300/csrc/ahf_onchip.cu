@@ -1,24 +1,36 @@
-// On-chip class: one CTA unbinds one halo entirely in shared memory.
+// On-chip classes: a halo unbound entirely in shared memory, by one CTA or
+// by a thread-block cluster of CS CTAs sharing their shared memory (DSMEM).
 //
 // Per halo (Sect. 2.1 and Appendix A):
 //   gather   candidates -> (radius key, candidate position), FP64-accurate
 //            recentring and sphere test, exponent maxima for the exact sums
-//   sort     stable LSD radix sort of the keys in shared memory (once: the
-//            centre is fixed and particles only leave, so the survivors of
-//            every later iteration stay in radial order)
+//   sort     stable LSD radix sort of the keys, once: the centre is fixed and
+//            particles only leave, so the survivors of every later iteration
+//            stay in radial order.  In a cluster each CTA holds a contiguous
+//            chunk of the order and the scatter writes into the owner CTA's
+//            shared memory.
 //   fill     sorted SoA: radius, mass, w = v + H d; exact sum m v
-//   iterate  block scan of the exact M(<r) and sum m/r prefixes ->
+//   iterate  scan of the exact M(<r) and sum m/r prefixes ->
 //            phi_i = -G [M(<r_i)/r_i + sum_{j>=i} m_j/r_j], escape test
 //            |w - v_bulk|^2 > 2|phi|, removal of every unbound particle, until
-//            an iteration removes nothing
+//            an iteration removes nothing.  Each thread keeps the exact sums
+//            of its own particles and subtracts what it removes, so one pass
+//            over the particles per iteration suffices.
 //   emit     bound list (particle index, phi) in radial order, virial crossing
 //            of the final set (Sect. 2.1, Eqs. 1-2), result record
 //
-// CTAs are persistent: each pulls the next halo from a counter over the
-// class's haloes, which the host orders largest first.
+// CTAs (clusters) are persistent: each pulls the next halo from a counter over
+// the class's haloes, which the host orders largest first.  Cross-CTA values
+// go through a small exchange record in each CTA's shared memory, read by the
+// others after a hardware cluster barrier; every CTA combines them in rank
+// order, so all CTAs hold identical cluster-wide values.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "ahf_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ahf {
 namespace {
@@ -28,28 +40,61 @@ namespace {
 // per-thread runs and for warp-striped access.
 __device__ __forceinline__ int sw(int p, int mask) { return p ^ ((p >> 5) & mask); }
 
-template <int NT>
-struct Smem {
-  static constexpr int NW = NT / 32;
-  long long red[NW][4];          // per-warp partials (block scans / reductions)
-  long long scan_base[NW][3];
-  unsigned int or_bits, and_bits;
-  unsigned int max_m, max_mr, max_mv;
-  int n_member;
-  long long mv[3];               // exact sum m v of the current set
-  long long rem[4];              // removed this iteration: m, m v (3)
-  long long tot[3];              // scan totals: M, sum m/r, count
-  int removed;
-  int band;
-  int k_first;
+template <int CS>
+struct Cl {
+  static __device__ __forceinline__ int rank() {
+    if constexpr (CS > 1) return (int)cg::this_cluster().block_rank();
+    else return 0;
+  }
+  static __device__ __forceinline__ void sync() {
+    if constexpr (CS > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+  template <typename T>
+  static __device__ __forceinline__ T* at(T* p, int r) {
+    if constexpr (CS > 1) return cg::this_cluster().map_shared_rank(p, r);
+    else return p;
+  }
+};
+
+// Values a CTA publishes to the other CTAs of its cluster.
+struct Xchg {
   int halo;
-  float vb[3];
-  uint32_t dtot[256];            // radix sort digit totals / offsets
+  uint32_t g_or, g_and, g_mxm, g_mxr, g_mxv;
+  int g_nmem;
+  uint32_t cnt[256];            // radix pass: digit counts of this CTA
+  long long mv[3];              // fill: partial sum m v
+  long long tot[3];             // scan totals of this CTA (M, sum m/r, count)
+  long long rem[4];             // removed this iteration: m, m v (3)
+  int rem_n, rem_band;
+  float first_r;                // emit: first compacted radius of this CTA
+  int nb_loc;                   // emit: bound particles held by this CTA
+  int kf;                       // emit: first local virial crossing (global index)
 };
 
 template <int NT>
-__device__ __forceinline__ void block_exclusive_scan3(long long& a, long long& b, long long& c, Smem<NT>& S,
-                                                      long long& ta, long long& tb, long long& tc) {
+struct Smem {
+  static constexpr int NW = NT / 32;
+  long long red[NW][4];
+  long long scan_base[NW][3];
+  long long tot[3];
+  uint32_t or_bits, and_bits, max_m, max_mr, max_mv;
+  int n_member;
+  long long acc[4];             // block accumulators (m v or removed m, m v)
+  int acc_n, acc_band;
+  // cluster-wide values
+  long long c_pre[3];           // exclusive prefix over lower ranks
+  long long c_tot[3];
+  long long mv[3];              // exact sum m v of the current set
+  int c_removed, c_band;
+  int k_first;
+  float vb[3];
+  uint32_t dtot[256];
+  uint32_t dpre[256];
+};
+
+template <int NT>
+__device__ __forceinline__ void block_exclusive_scan3(long long& a, long long& b, long long& c, Smem<NT>& S) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long ia = warp_inclusive_scan(a, lane);
@@ -68,53 +113,81 @@ __device__ __forceinline__ void block_exclusive_scan3(long long& a, long long& b
   a = S.scan_base[warp][0] + ia - a;
   b = S.scan_base[warp][1] + ib - b;
   c = S.scan_base[warp][2] + ic - c;
-  ta = S.tot[0]; tb = S.tot[1]; tc = S.tot[2];
 }
 
-// Stable LSD radix sort of n (key, val) pairs, 8-bit digits, skipping the
-// digits in which all keys agree.  The last pass writes element p at
-// sw(p, mask).  Returns 0 if the result is in (kA, vA), 1 if in (kB, vB).
-template <int NT, int IPT>
-__device__ int block_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, uint16_t* hist,
-                                uint32_t* dtot, int n, uint32_t diff, int mask) {
+// Publish this CTA's three scan totals and combine the cluster's: S.c_pre
+// gets the sum over lower ranks, S.c_tot the sum over all ranks.
+template <int NT, int CS>
+__device__ __forceinline__ void cluster_scan_totals(Smem<NT>& S, Xchg& X, int rank) {
+  if constexpr (CS == 1) {
+    if (threadIdx.x < 3) {
+      S.c_pre[threadIdx.x] = 0;
+      S.c_tot[threadIdx.x] = S.tot[threadIdx.x];
+    }
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) { X.tot[0] = S.tot[0]; X.tot[1] = S.tot[1]; X.tot[2] = S.tot[2]; }
+    Cl<CS>::sync();
+    if (threadIdx.x < 3) {
+      long long pre = 0, tot = 0;
+      for (int r = 0; r < CS; ++r) {
+        const long long v = Cl<CS>::at(&X.tot[0], r)[threadIdx.x];
+        if (r < rank) pre += v;
+        tot += v;
+      }
+      S.c_pre[threadIdx.x] = pre;
+      S.c_tot[threadIdx.x] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// Stable LSD radix sort of the halo's keys, 8-bit digits, skipping the digits
+// in which all keys agree.  Each CTA of the cluster holds `nloc` elements of a
+// chunk of `chunk` positions, in order; the result keeps that partition, the
+// last pass writing element p of a CTA at sw(p, mask).  Returns 0 if the
+// result is in (kA, vA), 1 if in (kB, vB) (the same in every CTA).
+template <int NT, int IPT, int CS>
+__device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, uint16_t* hist, Smem<NT>& S,
+                                  Xchg& X, int nloc, int chunk, uint32_t diff, int mask, int rank) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int passes[4], np = 0;
   for (int d = 0; d < 4; ++d)
     if ((diff >> (8 * d)) & 0xffu) passes[np++] = d;
-  uint32_t *kin = kA, *vin = vA, *kout = kB, *vout = vB;
   if (np == 0) {
-    for (int p = threadIdx.x; p < n; p += NT) {
+    for (int p = threadIdx.x; p < nloc; p += NT) {
       kB[sw(p, mask)] = kA[p];
       vB[sw(p, mask)] = vA[p];
     }
     __syncthreads();
     return 1;
   }
-  const int chunk = ((n + NW * 32 - 1) / (NW * 32)) * 32;      // per-warp run
-  const int nb = chunk / 32;                                   // <= IPT
+  uint32_t *kin = kA, *vin = vA, *kout = kB, *vout = vB;
+  const int wchunk = ((nloc + NW * 32 - 1) / (NW * 32)) * 32;   // per-warp run
+  const int nb = wchunk / 32;                                   // <= IPT
   for (int ip = 0; ip < np; ++ip) {
     const int shift = 8 * passes[ip];
     const bool last = (ip == np - 1);
     for (int i = threadIdx.x; i < NW * 256; i += NT) hist[i] = 0;
     __syncthreads();
     uint32_t key[IPT], val[IPT];
-    uint16_t rank[IPT];
+    uint16_t rank_in[IPT];
 #pragma unroll
     for (int b = 0; b < IPT; ++b) {
       if (b < nb) {
-        const int e = warp * chunk + b * 32 + lane;
-        const bool valid = e < n;
+        const int e = warp * wchunk + b * 32 + lane;
+        const bool valid = e < nloc;
         key[b] = valid ? kin[e] : 0u;
         val[b] = valid ? vin[e] : 0u;
         const unsigned vmask = __ballot_sync(FULL_MASK, valid);
-        rank[b] = 0;
+        rank_in[b] = 0;
         if (valid) {
           const uint32_t dg = (key[b] >> shift) & 0xffu;
           const unsigned peers = __match_any_sync(vmask, dg);
           const unsigned below = peers & lanemask_lt();
           const uint16_t base = hist[warp * 256 + dg];
-          rank[b] = (uint16_t)(base + __popc(below));
+          rank_in[b] = (uint16_t)(base + __popc(below));
           __syncwarp(vmask);
           if (below == 0) hist[warp * 256 + dg] = (uint16_t)(base + __popc(peers));
         }
@@ -122,47 +195,55 @@ __device__ int block_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32
       }
     }
     __syncthreads();
-    // digit-major, warp-minor exclusive offsets: digit totals, one warp scans
-    // them, then each digit's per-warp counts become running offsets
+    // this CTA's digit counts; per-warp counts become within-CTA offsets
     for (int dg = threadIdx.x; dg < 256; dg += NT) {
-      uint32_t tot = 0;
-      for (int w = 0; w < NW; ++w) tot += hist[w * 256 + dg];
-      dtot[dg] = tot;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t loc[8], s = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) { loc[i] = dtot[lane * 8 + i]; s += loc[i]; }
-      const uint32_t inc = warp_inclusive_scan(s, lane);
-      uint32_t run = inc - s;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) { dtot[lane * 8 + i] = run; run += loc[i]; }
-    }
-    __syncthreads();
-    for (int dg = threadIdx.x; dg < 256; dg += NT) {
-      uint32_t run = dtot[dg];
+      uint32_t run = 0;
       for (int w = 0; w < NW; ++w) {
         const uint32_t h = hist[w * 256 + dg];
         hist[w * 256 + dg] = (uint16_t)run;
         run += h;
       }
+      X.cnt[dg] = run;
+    }
+    Cl<CS>::sync();
+    // cluster: digit totals, and counts of this digit in lower-ranked CTAs
+    for (int dg = threadIdx.x; dg < 256; dg += NT) {
+      uint32_t tot = 0, pre = 0;
+      for (int r = 0; r < CS; ++r) {
+        const uint32_t v = Cl<CS>::at(X.cnt, r)[dg];
+        if (r < rank) pre += v;
+        tot += v;
+      }
+      S.dtot[dg] = tot;
+      S.dpre[dg] = pre;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t loc[8], s = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { loc[i] = S.dtot[lane * 8 + i]; s += loc[i]; }
+      const uint32_t inc = warp_inclusive_scan(s, lane);
+      uint32_t run = inc - s;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { S.dtot[lane * 8 + i] = run + S.dpre[lane * 8 + i]; run += loc[i]; }
     }
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < IPT; ++b) {
       if (b < nb) {
-        const int e = warp * chunk + b * 32 + lane;
-        if (e < n) {
+        const int e = warp * wchunk + b * 32 + lane;
+        if (e < nloc) {
           const uint32_t dg = (key[b] >> shift) & 0xffu;
-          int dst = (int)hist[warp * 256 + dg] + (int)rank[b];
-          if (last) dst = sw(dst, mask);
-          kout[dst] = key[b];
-          vout[dst] = val[b];
+          const int g = (int)S.dtot[dg] + (int)hist[warp * 256 + dg] + (int)rank_in[b];
+          const int q = CS > 1 ? g / chunk : 0;
+          int li = g - q * chunk;
+          if (last) li = sw(li, mask);
+          Cl<CS>::at(kout, q)[li] = key[b];
+          Cl<CS>::at(vout, q)[li] = val[b];
         }
       }
     }
-    __syncthreads();
+    Cl<CS>::sync();
     uint32_t* t;
     t = kin; kin = kout; kout = t;
     t = vin; vin = vout; vout = t;
@@ -170,16 +251,16 @@ __device__ int block_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32
   return (kin == kA) ? 0 : 1;
 }
 
-template <int NT>
-constexpr int min_blocks() { return NT <= 128 ? 8 : (NT <= 256 ? 2 : 1); }
+template <int NT, int CS>
+constexpr int min_blocks() { return CS > 1 ? 1 : (NT <= 128 ? 6 : (NT <= 256 ? 2 : 1)); }
 
-template <int NT, int CAP, int CT>
-__global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaunch L) {
-  constexpr int NW = NT / 32;
+template <int NT, int CAP, int CT, int CS>
+__global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(OnchipLaunch L) {
   constexpr int IPT = CAP / NT;
   static_assert(IPT * NT == CAP && IPT <= 32 && (IPT & (IPT - 1)) == 0, "bad tile");
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Smem<NT> S;
+  __shared__ Xchg X;
   uint32_t* kA = (uint32_t*)dyn;
   uint32_t* vA = kA + CAP;
   uint32_t* kB = vA + CAP;
@@ -188,35 +269,41 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
   float* ex2 = ex1 + CAP;
   uint16_t* hist = (uint16_t*)(ex2 + CAP);
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int rank = Cl<CS>::rank();
   const ParamsDev& P = L.prm;
 
   for (;;) {
-    if (tid == 0) S.halo = atomicAdd(L.queue, 1);
-    __syncthreads();
-    const int hq = S.halo;
+    if (rank == 0 && tid == 0) X.halo = atomicAdd(L.queue, 1);
+    Cl<CS>::sync();
+    const int hq = *Cl<CS>::at(&X.halo, 0);
+    Cl<CS>::sync();
     if (hq >= L.n_halos) break;
     const HaloDev H = L.halos[hq];
     const int n_cand = (int)H.count;
+    const int chunk = n_cand > 0 ? (n_cand + CS - 1) / CS : 1;
+    if (chunk > CAP) {    // the scheduler never does this; report, do not overrun
+      if (tid == 0 && rank == 0) atomicOr(L.out.err, ERR_CAPACITY);
+      continue;
+    }
+    const int lo = rank * chunk;
+    const int nloc = max(0, min(n_cand - lo, chunk));
     if (tid == 0) {
       S.or_bits = 0u; S.and_bits = 0xffffffffu;
       S.max_m = 0u; S.max_mr = 0u; S.max_mv = 0u;
       S.n_member = 0;
-      S.mv[0] = S.mv[1] = S.mv[2] = 0;
+      S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
+      S.acc_n = 0; S.acc_band = 0;
     }
     __syncthreads();
-    if (n_cand > CAP) {   // the scheduler never does this; report, do not overrun
-      if (tid == 0) atomicOr(L.out.err, ERR_CAPACITY);
-      __syncthreads();
-      continue;
-    }
 
     // ---- gather: key = radius bits of members, candidate position as value ----
     {
       uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u;
       int nmem = 0;
-      for (int i = tid; i < n_cand; i += NT) {
-        const long long slot = H.offset + i;
+      for (int i = tid; i < nloc; i += NT) {
+        const int j = lo + i;
+        const long long slot = H.offset + j;
         long long pi = slot;
         bool ok = true;
         if (L.out.member_idx) {
@@ -236,9 +323,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
             const float m = load_mass<CT>(L.p, pi);
             float v[3];
             load_velocity<CT>(L.p, pi, v);
-            const float mr = m * rinv_of(r, P.r_soft_f);
             mxm = max(mxm, __float_as_uint(fabsf(m)));
-            mxr = max(mxr, __float_as_uint(fabsf(mr)));
+            mxr = max(mxr, __float_as_uint(fabsf(m * rinv_of(r, P.r_soft_f))));
 #pragma unroll
             for (int k = 0; k < 3; ++k) mxv = max(mxv, __float_as_uint(fabsf(__fmul_rn(m, v[k]))));
             ++nmem;
@@ -246,7 +332,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
         }
         if (key == KEY_NONMEMBER && L.out.removed_iter) L.out.removed_iter[slot] = -1;
         kA[i] = key;
-        vA[i] = (uint32_t)i;
+        vA[i] = (uint32_t)j;
         orb |= key;
         andb &= key;
       }
@@ -266,16 +352,37 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
       }
     }
     __syncthreads();
-    const int n_mem = S.n_member;
+    if constexpr (CS > 1) {
+      if (tid == 0) {
+        X.g_or = S.or_bits; X.g_and = S.and_bits; X.g_mxm = S.max_m; X.g_mxr = S.max_mr; X.g_mxv = S.max_mv;
+        X.g_nmem = S.n_member;
+      }
+      Cl<CS>::sync();
+      if (tid == 0) {
+        uint32_t o = 0u, a = 0xffffffffu, m1 = 0u, m2 = 0u, m3 = 0u;
+        int nm = 0;
+        for (int r = 0; r < CS; ++r) {
+          const Xchg* Y = Cl<CS>::at(&X, r);
+          o |= Y->g_or; a &= Y->g_and;
+          m1 = max(m1, Y->g_mxm); m2 = max(m2, Y->g_mxr); m3 = max(m3, Y->g_mxv);
+          nm += Y->g_nmem;
+        }
+        S.or_bits = o; S.and_bits = a; S.max_m = m1; S.max_mr = m2; S.max_mv = m3; S.n_member = nm;
+      }
+      __syncthreads();
+    }
+    const int n_mem = S.n_member;                        // members of the halo
+    const int nmem_loc = max(0, min(n_mem - lo, nloc));  // held by this CTA after the sort
     int ipt = 1;
-    while (ipt * NT < n_mem) ipt <<= 1;
+    while (ipt * NT < chunk) ipt <<= 1;
     const int mask = ipt - 1;
     const int s_m = fix_scale(float_exponent_of_bits(S.max_m), n_mem);
     const int s_r = fix_scale(float_exponent_of_bits(S.max_mr), n_mem);
     const int s_v = fix_scale(float_exponent_of_bits(S.max_mv), n_mem);
 
     // ---- radial sort (once) ----
-    const int which = block_radix_sort<NT, IPT>(kA, vA, kB, vB, hist, S.dtot, n_cand, S.or_bits ^ S.and_bits, mask);
+    const int which = cluster_radix_sort<NT, IPT, CS>(kA, vA, kB, vB, hist, S, X, nloc, chunk,
+                                                      S.or_bits ^ S.and_bits, mask, rank);
     float* rr = (float*)(which ? kB : kA);         // radius, sorted, swizzled
     uint32_t* jj = which ? vB : vA;                // candidate position
     float* mm = (float*)(which ? kA : kB);         // mass; sign bit = removed
@@ -286,7 +393,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
     // ---- fill: sorted SoA and the exact sum m v of the members ----
     {
       long long smv[3] = {0, 0, 0};
-      for (int p = tid; p < n_mem; p += NT) {
+      for (int p = tid; p < nmem_loc; p += NT) {
         const int q = sw(p, mask);
         const int j = (int)jj[q];
         const long long slot = H.offset + j;
@@ -306,62 +413,75 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const long long t = warp_sum(smv[k]);
-        if (lane == 0) atomicAdd((unsigned long long*)&S.mv[k], (unsigned long long)t);
+        if (lane == 0 && t != 0) atomicAdd((unsigned long long*)&S.acc[k], (unsigned long long)t);
       }
     }
     __syncthreads();
+    if constexpr (CS > 1) {
+      if (tid == 0) { X.mv[0] = S.acc[0]; X.mv[1] = S.acc[1]; X.mv[2] = S.acc[2]; }
+      Cl<CS>::sync();
+      if (tid < 3) {
+        long long t = 0;
+        for (int r = 0; r < CS; ++r) t += Cl<CS>::at(&X.mv[0], r)[tid];
+        S.mv[tid] = t;
+      }
+    } else {
+      if (tid < 3) S.mv[tid] = S.acc[tid];
+    }
+    __syncthreads();
+
+    // per-thread exact sums of m, m/r and the alive count over its run
+    const int p0 = tid * ipt;
+    long long tm_own = 0, tr_own = 0, tc_own = 0;
+    for (int k = 0; k < ipt; ++k) {
+      const int p = p0 + k;
+      if (p < nmem_loc) {
+        const int q = sw(p, mask);
+        const float m = mm[q];
+        tm_own += fix_from_float(m, s_m);
+        tr_own += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
+        tc_own += 1;
+      }
+    }
 
     // ---- iterate (Appendix A) ----
     int n_iter = 0, status = 0;
     long long part_iter = 0, n_band = 0;
     int n_alive = n_mem;
     bool converged = false;
-    const int p0 = tid * ipt;
     while (n_alive > 0 && n_iter < P.max_iter) {
       ++n_iter;
       part_iter += n_alive;
-      // pass 1: per-thread exact sums of m and m/r over alive particles
-      long long tm = 0, tr = 0, tc = 0;
-      for (int k = 0; k < ipt; ++k) {
-        const int p = p0 + k;
-        if (p < n_mem) {
-          const int q = sw(p, mask);
-          const float m = mm[q];
-          if (!signbit(m)) {
-            tm += fix_from_float(m, s_m);
-            tr += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
-          }
-        }
-      }
-      long long M_tot, T_tot, C_tot;
-      block_exclusive_scan3<NT>(tm, tr, tc, S, M_tot, T_tot, C_tot);
+      long long tm = tm_own, tr = tr_own, tc = tc_own;
+      block_exclusive_scan3<NT>(tm, tr, tc, S);
+      cluster_scan_totals<NT, CS>(S, X, rank);
       if (tid == 0) {
         // v_bulk = sum m v / sum m of the current set, from the exact sums
-        const float mt = float_from_fix(M_tot, s_m);
+        const float mt = float_from_fix(S.c_tot[0], s_m);
         S.vb[0] = float_from_fix(S.mv[0], s_v) / mt;
         S.vb[1] = float_from_fix(S.mv[1], s_v) / mt;
         S.vb[2] = float_from_fix(S.mv[2], s_v) / mt;
-        S.rem[0] = S.rem[1] = S.rem[2] = S.rem[3] = 0;
-        S.removed = 0;
-        S.band = 0;
+        S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
+        S.acc_n = 0;
+        S.acc_band = 0;
       }
       __syncthreads();
+      tm += S.c_pre[0];
+      tr += S.c_pre[1];
+      const long long T_tot = S.c_tot[1];
       const float vb0 = S.vb[0], vb1 = S.vb[1], vb2 = S.vb[2];
-      // pass 2: phi, escape test, removal
-      long long rm = 0, rv0 = 0, rv1 = 0, rv2 = 0;
+      long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
       for (int k = 0; k < ipt; ++k) {
         const int p = p0 + k;
-        if (p < n_mem) {
+        if (p < nmem_loc) {
           const int q = sw(p, mask);
           const float m = mm[q];
           if (!signbit(m)) {
             const float ri = rinv_of(rr[q], P.r_soft_f);
             const long long mfix = fix_from_float(m, s_m);
             const long long rfix = fix_from_float(m * ri, s_r);
-            const float inner = float_from_fix(tm, s_m) * ri;
-            const float outer = float_from_fix(T_tot - tr, s_r);
-            const float phi = -P.Gf * (inner + outer);
+            const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
             const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
             const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
             const float two_phi = -2.0f * phi;
@@ -375,6 +495,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
               float v[3];
               load_velocity<CT>(L.p, pi, v);
               rm += mfix;
+              rq += rfix;
               rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
               rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
               rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);
@@ -385,30 +506,53 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
           }
         }
       }
+      tm_own -= rm;
+      tr_own -= rq;
+      tc_own -= nrem;
       nrem = __reduce_add_sync(FULL_MASK, nrem);
       nband = __reduce_add_sync(FULL_MASK, nband);
-      if (__any_sync(FULL_MASK, rm != 0 || rv0 != 0 || rv1 != 0 || rv2 != 0)) {
+      if (nrem) {
         rm = warp_sum(rm); rv0 = warp_sum(rv0); rv1 = warp_sum(rv1); rv2 = warp_sum(rv2);
         if (lane == 0) {
-          atomicAdd((unsigned long long*)&S.rem[0], (unsigned long long)rm);
-          atomicAdd((unsigned long long*)&S.rem[1], (unsigned long long)rv0);
-          atomicAdd((unsigned long long*)&S.rem[2], (unsigned long long)rv1);
-          atomicAdd((unsigned long long*)&S.rem[3], (unsigned long long)rv2);
+          atomicAdd((unsigned long long*)&S.acc[0], (unsigned long long)rm);
+          atomicAdd((unsigned long long*)&S.acc[1], (unsigned long long)rv0);
+          atomicAdd((unsigned long long*)&S.acc[2], (unsigned long long)rv1);
+          atomicAdd((unsigned long long*)&S.acc[3], (unsigned long long)rv2);
         }
       }
       if (lane == 0 && (nrem | nband)) {
-        atomicAdd(&S.removed, nrem);
-        atomicAdd(&S.band, nband);
+        atomicAdd(&S.acc_n, nrem);
+        atomicAdd(&S.acc_band, nband);
       }
       __syncthreads();
-      const int removed = S.removed;
-      n_band += S.band;
-      if (tid == 0) {
-        S.mv[0] -= S.rem[1];
-        S.mv[1] -= S.rem[2];
-        S.mv[2] -= S.rem[3];
+      if constexpr (CS > 1) {
+        if (tid == 0) {
+          X.rem[0] = S.acc[0]; X.rem[1] = S.acc[1]; X.rem[2] = S.acc[2]; X.rem[3] = S.acc[3];
+          X.rem_n = S.acc_n; X.rem_band = S.acc_band;
+        }
+        Cl<CS>::sync();
+        if (tid == 0) {
+          long long a1 = 0, a2 = 0, a3 = 0;
+          int nr = 0, nbd = 0;
+          for (int r = 0; r < CS; ++r) {
+            const Xchg* Y = Cl<CS>::at(&X, r);
+            a1 += Y->rem[1]; a2 += Y->rem[2]; a3 += Y->rem[3];
+            nr += Y->rem_n; nbd += Y->rem_band;
+          }
+          S.mv[0] -= a1; S.mv[1] -= a2; S.mv[2] -= a3;
+          S.c_removed = nr;
+          S.c_band = nbd;
+        }
+      } else {
+        if (tid == 0) {
+          S.mv[0] -= S.acc[1]; S.mv[1] -= S.acc[2]; S.mv[2] -= S.acc[3];
+          S.c_removed = S.acc_n;
+          S.c_band = S.acc_band;
+        }
       }
       __syncthreads();
+      const int removed = S.c_removed;
+      n_band += S.c_band;
       n_alive -= removed;
       if (removed == 0) { converged = true; break; }
     }
@@ -419,60 +563,64 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
     float* rc = wx;                       // reuse: w is no longer needed
     long long* mc = (long long*)ex1;      // ex1 and ex2 are contiguous
     {
-      long long tm = 0, tr = 0, tc = 0;
+      long long tm = tm_own, tr = tr_own, tc = tc_own;
+      block_exclusive_scan3<NT>(tm, tr, tc, S);
+      cluster_scan_totals<NT, CS>(S, X, rank);
+      const long long C_pre = S.c_pre[2];
+      const long long C_loc = S.tot[2];
+      const long long T_tot = S.c_tot[1];
+      const long long nb = S.c_tot[2];
+      tm += S.c_pre[0];
+      tr += S.c_pre[1];
+      long long tl = tc;                  // local rank of the thread's first bound particle
       for (int k = 0; k < ipt; ++k) {
         const int p = p0 + k;
-        if (p < n_mem) {
-          const int q = sw(p, mask);
-          const float m = mm[q];
-          if (!signbit(m)) {
-            tm += fix_from_float(m, s_m);
-            tr += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
-            tc += 1;
-          }
-        }
-      }
-      long long M_tot, T_tot, C_tot;
-      block_exclusive_scan3<NT>(tm, tr, tc, S, M_tot, T_tot, C_tot);
-      for (int k = 0; k < ipt; ++k) {
-        const int p = p0 + k;
-        if (p < n_mem) {
+        if (p < nmem_loc) {
           const int q = sw(p, mask);
           const float m = mm[q];
           if (!signbit(m)) {
             const float r = rr[q];
             const float ri = rinv_of(r, P.r_soft_f);
             const long long mfix = fix_from_float(m, s_m);
-            const float inner = float_from_fix(tm, s_m) * ri;
-            const float outer = float_from_fix(T_tot - tr, s_r);
-            const float phi = -P.Gf * (inner + outer);
+            const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
             const int j = (int)jj[q];
             const long long slot = H.offset + j;
             const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-            const long long dst = H.offset + tc;
+            const long long dst = H.offset + C_pre + tl;
             L.out.bound_idx[dst] = pi;
             if (L.out.phi) ((float*)L.out.phi)[dst] = phi;
             if (L.out.removed_iter) L.out.removed_iter[slot] = 0;
-            const int kq = sw((int)tc, mask);
+            const int kq = sw((int)tl, mask);
             rc[kq] = r;
             mc[kq] = tm + mfix;
             tm += mfix;
             tr += fix_from_float(m * ri, s_r);
-            tc += 1;
+            tl += 1;
           }
         }
       }
       if (tid == 0) S.k_first = 0x7fffffff;
       __syncthreads();
+      float r_after = __int_as_float(0x7f800000);   // +inf: radius of the next bound particle
+      if constexpr (CS > 1) {
+        if (tid == 0) {
+          X.nb_loc = (int)C_loc;
+          X.first_r = C_loc > 0 ? rc[sw(0, mask)] : 0.0f;
+        }
+        Cl<CS>::sync();
+        for (int r2 = rank + 1; r2 < CS; ++r2) {
+          const Xchg* Y = Cl<CS>::at(&X, r2);
+          if (Y->nb_loc > 0) { r_after = Y->first_r; break; }
+        }
+      }
       // virial: first k with M_k < delta_rho 4pi/3 r_{k+1}^3 (r_{N+1} = inf)
-      const int nb = (int)C_tot;
       int kf = 0x7fffffff;
       for (int k = 0; k < ipt; ++k) {
         const int kk = p0 + k;
-        if (kk < nb) {
+        if (kk < C_loc) {
+          const float rn = kk + 1 < C_loc ? rc[sw(kk + 1, mask)] : r_after;
           bool cross = true;
-          if (kk + 1 < nb) {
-            const float rn = rc[sw(kk + 1, mask)];
+          if (!isinf(rn)) {
             const long long mk = mc[sw(kk, mask)];
             const float lhs = float_from_fix(mk, s_m);
             const float rhs = P.crit_f * rn * rn * rn;
@@ -483,13 +631,26 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
               cross = double_from_fix(mk, s_m) < P.crit * rd * rd * rd;
             }
           }
-          if (cross) { kf = kk; break; }
+          if (cross) { kf = (int)(C_pre + kk); break; }
         }
       }
-      kf = __reduce_min_sync(FULL_MASK, (unsigned)kf);
+      kf = (int)__reduce_min_sync(FULL_MASK, (unsigned)kf);
       if (lane == 0 && kf != 0x7fffffff) atomicMin(&S.k_first, kf);
       __syncthreads();
-      if (tid == 0) {
+      if constexpr (CS > 1) {
+        if (tid == 0) X.kf = S.k_first;
+        Cl<CS>::sync();
+        if (tid == 0) {
+          int k = 0x7fffffff;
+          for (int r2 = 0; r2 < CS; ++r2) k = min(k, Cl<CS>::at(&X, r2)->kf);
+          S.k_first = k;
+        }
+        __syncthreads();
+      }
+      // the CTA holding the crossing particle writes the record
+      const int k = S.k_first;
+      const bool owner = nb > 0 ? (k >= C_pre && k < C_pre + C_loc) : rank == 0;
+      if (tid == 0 && owner) {
         ahf_result R;
         R.n_bound = nb;
         R.n_member = n_mem;
@@ -500,9 +661,9 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
         R.m_vir = 0.0;
         R.r_vir = 0.0;
         if (nb > 0) {
-          const int k = S.k_first;
-          const double mk = double_from_fix(mc[sw(k, mask)], s_m);
-          const double rk = (double)rc[sw(k, mask)];
+          const int kl = (int)(k - C_pre);
+          const double mk = double_from_fix(mc[sw(kl, mask)], s_m);
+          const double rk = (double)rc[sw(kl, mask)];
           if (k == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
           if (mk < P.crit * rk * rk * rk) {
             status |= AHF_HALO_RVIR_NONE;
@@ -511,7 +672,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
             R.m_vir = mk;
             R.r_vir = cbrt(mk / P.crit);
           }
-          const double mt = double_from_fix(M_tot, s_m);
+          const double mt = double_from_fix(S.c_tot[0], s_m);
           for (int c = 0; c < 3; ++c) R.vbulk[c] = double_from_fix(S.mv[c], s_v) / mt;
         } else {
           R.vbulk[0] = R.vbulk[1] = R.vbulk[2] = 0.0;
@@ -520,56 +681,115 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) onchip_kernel(OnchipLaun
         L.out.res[H.index] = R;
       }
     }
-    __syncthreads();
+    Cl<CS>::sync();
   }
 }
 
-// variant table: (threads, capacity)
 template <int NT, int CAP>
 constexpr size_t dyn_bytes() {
   return (size_t)CAP * 24 + (size_t)(NT / 32) * 256 * 2;
 }
 
-template <int NT, int CAP, int CT>
+template <int CS>
+void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+
+template <int NT, int CAP, int CT, int CS>
 cudaError_t launch_variant(const OnchipLaunch& L, int grid, cudaStream_t s) {
-  auto k = onchip_kernel<NT, CAP, CT>;
+  auto k = unbind_kernel<NT, CAP, CT, CS>;
   constexpr size_t smem = dyn_bytes<NT, CAP>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, smem, s>>>(L);
-  return cudaGetLastError();
+  if constexpr (CS == 1) {
+    k<<<grid, NT, smem, s>>>(L);
+    return cudaGetLastError();
+  } else {
+    if (CS > 8) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cluster_config<CS>(cfg, attr);
+    return cudaLaunchKernelEx(&cfg, k, L);
+  }
 }
 
-template <int NT, int CAP>
+// CTAs of the variant that can be resident at once (whole clusters only).
+template <int NT, int CAP, int CS>
 int max_grid_variant(int device) {
-  int per_sm = 0, sms = 0;
+  auto k = unbind_kernel<NT, CAP, AHF_COORD_F32_REL, CS>;
   constexpr size_t smem = dyn_bytes<NT, CAP>();
-  cudaFuncSetAttribute(onchip_kernel<NT, CAP, AHF_COORD_F32_REL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onchip_kernel<NT, CAP, AHF_COORD_F32_REL>, NT,
-                                                    smem) != cudaSuccess)
-    per_sm = 1;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  return (per_sm > 0 ? per_sm : 1) * sms;
+  if constexpr (CS == 1) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    return per_sm * sms;
+  } else {
+    if (CS > 8) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CS * (sms / CS)), 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    cluster_config<CS>(cfg, attr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      clusters = 0;
+    }
+    return clusters * CS;
+  }
 }
 
 }  // namespace
 
-// Variants: 0 = 128 threads / 1024 slots, 1 = 256 / 4096, 2 = 512 / 8192.
+// Variants: 0 = 1 CTA x 128 threads / 1024 slots, 1 = 1 x 256 / 4096,
+// 2 = 1 x 512 / 8192, 3/4/5 = clusters of 4/8/16 CTAs x 512 / 8192 slots.
+int onchip_cluster_size(int variant) {
+  switch (variant) {
+    case 3: return 4;
+    case 4: return 8;
+    case 5: return 16;
+    default: return 1;
+  }
+}
+
 int onchip_capacity(int variant) {
   switch (variant) {
     case 0: return 1024;
     case 1: return 4096;
     case 2: return 8192;
+    case 3: return 4 * 8192;
+    case 4: return 8 * 8192;
+    case 5: return 16 * 8192;
     default: return 0;
   }
 }
 
 int onchip_max_grid(int variant, int device) {
   switch (variant) {
-    case 0: return max_grid_variant<128, 1024>(device);
-    case 1: return max_grid_variant<256, 4096>(device);
-    case 2: return max_grid_variant<512, 8192>(device);
+    case 0: return max_grid_variant<128, 1024, 1>(device);
+    case 1: return max_grid_variant<256, 4096, 1>(device);
+    case 2: return max_grid_variant<512, 8192, 1>(device);
+    case 3: return max_grid_variant<512, 8192, 4>(device);
+    case 4: return max_grid_variant<512, 8192, 8>(device);
+    case 5: return max_grid_variant<512, 8192, 16>(device);
     default: return 0;
   }
 }
@@ -577,12 +797,18 @@ int onchip_max_grid(int variant, int device) {
 cudaError_t launch_onchip(const OnchipLaunch& L, int variant, int grid, cudaStream_t s) {
   const bool f64 = L.p.coord_type == AHF_COORD_F64;
   switch (variant) {
-    case 0: return f64 ? launch_variant<128, 1024, AHF_COORD_F64>(L, grid, s)
-                       : launch_variant<128, 1024, AHF_COORD_F32_REL>(L, grid, s);
-    case 1: return f64 ? launch_variant<256, 4096, AHF_COORD_F64>(L, grid, s)
-                       : launch_variant<256, 4096, AHF_COORD_F32_REL>(L, grid, s);
-    case 2: return f64 ? launch_variant<512, 8192, AHF_COORD_F64>(L, grid, s)
-                       : launch_variant<512, 8192, AHF_COORD_F32_REL>(L, grid, s);
+    case 0: return f64 ? launch_variant<128, 1024, AHF_COORD_F64, 1>(L, grid, s)
+                       : launch_variant<128, 1024, AHF_COORD_F32_REL, 1>(L, grid, s);
+    case 1: return f64 ? launch_variant<256, 4096, AHF_COORD_F64, 1>(L, grid, s)
+                       : launch_variant<256, 4096, AHF_COORD_F32_REL, 1>(L, grid, s);
+    case 2: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 1>(L, grid, s)
+                       : launch_variant<512, 8192, AHF_COORD_F32_REL, 1>(L, grid, s);
+    case 3: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 4>(L, grid, s)
+                       : launch_variant<512, 8192, AHF_COORD_F32_REL, 4>(L, grid, s);
+    case 4: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 8>(L, grid, s)
+                       : launch_variant<512, 8192, AHF_COORD_F32_REL, 8>(L, grid, s);
+    case 5: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 16>(L, grid, s)
+                       : launch_variant<512, 8192, AHF_COORD_F32_REL, 16>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

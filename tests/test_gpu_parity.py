@@ -55,3 +55,39 @@ def test_multi_cta_class_f64_masses():
                            with_masses=True)
     out, prm, _, _ = run_gpu(pop, ctx=ctx)
     compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+
+
+def test_cluster_variants_all_sizes():
+    # haloes of 9k..125k candidates: clusters of 4, 8 and 16 CTAs
+    rng = np.random.default_rng(31)
+    from tests.test_gpu_paths import _pop_from_arrays
+    pl, vl, cs, rs = [], [], [], []
+    for n in (8193, 9000, 20000, 32768, 32769, 50000, 65536, 65537, 90000, 125000):
+        n_nfw = int(n * 0.87)
+        p, v = synth.sample_nfw(rng, n_nfw, 10.0, 150.0)
+        p2, v2 = synth.sample_uniform_sphere(rng, n - n_nfw, 300.0, 600.0)
+        pl.append(np.concatenate([p, p2])); vl.append(np.concatenate([v, v2]))
+        cs.append([0.0, 0.0, 0.0]); rs.append(300.0)
+    pop = _pop_from_arrays(pl, vl, cs, rs, m0=synth.PARTICLE_MASS)
+    out, prm, ctx, _ = run_gpu(pop)
+    compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+    st = ctx.stats()
+    assert st["phase_halos"][3:6] == [4, 3, 3], st
+
+
+def test_cluster_and_grid_agree_bitwise():
+    # the same haloes through clusters and through the multi-CTA class
+    from paper_0904_3662_gb300 import ahf
+    from tests.gpu_util import require_gpu
+    require_gpu()
+    pop = synth.halo_batch(seed=32, n_halos=8, n_lo=9000, n_hi=60000)
+    a, prm, ctx, _ = run_gpu(pop)
+    ctx2 = ahf.Context(0)
+    ctx2.set_option(ahf.OPT_ONCHIP_MAX, 0)
+    b, _, _, _ = run_gpu(pop, ctx=ctx2)
+    np.testing.assert_array_equal(a["removed_iter"], b["removed_iter"])
+    np.testing.assert_array_equal(a["res"].view(np.uint8), b["res"].view(np.uint8))
+    for h in range(pop.n_halos):
+        lo, nb = int(pop.offset[h]), int(a["res"][h]["n_bound"])
+        np.testing.assert_array_equal(a["bound_idx"][lo:lo + nb], b["bound_idx"][lo:lo + nb])
+        np.testing.assert_array_equal(a["phi"][lo:lo + nb], b["phi"][lo:lo + nb])
