@@ -175,16 +175,15 @@ class ClockSampler:
 
 # ---- algorithmic bytes per phase (see the design notes) --------------------------------
 
-CAPS = [1024, 4096, 8192, 4 * 8192, 8 * 8192, 16 * 8192]
-
-
 def class_of(counts):
     """Size class of each halo as the library's scheduler assigns it:
-    0-2 single-CTA shared-memory variants, 3-5 clusters of 4/8/16 CTAs,
-    6 the multi-CTA class."""
-    cls = np.full(counts.shape[0], 6)
-    for v in range(5, -1, -1):
-        cls = np.where(counts <= CAPS[v], v, cls)
+    0 warp, 1-3 single-CTA shared-memory variants, 4-6 clusters of 4/8/16
+    CTAs, 7 the multi-CTA class."""
+    from paper_0904_3662_gb300 import ahf
+    caps = ahf.VARIANT_CAPS
+    cls = np.full(counts.shape[0], len(caps))
+    for v in range(len(caps) - 1, -1, -1):
+        cls = np.where(counts <= caps[v], v, cls)
     return cls
 
 
@@ -196,17 +195,18 @@ def phase_bytes(pop, res, cls):
     nb = res["n_bound"].astype(np.float64)
     nm = res["n_member"].astype(np.float64)
     pit = res["part_iter"].astype(np.float64)
-    out = np.zeros(10)
-    for v in range(6):
+    nv = 7
+    out = np.zeros(nv + 4)
+    for v in range(nv):
         s = cls == v
         # read the candidates once, write bound list + phi + the record
         out[v] = in_b * cand[s].sum() + 12.0 * nb[s].sum() + 88.0 * s.sum()
-    g = cls == 6
-    out[6] = in_b * cand[g].sum() + 24.0 * nm[g].sum()           # inputs in, sorted SoA out
-    out[7] = 20.0 * pit[g].sum()                                  # (w, m) + r per particle-iteration
-    out[8] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
+    g = cls == nv
+    out[nv] = in_b * cand[g].sum() + 24.0 * nm[g].sum()            # inputs in, sorted SoA out
+    out[nv + 1] = 20.0 * pit[g].sum()                               # (w, m) + r per particle-iteration
+    out[nv + 2] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
     pos_b = 3 * es + (es if pop.m is not None else 0)
-    out[9] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)    # gather bound particles, write rows
+    out[nv + 3] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)  # gather bound particles, write rows
     return out
 
 
@@ -218,10 +218,12 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-_ONCHIP = ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]
-_GRID = ["paper_0904_3662_gb300/csrc/ahf_grid.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]
-PHASE_SOURCES = {0: _ONCHIP, 1: _ONCHIP, 2: _ONCHIP, 3: _ONCHIP, 4: _ONCHIP, 5: _ONCHIP, 6: _GRID, 7: _GRID,
-                 8: _GRID, 9: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", "paper_0904_3662_gb300/csrc/ahf_device.cuh"]}
+_DEV = "paper_0904_3662_gb300/csrc/ahf_device.cuh"
+_ONCHIP = ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", _DEV]
+_GRID = ["paper_0904_3662_gb300/csrc/ahf_grid.cu", _DEV]
+PHASE_SOURCES = {0: ["paper_0904_3662_gb300/csrc/ahf_warp.cu", _DEV], 1: _ONCHIP, 2: _ONCHIP, 3: _ONCHIP,
+                 4: _ONCHIP, 5: _ONCHIP, 6: _ONCHIP, 7: _GRID, 8: _GRID, 9: _GRID,
+                 10: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", _DEV]}
 
 
 def measured_traffic(phase, workload):

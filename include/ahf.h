@@ -217,14 +217,15 @@ int ahf_sync(ahf_ctx *ctx);
 #define AHF_OPT_TIMING     3
 
 /* Per-call statistics of the most recent unbinding or profile call.
- * Phases: 0-2 the single-CTA shared-memory variants (1k / 4k / 8k slots),
- * 3-5 the cluster variants (4 / 8 / 16 CTAs, 32k / 64k / 128k slots), 6 the
- * multi-CTA class's gather + sort + fill, 7 its iterations, 8 its final
- * pass, 9 the profile.  phase_ms is device time between events recorded on the stream
+ * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the
+ * single-CTA shared-memory variants (1k / 4k / 8k slots), 4-6 the cluster
+ * variants (4 / 8 / 16 CTAs, 32k / 64k / 128k slots), 7 the multi-CTA
+ * class's gather + sort + fill, 8 its iterations, 9 its final pass, 10 the
+ * profile.  phase_ms is device time between events recorded on the stream
  * the phase ran on (valid only with AHF_OPT_TIMING on; -1 otherwise);
  * phase_halos / phase_candidates count the haloes and candidate slots each
  * phase covered. */
-#define AHF_N_PHASES 10
+#define AHF_N_PHASES 11
 typedef struct ahf_stats {
   int64_t launches;                    /* kernels launched by the call        */
   int64_t host_syncs;                  /* host synchronisations in the call   */

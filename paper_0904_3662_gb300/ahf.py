@@ -24,9 +24,10 @@ HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE =
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
 OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING = 1, 2, 3
-N_PHASES = 10
-PHASE_NAMES = ("onchip_1k", "onchip_4k", "onchip_8k", "cluster4_32k", "cluster8_64k", "cluster16_128k",
+N_PHASES = 11
+PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster4_32k", "cluster8_64k", "cluster16_128k",
                "grid_gather_sort", "grid_iterate", "grid_finish", "profile")
+VARIANT_CAPS = (512, 1024, 4096, 8192, 4 * 8192, 8 * 8192, 16 * 8192)
 
 HALO_DTYPE = np.dtype([("cx", "<f8"), ("cy", "<f8"), ("cz", "<f8"), ("radius", "<f8"),
                        ("offset", "<i8"), ("count", "<i8")])

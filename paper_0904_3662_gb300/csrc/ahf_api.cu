@@ -66,6 +66,32 @@ struct Bump {
 
 void ahf::set_last_error_static(const char* msg) { g_last_ptr = msg; }
 
+namespace {
+
+// Shared-memory variants in size order: 0 = one warp per halo, 1-3 = one CTA
+// of 128 / 256 / 512 threads, 4-6 = clusters of 4 / 8 / 16 CTAs.  Phases
+// 0..NV-1 time them; then the multi-CTA class's three phases and the profile.
+constexpr int NV = 7;
+constexpr int PH_GRID_SORT = NV, PH_GRID_ITER = NV + 1, PH_GRID_FINISH = NV + 2, PH_PROFILE = NV + 3;
+static_assert(PH_PROFILE + 1 == AHF_N_PHASES, "phase table");
+
+int variant_capacity(int v) { return v == 0 ? warp_capacity() : onchip_capacity(v - 1); }
+
+// Resident CTAs (whole clusters) of a variant on this device; 0 if it cannot run.
+int variant_max_grid(int v, int device) { return v == 0 ? warp_max_grid(device) : onchip_max_grid(v - 1, device); }
+
+// CTAs a launch of n haloes needs (before the residency cap).
+long long variant_grid_for(int v, long long n) {
+  if (v == 0) return (n + warp_halos_per_cta() - 1) / warp_halos_per_cta();
+  return n * onchip_cluster_size(v - 1);
+}
+
+cudaError_t launch_variant(const OnchipLaunch& L, int v, int grid, cudaStream_t s) {
+  return v == 0 ? launch_warp(L, grid, s) : launch_onchip(L, v - 1, grid, s);
+}
+
+}  // namespace
+
 struct ahf_ctx {
   int device = 0;
   int sms = 0;
@@ -96,10 +122,10 @@ struct ahf_ctx {
   ahf_stats stats{};
   bool phase_used[AHF_N_PHASES] = {};
   cudaEvent_t ev0[AHF_N_PHASES] = {}, ev1[AHF_N_PHASES] = {};
-  cudaStream_t side[6] = {};     // one stream per on-chip / cluster variant
+  cudaStream_t side[NV] = {};    // one stream per shared-memory variant
   cudaEvent_t fork = nullptr;
-  cudaEvent_t join[6] = {};
-  int variant_grid[6] = {-1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
+  cudaEvent_t join[NV] = {};
+  int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
 };
 
 namespace {
@@ -177,7 +203,7 @@ int ceil_log2(double x) {
 
 struct Plan {
   std::vector<HaloDev> hd;     // reordered: class 0, 1, 2 (on-chip), then grid class
-  int n_class[7] = {0, 0, 0, 0, 0, 0, 0};   // 0-5 shared-memory variants, 6 multi-CTA
+  int n_class[NV + 1] = {};     // 0..NV-1 shared-memory variants, NV multi-CTA
   long long grid_flat = 0;
   FrameDev frame;
 };
@@ -234,16 +260,16 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   P.frame.box = prm->box;
   // the smallest shared-memory variant that holds the halo and can run on
   // this device, else the multi-CTA class
-  int caps[6];
-  for (int v = 0; v < 6; ++v) {
-    if (c->variant_grid[v] < 0) c->variant_grid[v] = onchip_max_grid(v, c->device);
-    caps[v] = c->variant_grid[v] > 0 ? (int)std::min<int64_t>(onchip_capacity(v), c->onchip_max) : 0;
+  int caps[NV];
+  for (int v = 0; v < NV; ++v) {
+    if (c->variant_grid[v] < 0) c->variant_grid[v] = variant_max_grid(v, c->device);
+    caps[v] = c->variant_grid[v] > 0 ? (int)std::min<int64_t>(variant_capacity(v), c->onchip_max) : 0;
   }
   std::vector<int> cls((size_t)n_halos);
   for (int64_t h = 0; h < n_halos; ++h) {
     const int64_t n = halos[h].count;
-    int k = 6;
-    for (int v = 0; v < 6; ++v)
+    int k = NV;
+    for (int v = 0; v < NV; ++v)
       if (n <= caps[v]) { k = v; break; }
     cls[h] = k;
     P.n_class[k]++;
@@ -280,7 +306,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     d.count = H.count;
     d.index = h;
     d.gbase = 0;
-    if (cls[h] == 6) { d.gbase = gbase; gbase += H.count; }
+    if (cls[h] == NV) { d.gbase = gbase; gbase += H.count; }
   }
   P.grid_flat = gbase;
   return AHF_OK;
@@ -328,8 +354,8 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
   c->stats.launches += 4 * G.sort_passes;
   AHF_CUDA(grid_fill(G, s));
   c->stats.launches += 1;
-  if ((rc = phase_end(c, 6, s))) return rc;
-  if ((rc = phase_begin(c, 7, s, G.n_halos, G.n_flat))) return rc;
+  if ((rc = phase_end(c, PH_GRID_SORT, s))) return rc;
+  if ((rc = phase_begin(c, PH_GRID_ITER, s, G.n_halos, G.n_flat))) return rc;
   for (int it = 1; it <= prm->max_iter; ++it) {
     AHF_CUDA(cudaMemsetAsync(G.any_active, 0, sizeof(int), s));
     AHF_CUDA(grid_iterate(G, it, s));
@@ -340,11 +366,11 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
     c->stats.host_syncs += 1;
     if (c->flag_host[2] == 0) break;
   }
-  if ((rc = phase_end(c, 7, s))) return rc;
-  if ((rc = phase_begin(c, 8, s, G.n_halos, G.n_flat))) return rc;
+  if ((rc = phase_end(c, PH_GRID_ITER, s))) return rc;
+  if ((rc = phase_begin(c, PH_GRID_FINISH, s, G.n_halos, G.n_flat))) return rc;
   AHF_CUDA(grid_finish(G, s));
   c->stats.launches += 5;
-  return phase_end(c, 8, s);
+  return phase_end(c, PH_GRID_FINISH, s);
 }
 
 struct GridTables {
@@ -385,8 +411,8 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
   reset_stats(c);
   int n_onchip = 0;
-  for (int v = 0; v < 6; ++v) n_onchip += P.n_class[v];
-  const int n_grid = P.n_class[6];
+  for (int v = 0; v < NV; ++v) n_onchip += P.n_class[v];
+  const int n_grid = P.n_class[NV];
   if (P.grid_flat >= (1ll << 31)) return fail(AHF_ERR_INVALID, "multi-CTA class above 2^31 candidates");
   GridTables T;
   if (n_grid) build_tiles(P, n_onchip, n_grid, T);
@@ -462,7 +488,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
     G.p = pd; G.frame = P.frame; G.prm = prd; G.out = O;
     G.n_halos = n_grid; G.n_flat = (long long)nf; G.n_tiles = n_tiles;
-    if ((rc = phase_begin(c, 6, s, n_grid, (long long)nf))) return rc;
+    if ((rc = phase_begin(c, PH_GRID_SORT, s, n_grid, (long long)nf))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
   }
@@ -471,11 +497,11 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   // with the multi-CTA class on the caller's stream
   AHF_CUDA(cudaEventRecord(c->fork, s));
   int first = 0;
-  int used_side[6] = {0, 0, 0, 0, 0, 0};
-  // clusters (the largest haloes) first, then the single-CTA variants
-  int first_of[6];
-  for (int v = 0, f = 0; v < 6; ++v) { first_of[v] = f; f += P.n_class[v]; }
-  for (int v = 5; v >= 0; --v) {
+  int used_side[NV] = {};
+  // clusters (the largest haloes) first, then the single-CTA and warp variants
+  int first_of[NV];
+  for (int v = 0, f = 0; v < NV; ++v) { first_of[v] = f; f += P.n_class[v]; }
+  for (int v = NV - 1; v >= 0; --v) {
     const int n = P.n_class[v];
     if (n == 0) continue;
     OnchipLaunch L;
@@ -483,11 +509,10 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     L.halos = hd + first_of[v]; L.n_halos = n; L.queue = queues + v;
     long long cands = 0;
     for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first_of[v] + k].count;
-    const int cs = onchip_cluster_size(v);
-    const int grid = (int)std::min<long long>((long long)n * cs, c->variant_grid[v]);
+    const int grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
     AHF_CUDA(cudaStreamWaitEvent(c->side[v], c->fork, 0));
     if ((rc = phase_begin(c, v, c->side[v], n, cands))) return rc;
-    AHF_CUDA(launch_onchip(L, v, grid, c->side[v]));
+    AHF_CUDA(launch_variant(L, v, grid, c->side[v]));
     c->stats.launches += 1;
     if ((rc = phase_end(c, v, c->side[v]))) return rc;
     AHF_CUDA(cudaEventRecord(c->join[v], c->side[v]));
@@ -496,7 +521,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if (n_grid) {
     if ((rc = run_grid(c, G, prm, s))) return rc;
   }
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < NV; ++k)
     if (used_side[k]) AHF_CUDA(cudaStreamWaitEvent(s, c->join[k], 0));
   return end_call(c, s);
 }
@@ -586,14 +611,14 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   L.r_min_frac = r_min_frac;
   L.prof = prof;
   L.n_chunks = n_chunks;
-  c->phase_used[9] = false;
-  c->stats.phase_ms[9] = -1.0;
-  c->stats.phase_halos[9] = 0;
-  c->stats.phase_candidates[9] = 0;
-  if ((rc = phase_begin(c, 9, s, n_halos, (long long)n_chunks * PROFILE_CHUNK))) return rc;
+  c->phase_used[PH_PROFILE] = false;
+  c->stats.phase_ms[PH_PROFILE] = -1.0;
+  c->stats.phase_halos[PH_PROFILE] = 0;
+  c->stats.phase_candidates[PH_PROFILE] = 0;
+  if ((rc = phase_begin(c, PH_PROFILE, s, n_halos, (long long)n_chunks * PROFILE_CHUNK))) return rc;
   AHF_CUDA(launch_profile(L, hc0, s));
   c->stats.launches += (n_chunks > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0);
-  if ((rc = phase_end(c, 9, s))) return rc;
+  if ((rc = phase_end(c, PH_PROFILE, s))) return rc;
   return end_call(c, s);
 }
 
@@ -697,7 +722,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
       AHF_CUDA(cudaStreamSynchronize(s));
       continue;
     }
-    if ((rc = phase_begin(c, 6, s, 1, d.count))) return rc;
+    if ((rc = phase_begin(c, PH_GRID_SORT, s, 1, d.count))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
     if ((rc = run_grid(c, G, prm, s))) return rc;
@@ -807,7 +832,7 @@ int ahf_create(ahf_ctx** ctx, int device) {
       break;
     }
     if (cudaMallocHost(&c->flag_host, 16 * sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "pinned flags"); break; }
-    for (int k = 0; k < 6 && rc == AHF_OK; ++k) {
+    for (int k = 0; k < NV && rc == AHF_OK; ++k) {
       if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) != cudaSuccess)
         rc = fail(AHF_ERR_CUDA, "side stream");
@@ -845,7 +870,7 @@ int ahf_destroy(ahf_ctx* c) {
   if (c->last) cudaEventDestroy(c->last);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->flag_host) cudaFreeHost(c->flag_host);
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     if (c->side[k]) cudaStreamDestroy(c->side[k]);
     if (c->join[k]) cudaEventDestroy(c->join[k]);
   }
@@ -862,7 +887,7 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
   std::lock_guard<std::mutex> g(c->mu);
   switch (option) {
     case AHF_OPT_ONCHIP_MAX:
-      if (value < 0 || value > onchip_capacity(5)) return fail(AHF_ERR_INVALID, "onchip max out of range");
+      if (value < 0 || value > variant_capacity(NV - 1)) return fail(AHF_ERR_INVALID, "onchip max out of range");
       c->onchip_max = value;
       return AHF_OK;
     case AHF_OPT_WAIT_LIMIT:

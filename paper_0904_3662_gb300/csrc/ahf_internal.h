@@ -100,7 +100,13 @@ struct OnchipLaunch {
   int *queue;            // work counter (zeroed by the launcher)
 };
 
-// Shared-memory variants 0..5: candidate capacity, CTAs per cluster.
+// Warp class: one warp per halo of at most warp_capacity() candidates.
+int warp_capacity();
+int warp_max_grid(int device);
+int warp_halos_per_cta();
+cudaError_t launch_warp(const OnchipLaunch &L, int grid, cudaStream_t s);
+
+// Shared-memory CTA / cluster variants 0..5: candidate capacity, CTAs per cluster.
 int onchip_capacity(int variant);
 int onchip_cluster_size(int variant);
 // Launch the on-chip class (variant chosen by the scheduler).

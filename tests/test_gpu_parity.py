@@ -72,7 +72,7 @@ def test_cluster_variants_all_sizes():
     out, prm, ctx, _ = run_gpu(pop)
     compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
     st = ctx.stats()
-    assert st["phase_halos"][3:6] == [4, 3, 3], st
+    assert st["phase_halos"][4:7] == [4, 3, 3], st
 
 
 def test_cluster_and_grid_agree_bitwise():

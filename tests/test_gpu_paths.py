@@ -64,7 +64,7 @@ def test_edge_cases_small():
     p, _ = synth.sample_uniform_sphere(rng, 700, 5.0, 0.0)
     pl.append(p); vl.append(np.tile([[300.0, -200.0, 50.0]], (700, 1))); cs.append([0, 0, 0]); rs.append(10.0)
     # 7: ragged sizes just around the class boundaries
-    for n in (1023, 1024, 1025, 4095, 4097, 8191, 8192):
+    for n in (31, 32, 33, 511, 512, 513, 1023, 1024, 1025, 4095, 4097, 8191, 8192):
         p, v = synth.sample_nfw(rng, n, 10.0, 60.0)
         pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(120.0)
     pop = _pop_from_arrays(pl, vl, cs, rs, m0=1e9)
