@@ -3,8 +3,8 @@
 
 One step = one pass of the whole stage over one synthetic batch: gather +
 recentre + radial sort + iterated potential / escape test / removal +
-virial radius (ahf_unbind_batch) and the log-radial profile
-(ahf_profile_batch).  Metric: particle-iterations per second, where a
+virial radius and the log-radial profile, in one ahf_unbind_profile_batch
+call.  Metric: particle-iterations per second, where a
 particle-iteration is one member tested in one unbinding iteration (the
 count every implementation of the method performs; the library reports it
 per halo).
@@ -321,9 +321,8 @@ def run_ahf(args):
     ctx.set_option(ahf.OPT_TIMING, 1)
 
     def step():
-        ctx.unbind_batch(parts, hal, prm, out=out, stream=stream)
-        ctx.profile_batch(parts, hal, prm, out["res"], out["bound_idx"], n_bins=N_BINS, r_min_frac=R_MIN_FRAC,
-                          prof=prof, stream=stream)
+        ctx.unbind_profile_batch(parts, hal, prm, n_bins=N_BINS, r_min_frac=R_MIN_FRAC, out=out, prof=prof,
+                                 stream=stream)
 
     for _ in range(args.warmup):
         flush.zero_()

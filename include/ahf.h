@@ -203,6 +203,19 @@ int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halo
  * device wait gave up.  The device error word is cleared by the call. */
 int ahf_sync(ahf_ctx *ctx);
 
+/* ahf_unbind_batch and ahf_profile_batch in one call: the same arguments
+ * and outputs as the two (prof: device double [n_halos][n_bins][4]).  Haloes
+ * small enough for one warp or one CTA get their profile rows from the
+ * unbinding kernel itself (the bound set is still on chip); the others get
+ * them from the profile kernels.  Rows agree with ahf_profile_batch: counts
+ * exactly, masses to rounding (exact fixed-point sums here, FP64 sums there).
+ * Errors: those of the two calls. */
+int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
+                             int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
+                             ahf_result *out, int64_t *bound_idx, void *phi,
+                             int32_t *removed_iter, int32_t n_bins, double r_min_frac,
+                             double *prof, void *stream);
+
 /* Tuning and diagnostics knobs (values persist in the context).
  *   AHF_OPT_ONCHIP_MAX   largest candidate count handled in shared memory (by one
  *                        CTA or one thread-block cluster); larger haloes take the
@@ -257,7 +270,7 @@ int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
  * work is enqueued.  Only AHF_PREC_MIXED.
  *
  * Scratch: the halo descriptors and work counters live in one fixed array
- * in device memory (about 3.3 MiB) that every GPU loading the library holds
+ * in device memory (about 3.8 MiB) that every GPU loading the library holds
  * until the process exits.  All calls on a device share it and it keeps the
  * last call's contents; each call clears the counters it uses.  Calls whose
  * device work overlaps (different streams with no ordering between them)

@@ -39,7 +39,7 @@ assert HALO_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 88
 # every symbol include/ahf.h declares
 EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_unbind_batch",
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
-           "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static")
+           "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch")
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
 
 
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_unbind_batch_host.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     lib.ahf_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.ahf_unbind_batch_static.argtypes = sig[1:]
+    lib.ahf_unbind_profile_batch.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     if hasattr(lib, "ahf_profile_batch"):
         lib.ahf_profile_batch.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
                                           vp, vp, i32, ctypes.c_double, vp, vp]
@@ -247,6 +248,27 @@ class Context:
                   None if out["phi"] is None else out["phi"].data_ptr(),
                   None if out["removed_iter"] is None else out["removed_iter"].data_ptr(),
                   _stream_ptr(stream)))
+        return out
+
+    def unbind_profile_batch(self, parts: Particles, halos, params: Params, n_bins=32, r_min_frac=0.01,
+                             member_idx=None, out=None, prof=None, with_phi=True, with_removed=True, stream=None):
+        """ahf_unbind_profile_batch: unbinding and profile rows in one call."""
+        import torch
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        n_slots = n_slots_of(halos, parts.n, member_idx)
+        if out is None:
+            out = self.alloc_outputs(len(halos), n_slots, with_phi, with_removed, params.precision)
+        if prof is None:
+            prof = torch.empty((len(halos), n_bins, 4), dtype=torch.float64, device=torch.device("cuda", self.device))
+        pc, prc = parts.c(), params.c()
+        _check(self.lib.ahf_unbind_profile_batch(
+            self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
+            None if member_idx is None else member_idx.data_ptr(), ctypes.byref(prc),
+            out["res"].data_ptr(), out["bound_idx"].data_ptr(),
+            None if out["phi"] is None else out["phi"].data_ptr(),
+            None if out["removed_iter"] is None else out["removed_iter"].data_ptr(),
+            int(n_bins), float(r_min_frac), prof.data_ptr(), _stream_ptr(stream)))
+        out["prof"] = prof
         return out
 
     def unbind_batch_host(self, parts: Particles, halos, params: Params, member_idx=None, out=None,

@@ -195,6 +195,40 @@ int phase_end(ahf_ctx* c, int ph, cudaStream_t s) {
   return AHF_OK;
 }
 
+}  // namespace
+
+void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index, HaloDev& d) {
+  d.c[0] = H.cx; d.c[1] = H.cy; d.c[2] = H.cz;
+  // fixed-point frame of this halo alone (so a halo's result does not depend
+  // on the rest of the batch): its centre, every member and the box stay
+  // below 2^(60-frac)
+  const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
+  double span = std::max(cm + std::fabs(H.radius), box);
+  if (coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
+  int e = 0;
+  while (e < 1100 && std::ldexp(1.0, e) <= span + 1.0) ++e;
+  const int frac = std::max(-200, std::min(200, 60 - e));
+  d.frac = frac;
+  d.boxfix = box > 0.0 ? (long long)std::llround(std::ldexp(box, frac)) : 0;
+  for (int a = 0; a < 3; ++a) d.cfix[a] = (long long)std::llround(std::ldexp(d.c[a], frac));
+  const double R = H.radius;
+  d.R2 = R * R;
+  d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
+  d.R2hi = (float)(d.R2 * (1.0 + 4e-6));
+  d.offset = H.offset;
+  d.count = H.count;
+  d.gbase = 0;
+  d.index = index;
+  bool exact = coord_type != AHF_COORD_F64 && box == 0.0;
+  for (int a = 0; a < 3; ++a) {
+    d.cf[a] = (float)d.c[a];
+    exact = exact && (double)d.cf[a] == d.c[a];
+  }
+  d.fast = exact ? 1 : 0;
+}
+
+namespace {
+
 int ceil_log2(double x) {
   int e = 0;
   while (e < 1100 && std::ldexp(1.0, e) <= x) ++e;
@@ -223,7 +257,8 @@ int validate(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, con
   if (p->reserved != 0) return fail(AHF_ERR_INVALID, "reserved field must be 0");
   if (!p->m && !(p->m0 >= 0.0 && std::isfinite(p->m0))) return fail(AHF_ERR_INVALID, "m0 must be finite and >= 0");
   if (prm->max_iter < 1) return fail(AHF_ERR_INVALID, "max_iter must be >= 1");
-  if (prm->precision != AHF_PREC_MIXED) return fail(AHF_ERR_INVALID, "precision mode %d not available", prm->precision);
+  if (prm->precision != AHF_PREC_MIXED && prm->precision != AHF_PREC_FP64)
+    return fail(AHF_ERR_INVALID, "unknown precision mode %d", prm->precision);
   if (!(prm->G > 0.0) || !std::isfinite(prm->G)) return fail(AHF_ERR_INVALID, "G must be > 0");
   if (!std::isfinite(prm->H)) return fail(AHF_ERR_INVALID, "H must be finite");
   if (!(prm->delta_rho > 0.0) || !std::isfinite(prm->delta_rho)) return fail(AHF_ERR_INVALID, "delta_rho must be > 0");
@@ -269,8 +304,10 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   for (int64_t h = 0; h < n_halos; ++h) {
     const int64_t n = halos[h].count;
     int k = NV;
-    for (int v = 0; v < NV; ++v)
-      if (n <= caps[v]) { k = v; break; }
+    // the all-FP64 mode runs in the multi-CTA class only
+    if (prm->precision == AHF_PREC_MIXED)
+      for (int v = 0; v < NV; ++v)
+        if (n <= caps[v]) { k = v; break; }
     cls[h] = k;
     P.n_class[k]++;
   }
@@ -286,26 +323,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     const int h = order[k];
     const ahf_halo& H = halos[h];
     HaloDev& d = P.hd[k];
-    d.c[0] = H.cx; d.c[1] = H.cy; d.c[2] = H.cz;
-    // fixed-point frame of this halo alone (so a halo's result does not
-    // depend on the rest of the batch): its centre, every member and the
-    // box stay below 2^(60-frac)
-    const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
-    double span = std::max(cm + std::fabs(H.radius), prm->box);
-    if (p->coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
-    int frac = 60 - ceil_log2(span + 1.0);
-    frac = std::max(-200, std::min(200, frac));
-    d.frac = frac;
-    d.boxfix = prm->box > 0.0 ? (long long)std::llround(std::ldexp(prm->box, frac)) : 0;
-    for (int a = 0; a < 3; ++a) d.cfix[a] = (long long)std::llround(std::ldexp(d.c[a], frac));
-    const double R = H.radius;
-    d.R2 = R * R;
-    d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
-    d.R2hi = (float)(d.R2 * (1.0 + 4e-6));
-    d.offset = H.offset;
-    d.count = H.count;
-    d.index = h;
-    d.gbase = 0;
+    fill_halo_dev(H, p->coord_type, prm->box, h, d);
     if (cls[h] == NV) { d.gbase = gbase; gbase += H.count; }
   }
   P.grid_flat = gbase;
@@ -346,10 +364,12 @@ int end_call(ahf_ctx* c, cudaStream_t s) {
 // multi-CTA class; phases 3 (to the end of fill), 4 and 5.
 int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
   int rc;
-  AHF_CUDA(cudaMemcpyAsync(c->flag_host, G.key_or_and, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AHF_CUDA(cudaMemcpyAsync(c->flag_host, G.key_or_and, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   AHF_CUDA(cudaStreamSynchronize(s));
   c->stats.host_syncs += 1;
-  const uint32_t orb = (uint32_t)c->flag_host[0], andb = (uint32_t)c->flag_host[1];
+  unsigned long long orb, andb;
+  std::memcpy(&orb, c->flag_host, 8);
+  std::memcpy(&andb, c->flag_host + 2, 8);
   AHF_CUDA(grid_sort(G, s, orb, andb));
   c->stats.launches += 4 * G.sort_passes;
   AHF_CUDA(grid_fill(G, s));
@@ -361,10 +381,10 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
     AHF_CUDA(grid_iterate(G, it, s));
     c->stats.launches += 4;
     c->stats.grid_iterations += 1;
-    AHF_CUDA(cudaMemcpyAsync(c->flag_host + 2, G.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AHF_CUDA(cudaMemcpyAsync(c->flag_host + 4, G.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     AHF_CUDA(cudaStreamSynchronize(s));
     c->stats.host_syncs += 1;
-    if (c->flag_host[2] == 0) break;
+    if (c->flag_host[4] == 0) break;
   }
   if ((rc = phase_end(c, PH_GRID_ITER, s))) return rc;
   if ((rc = phase_begin(c, PH_GRID_FINISH, s, G.n_halos, G.n_flat))) return rc;
@@ -395,11 +415,24 @@ void build_tiles(const Plan& P, int first, int n, GridTables& T) {
   T.halo_tile0[n] = (int)T.tile_range.size();
 }
 
+int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                 const int64_t* member_idx, const ahf_params* prm, const ahf_result* res, const int64_t* bound_idx,
+                 int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s,
+                 const std::vector<char>* include = nullptr);
+
+// Unbinding of a batch; with prof != NULL also the profile rows.  The warp
+// and single-CTA variants form the rows from the bound set they hold on chip;
+// haloes of the cluster and multi-CTA classes get theirs from the profile
+// kernels afterwards.
 int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                 const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
-                int32_t* removed_iter, cudaStream_t s) {
+                int32_t* removed_iter, cudaStream_t s, int32_t n_bins = 0, double r_min_frac = 0.0,
+                double* prof = nullptr) {
   int rc = validate(p, halos, n_halos, prm, out, bound_idx);
   if (rc) return rc;
+  if (prof && (n_bins < 1 || n_bins > profile_max_bins()))
+    return fail(AHF_ERR_INVALID, "n_bins must be in [1, %d]", profile_max_bins());
+  if (prof && !(r_min_frac > 0.0 && r_min_frac < 1.0)) return fail(AHF_ERR_INVALID, "r_min_frac must be in (0, 1)");
   int64_t n_slots = p->n;
   if (member_idx) {
     n_slots = 0;
@@ -410,6 +443,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Plan P;
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
   reset_stats(c);
+  constexpr int FUSED_MAX = 3;     // variants 0..3 form profile rows themselves
   int n_onchip = 0;
   for (int v = 0; v < NV; ++v) n_onchip += P.n_class[v];
   const int n_grid = P.n_class[NV];
@@ -418,22 +452,27 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if (n_grid) build_tiles(P, n_onchip, n_grid, T);
   const int n_tiles = (int)T.tile_range.size();
   const size_t nf = (size_t)P.grid_flat;
+  const bool fp64 = prm->precision == AHF_PREC_FP64;
 
   // workspace layout (must match the Bump sequence below)
+  double* dfac = nullptr;
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
     int* queues = B.take<int>(16);
-    if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (uint32_t*)(queues + 10); }
+    double* fac = B.take<double>(prof ? (size_t)n_bins : 0);
+    if (G) dfac = fac;
+    if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (unsigned long long*)(queues + 10); }
     if (n_grid) {
+      const size_t es = fp64 ? 8 : 4;
       GridHaloState* st = B.take<GridHaloState>((size_t)n_grid);
-      uint32_t* ka = B.take<uint32_t>(nf);
-      uint32_t* kb = B.take<uint32_t>(nf);
+      char* ka = B.take<char>(nf * es);
+      char* kb = B.take<char>(nf * es);
       uint32_t* va = B.take<uint32_t>(nf);
       uint32_t* vb = B.take<uint32_t>(nf);
-      float4* wm = B.take<float4>(nf);
-      float* r = B.take<float>(nf);
+      char* wm = B.take<char>(nf * 4 * es);
+      char* r = B.take<char>(nf * es);
       long long* mc = B.take<long long>(nf);
-      float* rcp = B.take<float>(nf);
+      char* rcp = B.take<char>(nf * es);
       int2* trg = B.take<int2>((size_t)n_tiles);
       int* th = B.take<int>((size_t)n_tiles);
       int* ht0 = B.take<int>((size_t)n_grid + 1);
@@ -452,7 +491,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
-  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 +
+  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 8 * (size_t)n_bins + 256 : 0) +
                           (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
@@ -472,6 +511,11 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   };
   AHF_CUDA(stage(hd, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos));
   AHF_CUDA(cudaMemsetAsync(queues, 0, 16 * sizeof(int), s));
+  if (prof) {
+    std::vector<double> factor((size_t)n_bins);
+    for (int b = 0; b < n_bins; ++b) factor[(size_t)b] = std::pow(r_min_frac, 1.0 - (double)b / (double)n_bins);
+    AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * (size_t)n_bins));
+  }
 
   OutputsDev O;
   O.res = out; O.bound_idx = (long long*)bound_idx; O.phi = phi; O.removed_iter = removed_iter;
@@ -484,8 +528,9 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     AHF_CUDA(stage(G.tile_halo, T.tile_halo.data(), sizeof(int) * (size_t)n_tiles));
     AHF_CUDA(stage(G.halo_tile0, T.halo_tile0.data(), sizeof(int) * ((size_t)n_grid + 1)));
     AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState) * (size_t)n_grid, s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(uint32_t), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(unsigned long long), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(unsigned long long), s));
+    G.fp64 = fp64 ? 1 : 0;
     G.p = pd; G.frame = P.frame; G.prm = prd; G.out = O;
     G.n_halos = n_grid; G.n_flat = (long long)nf; G.n_tiles = n_tiles;
     if ((rc = phase_begin(c, PH_GRID_SORT, s, n_grid, (long long)nf))) return rc;
@@ -507,6 +552,9 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     OnchipLaunch L;
     L.p = pd; L.frame = P.frame; L.prm = prd; L.out = O;
     L.halos = hd + first_of[v]; L.n_halos = n; L.queue = queues + v;
+    L.rows.prof = (prof && v <= FUSED_MAX) ? prof : nullptr;
+    L.rows.factor = dfac;
+    L.rows.n_bins = n_bins;
     long long cands = 0;
     for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first_of[v] + k].count;
     const int grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
@@ -523,13 +571,29 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   }
   for (int k = 0; k < NV; ++k)
     if (used_side[k]) AHF_CUDA(cudaStreamWaitEvent(s, c->join[k], 0));
-  return end_call(c, s);
+  if ((rc = end_call(c, s))) return rc;
+  if (prof) {
+    // rows of the haloes the fused variants did not cover
+    std::vector<char> rest((size_t)n_halos, 0);
+    bool any = false;
+    int64_t first = 0;
+    for (int v = 0; v <= NV; ++v) {
+      for (int k = 0; k < P.n_class[v]; ++k)
+        if (v > FUSED_MAX) { rest[(size_t)P.hd[(size_t)(first + k)].index] = 1; any = true; }
+      first += P.n_class[v];
+    }
+    if (any) return profile_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, n_bins, r_min_frac, prof, s,
+                                 &rest);
+    // the profile phase then covers the fused rows only
+    c->stats.phase_halos[PH_PROFILE] = 0;
+  }
+  return AHF_OK;
 }
 
 
 int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                  const int64_t* member_idx, const ahf_params* prm, const ahf_result* res, const int64_t* bound_idx,
-                 int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s) {
+                 int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s, const std::vector<char>* include) {
   int rc = validate(p, halos, n_halos, prm, res, bound_idx);
   if (rc) return rc;
   if (n_halos > 0 && !prof) return fail(AHF_ERR_INVALID, "prof must not be NULL");
@@ -551,7 +615,10 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   std::vector<long long> chunk_start;
   for (int64_t h = 0; h < n_halos; ++h) {
     halo_chunk0[(size_t)h] = (int)chunk_halo.size();
-    for (long long o = 0; o < halos[h].count; o += PROFILE_CHUNK) {
+    if (include && !(*include)[(size_t)h]) continue;
+    // a halo with no candidates still needs one chunk to write its zero rows
+    const long long cnt = std::max<long long>(halos[h].count, 1);
+    for (long long o = 0; o < cnt; o += PROFILE_CHUNK) {
       chunk_halo.push_back((int)h);
       chunk_start.push_back(o);
     }
@@ -645,15 +712,16 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>(1);
     int* words = B.take<int>(16);
+    const size_t es = prm->precision == AHF_PREC_FP64 ? 8 : 4;
     GridHaloState* st = B.take<GridHaloState>(1);
-    uint32_t* ka = B.take<uint32_t>(nf);
-    uint32_t* kb = B.take<uint32_t>(nf);
+    char* ka = B.take<char>(nf * es);
+    char* kb = B.take<char>(nf * es);
     uint32_t* va = B.take<uint32_t>(nf);
     uint32_t* vb = B.take<uint32_t>(nf);
-    float4* wm = B.take<float4>(nf);
-    float* r = B.take<float>(nf);
+    char* wm = B.take<char>(nf * 4 * es);
+    char* r = B.take<char>(nf * es);
     long long* mc = B.take<long long>(nf);
-    float* rcp = B.take<float>(nf);
+    char* rcp = B.take<char>(nf * es);
     int2* trg = B.take<int2>((size_t)max_tiles);
     int* th = B.take<int>((size_t)max_tiles);
     int* ht0 = B.take<int>(2);
@@ -662,7 +730,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     long long* agg = B.take<long long>((size_t)max_tiles * 3);
     long long* pre = B.take<long long>((size_t)max_tiles * 3);
     if (G) {
-      G->halos = hd; G->any_active = words + 8; G->key_or_and = (uint32_t*)(words + 10);
+      G->halos = hd; G->any_active = words + 8; G->key_or_and = (unsigned long long*)(words + 10);
       G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
       G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
       G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
@@ -680,6 +748,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
   O.res = out; O.bound_idx = (long long*)bound_idx; O.phi = phi; O.removed_iter = removed_iter;
   O.member_idx = (const long long*)member_idx; O.n_slots = n_slots; O.err = c->err_dev;
   G.p = to_dev(p); G.frame = P.frame; G.prm = to_dev(prm); G.out = O; G.n_halos = 1;
+  G.fp64 = prm->precision == AHF_PREC_FP64 ? 1 : 0;
   reset_stats(c);
   for (const HaloDev& d0 : P.hd) {
     HaloDev d = d0;
@@ -711,8 +780,8 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     AHF_CUDA(stage(G.halo_tile0, ht0, sizeof(ht0)));
     if ((rc = pin_release(c, s))) return rc;
     AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(uint32_t), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(uint32_t), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(unsigned long long), s));
+    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(unsigned long long), s));
     if (G.n_tiles == 0) {
       // no candidates: an empty record
       ahf_result R{};
@@ -783,9 +852,8 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   void* dphi = phi ? (void*)B.take<char>((size_t)std::max<int64_t>(n_slots, 1) * ps) : nullptr;
   int32_t* dri = removed_iter ? B.take<int32_t>((size_t)std::max<int64_t>(n_slots, 1)) : nullptr;
   double* dprof = n_bins > 0 ? B.take<double>((size_t)n_halos * n_bins * 4 + 1) : nullptr;
-  if ((rc = unbind_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, dphi, dri, s))) return rc;
-  if (n_bins > 0 &&
-      (rc = profile_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, n_bins, r_min_frac, dprof, s)))
+  if ((rc = unbind_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, dphi, dri, s, n_bins, r_min_frac,
+                        n_bins > 0 ? dprof : nullptr)))
     return rc;
   if (n_halos) AHF_CUDA(cudaMemcpyAsync(out, dout, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
   if (n_bins > 0 && n_halos)
@@ -973,6 +1041,17 @@ int ahf_unbind_plain(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, 
   if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
   std::lock_guard<std::mutex> g(c->mu);
   return plain_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, (cudaStream_t)stream);
+}
+
+int ahf_unbind_profile_batch(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                             const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx,
+                             void* phi, int32_t* removed_iter, int32_t n_bins, double r_min_frac, double* prof,
+                             void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  if (n_halos > 0 && !prof) return fail(AHF_ERR_INVALID, "prof must not be NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return unbind_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, (cudaStream_t)stream,
+                     n_bins, r_min_frac, n_halos > 0 ? prof : nullptr);
 }
 
 int ahf_profile_batch(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,

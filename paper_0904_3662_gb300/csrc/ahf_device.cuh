@@ -203,6 +203,25 @@ __device__ __forceinline__ float load_mass(const ParticlesDev& p, long long i) {
   return __ldg((const float*)p.m + i);
 }
 
+// Offset d = x - c of candidate i from the halo centre, rounded once to
+// float.  With float inputs, no periodic box and a float-exact centre the
+// IEEE subtraction already is that correctly rounded offset; otherwise the
+// exact fixed-point route above.  Returns the fixed-point offset in f (valid
+// only on the second route).
+template <int CT>
+__device__ __forceinline__ void offset_of(const ParticlesDev& p, long long i, const HaloDev& H, float d[3],
+                                          long long f[3]) {
+  if (CT != AHF_COORD_F64 && H.fast) {
+    d[0] = __fsub_rn(__ldg((const float*)p.x + i), H.cf[0]);
+    d[1] = __fsub_rn(__ldg((const float*)p.y + i), H.cf[1]);
+    d[2] = __fsub_rn(__ldg((const float*)p.z + i), H.cf[2]);
+  } else {
+    load_offset_fix<CT>(p, i, H.cfix, H.boxfix, H.frac, f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = f32_from_fixcoord(f[k], H.frac);
+  }
+}
+
 // Member of the gather sphere: |d| <= R decided in FP64 arithmetic.  The
 // float test settles all but the candidates within ~1e-6 of the surface.
 __device__ __forceinline__ bool inside_sphere(const long long f[3], const float df[3], int frac, double R2,
@@ -215,6 +234,26 @@ __device__ __forceinline__ bool inside_sphere(const long long f[3], const float 
   for (int k = 0; k < 3; ++k) dd[k] = scale_pow2d((double)f[k], -frac);
   const double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
   return r2 <= R2;
+}
+
+// Membership of the candidate whose offset offset_of returned (FP64 decision).
+template <int CT>
+__device__ __forceinline__ bool member_of(const ParticlesDev& p, long long i, const HaloDev& H, const float df[3],
+                                          const long long f[3]) {
+  const float r2f = fmaf(df[2], df[2], fmaf(df[1], df[1], df[0] * df[0]));
+  if (r2f < H.R2lo) return true;
+  if (r2f > H.R2hi) return false;
+  double dd[3];
+  if (CT != AHF_COORD_F64 && H.fast) {
+    // exact in FP64: the difference of two floats of similar magnitude
+    dd[0] = (double)__ldg((const float*)p.x + i) - (double)H.cf[0];
+    dd[1] = (double)__ldg((const float*)p.y + i) - (double)H.cf[1];
+    dd[2] = (double)__ldg((const float*)p.z + i) - (double)H.cf[2];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dd[k] = scale_pow2d((double)f[k], -H.frac);
+  }
+  return dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] <= H.R2;
 }
 
 __device__ __forceinline__ float radius_of(const float df[3]) {
@@ -234,6 +273,62 @@ __device__ __forceinline__ float rinv_of(float r, float r_soft) {
 // way in every kernel (explicit FMA: no compiler contraction choices).
 __device__ __forceinline__ float phi_of(float m_inner, float rinv, float outer, float G) {
   return __fmul_rn(-G, __fmaf_rn(m_inner, rinv, outer));
+}
+
+// r <= e for a float radius r against the FP64 edge e (ef its float
+// rounding), decided exactly.
+__device__ __forceinline__ bool le_edge(float r, float ef, double e) {
+  if (r < ef) return true;
+  if (r > ef) return false;
+  return (double)r <= e;
+}
+
+// Log-radial profile rows of one halo from its compacted bound set held on
+// chip: radii rc[idx(k)] ascending and inclusive exact masses mc[idx(k)]
+// (scale 2^-s_m), k < nb.  Row b covers (e_b, e_{b+1}], e_b = r_out f^(1-b/n),
+// r_out = r_vir or the outermost bound radius (Sect. 2.1, the radially binned
+// output).  The calling threads take rows t0, t0 + stride, ...
+template <typename Idx>
+__device__ void profile_rows(const ProfileRows& Q, int h, const float* rc, const long long* mc, Idx idx, long long nb,
+                             double r_vir, int s_m, double G, const double* m0, int t0, int stride) {
+  const int n = Q.n_bins;
+  double* out = Q.prof + (size_t)h * n * 4;
+  if (nb == 0) {
+    for (int i = t0; i < 4 * n; i += stride) out[i] = 0.0;
+    return;
+  }
+  const double r_out = r_vir > 0.0 ? r_vir : (double)rc[idx(nb - 1)];
+  auto count_le = [&](double e) {
+    const float ef = (float)e;
+    long long lo = 0, hi = nb;            // first k with rc[k] > e
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (le_edge(rc[idx(mid)], ef, e)) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  for (int b = t0; b < n; b += stride) {
+    const double e0 = r_out * Q.factor[b];
+    const double e1 = b + 1 == n ? r_out : r_out * Q.factor[b + 1];
+    const long long c0 = count_le(e0), c1 = count_le(e1);
+    // masses: count * m0 for a uniform particle mass (m0 != NULL), else the
+    // exact fixed-point sums
+    double M1, Mshell;
+    if (m0) {
+      M1 = (double)c1 * *m0;
+      Mshell = (double)(c1 - c0) * *m0;
+    } else {
+      const long long f0 = c0 > 0 ? mc[idx(c0 - 1)] : 0;
+      const long long f1 = c1 > 0 ? mc[idx(c1 - 1)] : 0;
+      M1 = double_from_fix(f1, s_m);
+      Mshell = double_from_fix(f1 - f0, s_m);
+    }
+    out[4 * b + 0] = (double)(c1 - c0);
+    out[4 * b + 1] = M1;
+    out[4 * b + 2] = Mshell / (4.0 * 3.14159265358979323846 / 3.0 * (e1 * e1 * e1 - e0 * e0 * e0));
+    out[4 * b + 3] = sqrt(G * M1 / e1);
+  }
 }
 
 // ---- warp / block scans ---------------------------------------------------------

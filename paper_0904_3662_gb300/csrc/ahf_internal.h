@@ -31,7 +31,13 @@ struct HaloDev {
   long long boxfix;    // periodic box in this halo's 2^-frac units (0 = none)
   int frac;            // fractional bits of this halo's fixed-point offsets
   int index;           // caller's halo index
-};
+  float cf[3];         // centre as float (when fast)
+  int fast;            // float inputs, no box, float-exact centre: x - c in FP32
+};                     // is already the correctly rounded offset
+
+// Fill the device descriptor of one halo (shared by every entry point, so a
+// halo gets the same frame whichever way it is submitted).
+void fill_halo_dev(const ahf_halo &H, int coord_type, double box, int index, HaloDev &d);
 
 struct FrameDev {
   double box;          // periodic box (0 = none)
@@ -82,13 +88,21 @@ struct GridHaloState {
   int status;
   int active;
   int s_m, s_mr, s_mv;               // fixed-point scales
-  float vbulk[3];
+  float vbulk[3];                    // v_bulk of the current set (mixed precision)
+  double vbulk_d[3];                 // v_bulk of the current set (all-FP64 mode)
 };
 
 // Record a static message as the thread's last error (no allocation).
 void set_last_error_static(const char *msg);
 
 // ---- launchers (defined in the .cu files) -----------------------------------
+
+// Profile rows requested from the unbinding kernels themselves.
+struct ProfileRows {
+  double *prof;              // [n_halos][n_bins][4] (caller order), NULL = none
+  const double *factor;      // f^(1 - b/n), b = 0..n-1
+  int n_bins;
+};
 
 struct OnchipLaunch {
   ParticlesDev p;
@@ -98,6 +112,7 @@ struct OnchipLaunch {
   const HaloDev *halos;  // this class's haloes, largest first
   int n_halos;
   int *queue;            // work counter (zeroed by the launcher)
+  ProfileRows rows;      // rows.prof == NULL: no profile from this launch
 };
 
 // Warp class: one warp per halo of at most warp_capacity() candidates.
@@ -122,13 +137,16 @@ struct GridLaunch {
   int n_halos;
   long long n_flat;        // sum of candidate counts of the class
   GridHaloState *state;    // n_halos
-  // flat arrays (n_flat each unless noted)
-  uint32_t *key_a, *key_b, *val_a, *val_b;
-  uint32_t *key_x, *val_x;  // the sorted pair (one of a / b)
-  float4 *wm;              // (w.x, w.y, w.z, m) with m's sign bit = removed
-  float *r;
+  int fp64;                // 0: mixed precision (float), 1: all-FP64 (double)
+  // flat arrays (n_flat each unless noted); element types follow fp64
+  void *key_a, *key_b;     // radius keys: uint32 / uint64
+  uint32_t *val_a, *val_b;
+  void *key_x;             // the sorted keys (one of a / b)
+  uint32_t *val_x;         // the sorted candidate positions
+  void *wm;                // (w.x, w.y, w.z, m), m's sign bit = removed: float4 / 4 doubles
+  void *r;                 // radius: float / double
   long long *mc;           // compacted inclusive mass (final pass)
-  float *rc;               // compacted radius (final pass)
+  void *rc;                // compacted radius (final pass): float / double
   // tiles
   int n_tiles;
   int2 *tile_range;        // (first flat index, length)
@@ -139,7 +157,7 @@ struct GridLaunch {
   long long *tile_agg;     // n_tiles * 3
   long long *tile_pre;     // n_tiles * 3
   int *any_active;         // device flag read by the host loop
-  uint32_t *key_or_and;    // 2 words
+  unsigned long long *key_or_and;  // OR and AND of every key
   int sort_passes;         // radix passes the last grid_sort launched
 };
 
@@ -147,7 +165,7 @@ constexpr int GRID_TILE = 2048;
 constexpr int GRID_THREADS = 256;
 
 cudaError_t grid_prepare(const GridLaunch &L, cudaStream_t s);
-cudaError_t grid_sort(GridLaunch &L, cudaStream_t s, uint32_t or_bits, uint32_t and_bits);
+cudaError_t grid_sort(GridLaunch &L, cudaStream_t s, unsigned long long or_bits, unsigned long long and_bits);
 cudaError_t grid_fill(const GridLaunch &L, cudaStream_t s);
 cudaError_t grid_iterate(const GridLaunch &L, int iter, cudaStream_t s);
 cudaError_t grid_finish(const GridLaunch &L, cudaStream_t s);

@@ -57,6 +57,10 @@ struct Cl {
   }
 };
 
+// Largest bin count a cluster forms profile rows for itself (larger requests
+// use the profile kernels).
+constexpr int FUSE_BINS = 128;
+
 // Values a CTA publishes to the other CTAs of its cluster.
 struct Xchg {
   int halo;
@@ -70,6 +74,13 @@ struct Xchg {
   float first_r;                // emit: first compacted radius of this CTA
   int nb_loc;                   // emit: bound particles held by this CTA
   int kf;                       // emit: first local virial crossing (global index)
+  // fused profile rows: r_vir from the owner CTA, last radius, and this CTA's
+  // bound count and inclusive mass at every bin edge
+  double rvir;
+  int has_rvir;
+  float last_r;
+  int pc[FUSE_BINS + 1];
+  long long pm[FUSE_BINS + 1];
 };
 
 template <int NT>
@@ -313,11 +324,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         uint32_t key = KEY_NONMEMBER;
         if (ok) {
           long long f[3];
-          load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
           float df[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) df[k] = f32_from_fixcoord(f[k], H.frac);
-          if (inside_sphere(f, df, H.frac, H.R2, H.R2lo, H.R2hi)) {
+          offset_of<CT>(L.p, pi, H, df, f);
+          if (member_of<CT>(L.p, pi, H, df, f)) {
             const float r = radius_of(df);
             key = __float_as_uint(r);
             const float m = load_mass<CT>(L.p, pi);
@@ -379,6 +388,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     const int s_m = fix_scale(float_exponent_of_bits(S.max_m), n_mem);
     const int s_r = fix_scale(float_exponent_of_bits(S.max_mr), n_mem);
     const int s_v = fix_scale(float_exponent_of_bits(S.max_mv), n_mem);
+    const bool unim = L.p.m == nullptr;                  // every particle has mass m0
+    const long long m0fix = fix_from_float(L.p.m0f, s_m);
 
     // ---- radial sort (once) ----
     const int which = cluster_radix_sort<NT, IPT, CS>(kA, vA, kB, vB, hist, S, X, nloc, chunk,
@@ -399,14 +410,15 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         const long long slot = H.offset + j;
         const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
         long long f[3];
-        load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
+        float dfl[3];
+        offset_of<CT>(L.p, pi, H, dfl, f);
         float v[3];
         load_velocity<CT>(L.p, pi, v);
         const float m = load_mass<CT>(L.p, pi);
         mm[q] = m;
-        wx[q] = fmaf(P.Hf, f32_from_fixcoord(f[0], H.frac), v[0]);
-        wy[q] = fmaf(P.Hf, f32_from_fixcoord(f[1], H.frac), v[1]);
-        wz[q] = fmaf(P.Hf, f32_from_fixcoord(f[2], H.frac), v[2]);
+        wx[q] = fmaf(P.Hf, dfl[0], v[0]);
+        wy[q] = fmaf(P.Hf, dfl[1], v[1]);
+        wz[q] = fmaf(P.Hf, dfl[2], v[2]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) smv[k] += fix_from_float(__fmul_rn(m, v[k]), s_v);
       }
@@ -438,7 +450,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       if (p < nmem_loc) {
         const int q = sw(p, mask);
         const float m = mm[q];
-        tm_own += fix_from_float(m, s_m);
+        tm_own += (unim ? m0fix : fix_from_float(m, s_m));
         tr_own += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
         tc_own += 1;
       }
@@ -479,7 +491,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           const float m = mm[q];
           if (!signbit(m)) {
             const float ri = rinv_of(rr[q], P.r_soft_f);
-            const long long mfix = fix_from_float(m, s_m);
+            const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
             const long long rfix = fix_from_float(m * ri, s_r);
             const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
             const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
@@ -581,7 +593,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           if (!signbit(m)) {
             const float r = rr[q];
             const float ri = rinv_of(r, P.r_soft_f);
-            const long long mfix = fix_from_float(m, s_m);
+            const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
             const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
             const int j = (int)jj[q];
             const long long slot = H.offset + j;
@@ -662,7 +674,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         R.r_vir = 0.0;
         if (nb > 0) {
           const int kl = (int)(k - C_pre);
-          const double mk = double_from_fix(mc[sw(kl, mask)], s_m);
+          // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
+          const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(kl, mask)], s_m);
           const double rk = (double)rc[sw(kl, mask)];
           if (k == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
           if (mk < P.crit * rk * rk * rk) {
@@ -679,6 +692,87 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         }
         R.status = status;
         L.out.res[H.index] = R;
+        if constexpr (CS > 1) {
+          X.rvir = R.r_vir;
+          X.has_rvir = 1;
+        }
+      }
+      if constexpr (CS > 1) {
+        if (L.rows.prof && L.rows.n_bins <= FUSE_BINS) {
+          // rows of a halo spread over the cluster: each CTA counts its chunk
+          // of the radial order at every edge; rank 0 adds the counts and
+          // takes the largest inclusive mass (the last particle inside)
+          if (tid == 0) {
+            if (!owner) X.has_rvir = 0;
+            X.last_r = C_loc > 0 ? rc[sw((int)C_loc - 1, mask)] : 0.0f;
+          }
+          Cl<CS>::sync();
+          double r_vir = 0.0;
+          float r_last = 0.0f;
+          for (int r2 = 0; r2 < CS; ++r2) {
+            const Xchg* Y = Cl<CS>::at(&X, r2);
+            if (Y->has_rvir) r_vir = Y->rvir;
+            if (Y->nb_loc > 0) r_last = Y->last_r;
+          }
+          const double r_out = r_vir > 0.0 ? r_vir : (double)r_last;
+          const int n = L.rows.n_bins;
+          for (int b = tid; b <= n; b += NT) {
+            const double e = b == n ? r_out : r_out * L.rows.factor[b];
+            const float ef = (float)e;
+            int lo = 0, hi = (int)C_loc;            // first local k with rc[k] > e
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (le_edge(rc[sw(mid, mask)], ef, e)) lo = mid + 1;
+              else hi = mid;
+            }
+            X.pc[b] = lo;
+            X.pm[b] = lo > 0 ? mc[sw(lo - 1, mask)] : 0;
+          }
+          Cl<CS>::sync();
+          if (rank == 0) {
+            double* out = L.rows.prof + (size_t)H.index * n * 4;
+            for (int b = tid; b < n; b += NT) {
+              long long c0 = 0, c1 = 0, f0 = 0, f1 = 0;
+              for (int r2 = 0; r2 < CS; ++r2) {
+                const Xchg* Y = Cl<CS>::at(&X, r2);
+                c0 += Y->pc[b];
+                c1 += Y->pc[b + 1];
+                f0 = max(f0, Y->pm[b]);
+                f1 = max(f1, Y->pm[b + 1]);
+              }
+              if (nb == 0) {
+                out[4 * b + 0] = out[4 * b + 1] = out[4 * b + 2] = out[4 * b + 3] = 0.0;
+                continue;
+              }
+              const double e0 = r_out * L.rows.factor[b];
+              const double e1 = b + 1 == n ? r_out : r_out * L.rows.factor[b + 1];
+              double M1, Ms;
+              if (unim) {
+                M1 = (double)c1 * L.p.m0;
+                Ms = (double)(c1 - c0) * L.p.m0;
+              } else {
+                M1 = double_from_fix(f1, s_m);
+                Ms = double_from_fix(f1 - f0, s_m);
+              }
+              out[4 * b + 0] = (double)(c1 - c0);
+              out[4 * b + 1] = M1;
+              out[4 * b + 2] = Ms / (4.0 * 3.14159265358979323846 / 3.0 * (e1 * e1 * e1 - e0 * e0 * e0));
+              out[4 * b + 3] = sqrt(P.G * M1 / e1);
+            }
+          }
+        }
+      }
+      if constexpr (CS == 1) {
+        if (L.rows.prof) {
+          double r_vir = 0.0;
+          if (nb > 0) {
+            const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(k, mask)], s_m);
+            const double rk = (double)rc[sw(k, mask)];
+            if (!(mk < P.crit * rk * rk * rk)) r_vir = cbrt(mk / P.crit);
+          }
+          profile_rows(L.rows, H.index, rc, mc, [&](long long kk) { return sw((int)kk, mask); }, nb, r_vir, s_m,
+                       P.G, unim ? &L.p.m0 : nullptr, tid, NT);
+        }
       }
     }
     Cl<CS>::sync();

@@ -26,18 +26,9 @@ constexpr int MAX_BINS = 4096;
 template <int CT>
 __device__ __forceinline__ float bound_radius(const ProfileLaunch& L, const HaloDev& H, long long pi) {
   long long f[3];
-  load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
   float df[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) df[a] = f32_from_fixcoord(f[a], H.frac);
+  offset_of<CT>(L.p, pi, H, df, f);
   return radius_of(df);
-}
-
-// r <= e (FP64 edge e, its float rounding ef) for a float radius r, exactly.
-__device__ __forceinline__ bool le_edge(float r, float ef, double e) {
-  if (r < ef) return true;
-  if (r > ef) return false;
-  return (double)r <= e;
 }
 
 // Inclusive block scan of one double per thread (PT threads).

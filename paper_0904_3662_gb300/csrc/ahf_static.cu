@@ -31,7 +31,7 @@ constexpr size_t STATIC_COUNTER_BYTES = 256;   // 3 queue counters + the error w
 constexpr size_t STATIC_SCRATCH_BYTES =
     STATIC_COUNTER_BYTES + sizeof(HaloDev) * (size_t)AHF_STATIC_MAX_HALOS;
 
-// The scratch array (about 3.3 MiB, held by every GPU that loads the
+// The scratch array (about 3.8 MiB, held by every GPU that loads the
 // library until the process exits).  In host code this name is only a
 // host-side stand-in; kernels receive the device address looked up below.
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
@@ -49,11 +49,6 @@ int fail_static(int code, const char* msg) {
   return code;
 }
 
-int ceil_log2_static(double x) {
-  int e = 0;
-  while (e < 1100 && std::ldexp(1.0, e) <= x) ++e;
-  return e;
-}
 
 }  // namespace
 
@@ -143,22 +138,7 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
     const int h = g_order[k];
     const ahf_halo& H = halos[h];
     n_class[cls(H.count)]++;
-    HaloDev& d = g_stage[k];
-    d.c[0] = H.cx; d.c[1] = H.cy; d.c[2] = H.cz;
-    const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
-    double span = std::max(cm + std::fabs(H.radius), prm->box);
-    if (p->coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
-    const int frac = std::max(-200, std::min(200, 60 - ceil_log2_static(span + 1.0)));
-    d.frac = frac;
-    d.boxfix = prm->box > 0.0 ? (long long)std::llround(std::ldexp(prm->box, frac)) : 0;
-    for (int a = 0; a < 3; ++a) d.cfix[a] = (long long)std::llround(std::ldexp(d.c[a], frac));
-    d.R2 = H.radius * H.radius;
-    d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
-    d.R2hi = (float)(d.R2 * (1.0 + 4e-6));
-    d.offset = H.offset;
-    d.count = H.count;
-    d.gbase = 0;
-    d.index = h;
+    fill_halo_dev(H, p->coord_type, prm->box, h, g_stage[k]);
   }
   cudaStream_t s = (cudaStream_t)stream;
   // pageable source: the copy has taken the bytes when the call returns
@@ -182,6 +162,7 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   L.prm.precision = prm->precision;
   L.out.res = out; L.out.bound_idx = (long long*)bound_idx; L.out.phi = phi; L.out.removed_iter = removed_iter;
   L.out.member_idx = (const long long*)member_idx; L.out.n_slots = n_slots; L.out.err = counters + 8;
+  L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.n_bins = 0;
   // variants in the order the descriptors were staged; each class is its own queue
   int base = 0;
   for (int v = 0; v < 3; ++v) {

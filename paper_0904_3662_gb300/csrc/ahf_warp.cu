@@ -148,11 +148,9 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       uint32_t key = KEY_NONMEMBER;
       if (ok) {
         long long f[3];
-        load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
         float df[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) df[k] = f32_from_fixcoord(f[k], H.frac);
-        if (inside_sphere(f, df, H.frac, H.R2, H.R2lo, H.R2hi)) {
+        offset_of<CT>(L.p, pi, H, df, f);
+        if (member_of<CT>(L.p, pi, H, df, f)) {
           const float r = radius_of(df);
           key = __float_as_uint(r);
           const float m = load_mass<CT>(L.p, pi);
@@ -184,6 +182,8 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     const int s_m = fix_scale(float_exponent_of_bits(mxm), n_mem);
     const int s_r = fix_scale(float_exponent_of_bits(mxr), n_mem);
     const int s_v = fix_scale(float_exponent_of_bits(mxv), n_mem);
+    const bool unim = L.p.m == nullptr;                  // every particle has mass m0
+    const long long m0fix = fix_from_float(L.p.m0f, s_m);
 
     // ---- radial sort (once) ----
     const int which = warp_radix_sort(kA, vA, kB, vB, hist, n_cand, orb ^ andb, mask, lane);
@@ -202,14 +202,15 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       const long long slot = H.offset + j;
       const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
       long long f[3];
-      load_offset_fix<CT>(L.p, pi, H.cfix, H.boxfix, H.frac, f);
+      float dfl[3];
+      offset_of<CT>(L.p, pi, H, dfl, f);
       float v[3];
       load_velocity<CT>(L.p, pi, v);
       const float m = load_mass<CT>(L.p, pi);
       mm[q] = m;
-      wx[q] = fmaf(P.Hf, f32_from_fixcoord(f[0], H.frac), v[0]);
-      wy[q] = fmaf(P.Hf, f32_from_fixcoord(f[1], H.frac), v[1]);
-      wz[q] = fmaf(P.Hf, f32_from_fixcoord(f[2], H.frac), v[2]);
+      wx[q] = fmaf(P.Hf, dfl[0], v[0]);
+      wy[q] = fmaf(P.Hf, dfl[1], v[1]);
+      wz[q] = fmaf(P.Hf, dfl[2], v[2]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) mv[k] += fix_from_float(__fmul_rn(m, v[k]), s_v);
     }
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       if (p < n_mem) {
         const int q = sw(p, mask);
         const float m = mm[q];
-        tm_own += fix_from_float(m, s_m);
+        tm_own += (unim ? m0fix : fix_from_float(m, s_m));
         tr_own += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
         tc_own += 1;
       }
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
           const float m = mm[q];
           if (!signbit(m)) {
             const float ri = rinv_of(rr[q], P.r_soft_f);
-            const long long mfix = fix_from_float(m, s_m);
+            const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
             const long long rfix = fix_from_float(m * ri, s_r);
             const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
             const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
         if (!signbit(m)) {
           const float r = rr[q];
           const float ri = rinv_of(r, P.r_soft_f);
-          const long long mfix = fix_from_float(m, s_m);
+          const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
           const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
           const long long slot = H.offset + (long long)jj[q];
           const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
@@ -363,7 +364,8 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       R.m_vir = 0.0;
       R.r_vir = 0.0;
       if (nb > 0) {
-        const double mk = double_from_fix(mc[sw(kf, mask)], s_m);
+        // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
+        const double mk = unim ? (double)(kf + 1) * L.p.m0 : double_from_fix(mc[sw(kf, mask)], s_m);
         const double rk = (double)rc[sw(kf, mask)];
         if (kf == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
         if (mk < P.crit * rk * rk * rk) {
@@ -380,6 +382,17 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       }
       R.status = status;
       L.out.res[H.index] = R;
+    }
+    if (L.rows.prof) {
+      // r_vir as the record has it (lane 0 computed it; recompute identically)
+      double r_vir = 0.0;
+      if (nb > 0) {
+        const double mk = unim ? (double)(kf + 1) * L.p.m0 : double_from_fix(mc[sw(kf, mask)], s_m);
+        const double rk = (double)rc[sw(kf, mask)];
+        if (!(mk < P.crit * rk * rk * rk)) r_vir = cbrt(mk / P.crit);
+      }
+      profile_rows(L.rows, H.index, rc, mc, [&](long long k) { return sw((int)k, mask); }, nb, r_vir, s_m, P.G,
+                   unim ? &L.p.m0 : nullptr, lane, 32);
     }
     __syncwarp();
   }

@@ -91,3 +91,32 @@ def test_cluster_and_grid_agree_bitwise():
         lo, nb = int(pop.offset[h]), int(a["res"][h]["n_bound"])
         np.testing.assert_array_equal(a["bound_idx"][lo:lo + nb], b["bound_idx"][lo:lo + nb])
         np.testing.assert_array_equal(a["phi"][lo:lo + nb], b["phi"][lo:lo + nb])
+
+
+def test_all_fp64_mode_single_and_batch():
+    # the all-FP64 path: phi to 1e-11, virial to 1e-11, bound lists in the
+    # oracle's exact radial order
+    from paper_0904_3662_gb300 import ahf
+    from tests.gpu_util import require_gpu
+    require_gpu()
+    for pop in (synth.single_halo(),
+                synth.halo_batch(seed=51, n_halos=25, n_lo=100, n_hi=20000, coord_type=synth.COORD_F64,
+                                 with_masses=True),
+                synth.halo_batch(seed=52, n_halos=10, n_lo=100, n_hi=5000)):
+        prm = ahf.params_for(pop, precision=ahf.PREC_FP64)
+        out, prm, ctx, _ = run_gpu(pop, params=prm)
+        assert out["phi"].dtype == np.float64
+        s = compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"], phi_rtol=1e-11,
+                    vir_rtol=1e-11, exact_order=True)
+        assert s["worst_phi_rel"] < 1e-11
+
+
+def test_all_fp64_mode_periodic_box():
+    from paper_0904_3662_gb300 import ahf
+    from tests.gpu_util import require_gpu
+    require_gpu()
+    pop = synth.large_tail(seed=53, n_halos=2, n_lo=3000, n_hi=20000, n_sub=4, box=5e5)
+    prm = ahf.params_for(pop, precision=ahf.PREC_FP64)
+    out, prm, _, _ = run_gpu(pop, params=prm)
+    compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"], phi_rtol=1e-11,
+            vir_rtol=1e-11, exact_order=True)

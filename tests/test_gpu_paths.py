@@ -262,3 +262,28 @@ def test_invalid_arguments_are_rejected():
         ctx.sync()
     assert e.value.code == ahf.ERR_INVALID
     ctx.sync()                                    # cleared
+
+
+def test_fused_profile_matches_standalone_and_oracle():
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    # every class: warp, CTA, clusters (and the multi-CTA class through a second context)
+    pop = synth.halo_batch(seed=41, n_halos=60, n_lo=100, n_hi=100_000, with_masses=True)
+    ctx = ahf.Context(0)
+    parts = ahf.particles_from_population(pop)
+    hal = ahf.halos_from_population(pop)
+    prm = ahf.params_for(pop)
+    for onchip_max in (None, 0):
+        if onchip_max is not None:
+            ctx.set_option(ahf.OPT_ONCHIP_MAX, onchip_max)
+        fused = ctx.unbind_profile_batch(parts, hal, prm, n_bins=20, r_min_frac=0.02)
+        sep = ctx.profile_batch(parts, hal, prm, fused["res"], fused["bound_idx"], n_bins=20, r_min_frac=0.02)
+        torch.cuda.synchronize()
+        a = fused["prof"].cpu().numpy()
+        b = sep.cpu().numpy()
+        np.testing.assert_array_equal(a[:, :, 0], b[:, :, 0])
+        np.testing.assert_allclose(a[:, :, 1:], b[:, :, 1:], rtol=1e-12, atol=0)
+        res = ahf.results_to_numpy(fused["res"])
+        compare(pop, prm, res, fused["bound_idx"].cpu().numpy(), fused["phi"].cpu().numpy(),
+                fused["removed_iter"].cpu().numpy())
+        _check_profiles(pop, prm, res, a, 20, 0.02)
