@@ -54,7 +54,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ahf", "reference"], default="ahf")
-    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep"], default="batch")
+    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep", "serve"], default="batch")
+    ap.add_argument("--requests", type=int, default=50_000, help="serve workload: requests per rate")
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000",
+                    help="serve workload: Poisson arrival rates (requests/s)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -458,10 +461,97 @@ def time_e2e(ctx, pop, hal, prm, units, args):
             "ms_per_step": s * 1e3, "api": "ahf_unbind_batch_host (unbinding + profile, host buffers)"}
 
 
+def run_serve(args):
+    """Serving stream: Poisson arrivals of one-halo requests (95 % with
+    N_p ~ N^-1.9 on [100, 1e4), 5 % on [1e4, 1e5], 15 % contaminants each)
+    submitted from host memory through ahf_serve_submit at each rate of the
+    sweep; latency is the library's submit-to-poll-visible time."""
+    import collections
+    import torch
+    from paper_0904_3662_gb300 import ahf, build_lib, synth
+    build_lib.build()
+    torch.cuda.init()
+    t0 = time.perf_counter()
+    small = synth.halo_batch(seed=synth.SEED_BASE + 5, n_halos=1900, n_lo=100, n_hi=9_999)
+    large = synth.halo_batch(seed=synth.SEED_BASE + 6, n_halos=100, n_lo=10_000, n_hi=100_000)
+    t_unit, counts = synth.serving_stream(n_requests=args.requests, rate_hz=1.0)
+    big = counts >= 10_000
+    pools = []
+    for pop in (small, large):
+        parts = ahf.Particles(pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz, None, pop.m0, pop.coord_type)
+        hal = ahf.halos_from_population(pop)
+        pools.append([ahf.Serve.request(parts, hal[h:h + 1]) for h in range(pop.n_halos)])
+    reqs, k_small, k_big, cand = [], 0, 0, 0
+    for b in big:
+        if b:
+            reqs.append(pools[1][k_big % len(pools[1])])
+            cand += int(large.count[k_big % large.n_halos])
+            k_big += 1
+        else:
+            reqs.append(pools[0][k_small % len(pools[0])])
+            cand += int(small.count[k_small % small.n_halos])
+            k_small += 1
+    log(f"serve pool ready in {time.perf_counter() - t0:.1f} s; {len(reqs)} requests, {cand} candidates")
+    prm = ahf.params_for(small)
+    srv = ahf.Serve(prm, hbm_cap_bytes=60 << 30, coord_type=small.coord_type, m0=small.m0)
+    # warm-up: a few hundred requests at no particular rate
+    warm = [srv.submit_prepared(reqs[i]) for i in range(min(300, len(reqs)))]
+    for rid in warm:
+        while rid is not None and srv.poll(rid) is None:
+            time.sleep(1e-4)
+    sweep = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        arr = t_unit / rate
+        srv.reset_stats()
+        pending = collections.deque()
+        refused, i, n = 0, 0, len(reqs)
+        rid = 0
+        start = time.perf_counter()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            while i < n:
+                now = time.perf_counter() - start
+                if now >= arr[i]:
+                    rid = srv.submit_prepared(reqs[i])
+                    if rid is None:
+                        refused += 1
+                    else:
+                        pending.append(rid)
+                        i += 1
+                        continue
+                while pending and srv.poll(pending[0]) is not None:
+                    pending.popleft()
+            t_sub = time.perf_counter() - start
+            while pending:
+                if srv.poll(pending[0]) is None:
+                    time.sleep(1e-4)
+                else:
+                    pending.popleft()
+        st = srv.stats()
+        row = {"rate": rate, "offered": n / t_sub, "throughput": st["throughput"], "p50_us": st["p50_us"],
+               "p99_us": st["p99_us"], "batches": st["batches"], "mean_batch": n / max(1, st["batches"]),
+               "refused": refused, "clocks": clk.summary()}
+        log(f"rate {rate:.0f}/s: offered {row['offered']:.0f}/s, {st['throughput']:.0f} req/s, "
+            f"p50 {st['p50_us']:.0f} us, p99 {st['p99_us']:.0f} us, {st['batches']} batches")
+        sweep.append(row)
+    srv.close()
+    best = max(sweep, key=lambda r: r["throughput"])
+    line = {"metric": "requests/s", "value": best["throughput"], "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64",
+            "data": "synthetic",
+            "config": {"workload": "Poisson stream of one-halo requests, 95% N_p on [100, 1e4), 5% on [1e4, 1e5], "
+                                   "+15% contaminants, float32 relative, HBM cap 60 GB",
+                       "requests_per_rate": len(reqs), "candidates_per_pass": cand},
+            "sweep": sweep}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ahf(args)
 
 

@@ -289,6 +289,76 @@ int ahf_unbind_batch_static(const ahf_particles *p, const ahf_halo *halos, int64
                             const int64_t *member_idx, const ahf_params *prm, ahf_result *out,
                             int64_t *bound_idx, void *phi, int32_t *removed_iter, void *stream);
 
+/* ---- serving: continuous batching of one-halo requests --------------------
+ *
+ * For callers that produce candidate haloes over time rather than as one
+ * snapshot (the paper analyses a snapshot in one pass and has no such
+ * layer).  A request is one halo with its candidates; a worker thread packs
+ * the queued requests into batches and runs them through ahf_unbind_batch,
+ * forming and copying the next batch while the previous one computes.  A
+ * request's result is identical to unbinding that halo alone: every halo is
+ * computed independently and order-independently.
+ *
+ * Memory: ring buffers of S candidate slots in pinned host memory and in
+ * device memory, S fixed at creation from hbm_cap_bytes (device bytes for the
+ * rings, the result records and the context's workspace; S is at most 2^23).
+ * A request holds max(count, 1) slots from submission until its batch has
+ * completed; slots return in submission order. */
+typedef struct ahf_serve ahf_serve;
+
+/* Create a serving instance on `device` with parameters `prm` (copied).
+ * Every request uses coordinate encoding `coord_type`; m0 > 0 means every
+ * particle has mass m0 and requests carry no masses, m0 == 0 means every
+ * request carries per-particle masses.  Starts the worker thread.
+ * Errors: AHF_ERR_INVALID (NULL, bad params or coord_type, a cap too small
+ * for a request of AHF_SERVE_MAX_COUNT candidates), AHF_ERR_NOMEM,
+ * AHF_ERR_CUDA. */
+#define AHF_SERVE_MAX_COUNT 131072
+int ahf_serve_create(ahf_serve **s, int device, size_t hbm_cap_bytes, const ahf_params *prm,
+                     int32_t coord_type, double m0);
+
+/* Submit one halo.  p: HOST particle arrays (coord_type and masses as the
+ * instance takes them); halo: centre, gather radius, and the candidates
+ * [offset, offset + count) of p (count <= AHF_SERVE_MAX_COUNT).  The
+ * candidates are copied before the call returns, so the caller may reuse p.
+ * On success *req_id identifies the request.  Never blocks on the GPU.
+ * Errors: AHF_ERR_INVALID, AHF_ERR_NOMEM, AHF_ERR_FULL (no room in the ring
+ * now: poll completed requests and retry). */
+int ahf_serve_submit(ahf_serve *s, const ahf_particles *p, const ahf_halo *halo, uint64_t *req_id);
+
+/* Non-blocking: AHF_PENDING while the request runs; AHF_OK once it has
+ * completed, after writing its record to *out_host (nullable) and its bound
+ * list, sorted by radius and given as indices into the submitted p, to
+ * bound_idx_host[0 .. n_bound) (nullable; cap entries available).  A
+ * completed request is forgotten after AHF_OK (a second poll returns
+ * AHF_ERR_NOT_FOUND).  Errors: AHF_ERR_NOT_FOUND, AHF_ERR_INVALID (cap below
+ * n_bound: *out_host is written, the request is kept, poll again with a
+ * larger buffer), or the error that failed the request's batch (the request
+ * is then forgotten). */
+int ahf_serve_poll(ahf_serve *s, uint64_t req_id, ahf_result *out_host, int64_t *bound_idx_host,
+                   int64_t cap);
+
+/* Latency percentiles (microseconds from entering ahf_serve_submit until the
+ * result is visible to ahf_serve_poll, nearest rank over the requests
+ * completed since creation or the last reset) and throughput (completed
+ * requests per second between the first submission and the last completion).
+ * Any pointer may be NULL.  Errors: AHF_ERR_INVALID. */
+int ahf_serve_stats(ahf_serve *s, double *p50_us, double *p99_us, double *throughput);
+
+/* Counters since creation or the last reset; any pointer may be NULL:
+ * requests accepted, completed, refused with AHF_ERR_FULL, batches run. */
+int ahf_serve_counters(ahf_serve *s, int64_t *submitted, int64_t *completed, int64_t *rejected,
+                       int64_t *batches);
+
+/* Clear the latency samples and counters (requests in flight still count when
+ * they complete). */
+int ahf_serve_reset_stats(ahf_serve *s);
+
+/* Stop accepting requests, finish every accepted one, stop the worker and
+ * release the instance (results not yet polled are dropped).  NULL is
+ * accepted. */
+int ahf_serve_destroy(ahf_serve *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,10 @@ assert HALO_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 88
 # every symbol include/ahf.h declares
 EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_unbind_batch",
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
-           "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch")
+           "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch",
+           "ahf_serve_create", "ahf_serve_submit", "ahf_serve_poll", "ahf_serve_stats", "ahf_serve_counters",
+           "ahf_serve_reset_stats", "ahf_serve_destroy")
+SERVE_MAX_COUNT = 131072
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
 
 
@@ -98,6 +101,16 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.ahf_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     lib.ahf_sync.argtypes = [vp]
+    lib.ahf_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_Params),
+                                     i32, ctypes.c_double]
+    lib.ahf_serve_submit.argtypes = [vp, ctypes.POINTER(_Particles), vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ahf_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, vp, i64]
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.ahf_serve_stats.argtypes = [vp, dp, dp, dp]
+    ip = ctypes.POINTER(i64)
+    lib.ahf_serve_counters.argtypes = [vp, ip, ip, ip, ip]
+    lib.ahf_serve_reset_stats.argtypes = [vp]
+    lib.ahf_serve_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -308,6 +321,74 @@ class Context:
                                           ctypes.byref(prc), res_dev.data_ptr(), bound_idx.data_ptr(),
                                           int(n_bins), float(r_min_frac), prof.data_ptr(), _stream_ptr(stream)))
         return prof
+
+
+class Serve:
+    """An ahf_serve instance: one-halo requests from host arrays, continuous
+    batching on the device, non-blocking polls."""
+
+    def __init__(self, params: Params, device: int = 0, hbm_cap_bytes: int = 1 << 30,
+                 coord_type: int = COORD_F32_REL, m0: float = 0.0):
+        self.lib = load_library()
+        self._p = ctypes.c_void_p()
+        self._prm = params.c()
+        _check(self.lib.ahf_serve_create(ctypes.byref(self._p), int(device), int(hbm_cap_bytes),
+                                         ctypes.byref(self._prm), int(coord_type), float(m0)))
+        self._res = np.zeros(1, dtype=RESULT_DTYPE)
+        self._bound = np.empty(SERVE_MAX_COUNT, dtype=np.int64)
+
+    def close(self):
+        if self._p:
+            self.lib.ahf_serve_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def request(parts: Particles, halo):
+        """Prepared arguments of one submission (numpy particle arrays and a
+        one-element HALO_DTYPE array); keep the returned tuple alive until
+        submit returns."""
+        halo = np.ascontiguousarray(halo, dtype=HALO_DTYPE).reshape(1)
+        return (parts.c(), halo, parts)
+
+    def submit_prepared(self, req):
+        """Return the request id, or None when the ring is full (AHF_ERR_FULL)."""
+        rid = ctypes.c_uint64()
+        rc = self.lib.ahf_serve_submit(self._p, ctypes.byref(req[0]), req[1].ctypes.data, ctypes.byref(rid))
+        if rc == ERR_FULL:
+            return None
+        _check(rc)
+        return rid.value
+
+    def submit(self, parts: Particles, halo):
+        return self.submit_prepared(self.request(parts, halo))
+
+    def poll(self, req_id, cap=SERVE_MAX_COUNT):
+        """None while pending, else (result record, bound indices)."""
+        cap = max(1, min(int(cap), SERVE_MAX_COUNT))
+        bound = self._bound
+        rc = self.lib.ahf_serve_poll(self._p, int(req_id), self._res.ctypes.data, bound.ctypes.data, cap)
+        if rc == PENDING:
+            return None
+        _check(rc)
+        res = self._res[0].copy()
+        return res, bound[:int(res["n_bound"])].copy()
+
+    def stats(self):
+        p50, p99, thr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.ahf_serve_stats(self._p, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(thr)))
+        c = [ctypes.c_int64() for _ in range(4)]
+        _check(self.lib.ahf_serve_counters(self._p, *[ctypes.byref(x) for x in c]))
+        return {"p50_us": p50.value, "p99_us": p99.value, "throughput": thr.value, "submitted": c[0].value,
+                "completed": c[1].value, "rejected": c[2].value, "batches": c[3].value}
+
+    def reset_stats(self):
+        _check(self.lib.ahf_serve_reset_stats(self._p))
 
 
 def results_to_numpy(res_tensor):

@@ -66,6 +66,17 @@ struct Bump {
 
 void ahf::set_last_error_static(const char* msg) { g_last_ptr = msg; }
 
+int ahf::set_last_error_fmt(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  g_last_ptr = g_last_error.c_str();
+  return code;
+}
+
 namespace {
 
 // Shared-memory variants in size order: 0 = one warp per halo, 1-3 = one CTA
@@ -443,7 +454,9 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Plan P;
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
   reset_stats(c);
-  constexpr int FUSED_MAX = 3;     // variants 0..3 form profile rows themselves
+  // variants 0..3 form profile rows themselves, the clusters (4..6) too when
+  // the bin count fits their exchange record
+  const int FUSED_MAX = n_bins <= 128 ? NV - 1 : 3;
   int n_onchip = 0;
   for (int v = 0; v < NV; ++v) n_onchip += P.n_class[v];
   const int n_grid = P.n_class[NV];

@@ -94,6 +94,8 @@ struct GridHaloState {
 
 // Record a static message as the thread's last error (no allocation).
 void set_last_error_static(const char *msg);
+// Record a formatted message as the thread's last error and return `code`.
+int set_last_error_fmt(int code, const char *fmt, ...);
 
 // ---- launchers (defined in the .cu files) -----------------------------------
 

@@ -56,3 +56,31 @@ def test_create_without_gpu_reports_error():
         assert e.code == ahf.ERR_INVALID
     else:
         raise AssertionError("context creation without a GPU must fail")
+
+
+def test_serve_create_checks_arguments_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        return
+    from paper_0904_3662_gb300 import ahf
+    prm = ahf.Params()
+    # a cap below one full-size request is refused before any device call
+    try:
+        ahf.Serve(prm, hbm_cap_bytes=1 << 20)
+    except ahf.AHFError as e:
+        assert e.code == ahf.ERR_INVALID and "slots" in str(e)
+    else:
+        raise AssertionError("a tiny cap must be refused")
+    bad = ahf.Params(max_iter=0)
+    try:
+        ahf.Serve(bad)
+    except ahf.AHFError as e:
+        assert e.code == ahf.ERR_INVALID and "max_iter" in str(e)
+    else:
+        raise AssertionError("max_iter 0 must be refused")
+    try:
+        ahf.Serve(prm)
+    except ahf.AHFError as e:
+        assert e.code == ahf.ERR_INVALID
+    else:
+        raise AssertionError("serving without a GPU must fail")

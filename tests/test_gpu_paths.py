@@ -264,11 +264,12 @@ def test_invalid_arguments_are_rejected():
     ctx.sync()                                    # cleared
 
 
-def test_fused_profile_matches_standalone_and_oracle():
+@pytest.mark.parametrize("with_masses", [True, False])
+def test_fused_profile_matches_standalone_and_oracle(with_masses):
     torch = require_gpu()
     from paper_0904_3662_gb300 import ahf
     # every class: warp, CTA, clusters (and the multi-CTA class through a second context)
-    pop = synth.halo_batch(seed=41, n_halos=60, n_lo=100, n_hi=100_000, with_masses=True)
+    pop = synth.halo_batch(seed=41, n_halos=60, n_lo=100, n_hi=100_000, with_masses=with_masses)
     ctx = ahf.Context(0)
     parts = ahf.particles_from_population(pop)
     hal = ahf.halos_from_population(pop)
