@@ -344,6 +344,10 @@ def run_ahf(args):
     launches = 0
     barrier(world)
     torch.cuda.synchronize()
+    # steps back to back, as a caller streaming batches runs them: the host
+    # prepares step i + 1 while the device runs step i; the phase events stay
+    # off here (reading them needs a host wait per step)
+    ctx.set_option(ahf.OPT_TIMING, 0)
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
@@ -351,16 +355,22 @@ def run_ahf(args):
             starts[i].record(stream)
             step()
             ends[i].record(stream)
-            st = ctx.stats()                      # waits for this step's phase events
-            launches += st["launches"]
-            for k in range(ahf.N_PHASES):
-                if st["phase_ms"][k] >= 0:
-                    phase_ms[k] += st["phase_ms"][k]
-                    phase_n[k] += 1
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # the same steps again with per-phase events (one host wait per step) for
+    # the per-kernel durations the roofline uses
+    ctx.set_option(ahf.OPT_TIMING, 1)
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+        st = ctx.stats()
+        launches += st["launches"]
+        for k in range(ahf.N_PHASES):
+            if st["phase_ms"][k] >= 0:
+                phase_ms[k] += st["phase_ms"][k]
+                phase_n[k] += 1
     ms = float(np.mean(step_ms))
     ms_max = reduce_max(world, ms)
     total_units = reduce_sum(world, units)

@@ -152,8 +152,9 @@ int ahf_destroy(ahf_ctx *ctx);
  *   removed_iter device int32 per slot, nullable: -1 outside the gather sphere,
  *                0 bound, t > 0 removed in iteration t
  * Slots of a halo beyond offset + n_bound are left unspecified in bound_idx
- * and phi.  Errors: AHF_ERR_INVALID (NULL pointers, negative sizes, slots out
- * of range or shared, bad coord_type/precision/max_iter), AHF_ERR_NOMEM,
+ * and phi.  Errors: AHF_ERR_INVALID (NULL pointers, negative sizes, n_halos
+ * of 2^27 or more, slots out of range or shared, bad coord_type/precision/
+ * max_iter), AHF_ERR_NOMEM,
  * AHF_ERR_CUDA, AHF_ERR_TIMEOUT.  Outputs are undefined after an error. */
 int ahf_unbind_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
                      int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,

@@ -216,12 +216,21 @@ void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index
   const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
   double span = std::max(cm + std::fabs(H.radius), box);
   if (coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
+  // e: the smallest integer with 2^e > span + 1 (span + 1 >= 1 is finite)
   int e = 0;
-  while (e < 1100 && std::ldexp(1.0, e) <= span + 1.0) ++e;
+  std::frexp(span + 1.0, &e);
+  e = std::min(e, 1100);
   const int frac = std::max(-200, std::min(200, 60 - e));
   d.frac = frac;
+  bool exact = coord_type != AHF_COORD_F64 && box == 0.0;
+  for (int a = 0; a < 3; ++a) {
+    d.cf[a] = (float)d.c[a];
+    exact = exact && (double)d.cf[a] == d.c[a];
+  }
+  d.fast = exact ? 1 : 0;
+  // the fixed-point frame (used only off the fast path)
   d.boxfix = box > 0.0 ? (long long)std::llround(std::ldexp(box, frac)) : 0;
-  for (int a = 0; a < 3; ++a) d.cfix[a] = (long long)std::llround(std::ldexp(d.c[a], frac));
+  for (int a = 0; a < 3; ++a) d.cfix[a] = exact ? 0 : (long long)std::llround(std::ldexp(d.c[a], frac));
   const double R = H.radius;
   d.R2 = R * R;
   d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
@@ -230,21 +239,9 @@ void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index
   d.count = H.count;
   d.gbase = 0;
   d.index = index;
-  bool exact = coord_type != AHF_COORD_F64 && box == 0.0;
-  for (int a = 0; a < 3; ++a) {
-    d.cf[a] = (float)d.c[a];
-    exact = exact && (double)d.cf[a] == d.c[a];
-  }
-  d.fast = exact ? 1 : 0;
 }
 
 namespace {
-
-int ceil_log2(double x) {
-  int e = 0;
-  while (e < 1100 && std::ldexp(1.0, e) <= x) ++e;
-  return e;
-}
 
 struct Plan {
   std::vector<HaloDev> hd;     // reordered: class 0, 1, 2 (on-chip), then grid class
@@ -259,7 +256,7 @@ int validate(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, con
   if (n_halos < 0) return fail(AHF_ERR_INVALID, "n_halos < 0");
   if (n_halos > 0 && (!halos || !out || !bound_idx))
     return fail(AHF_ERR_INVALID, "halos, out and bound_idx must not be NULL");
-  if (n_halos > (int64_t)0x7fffffff) return fail(AHF_ERR_INVALID, "n_halos above 2^31-1");
+  if (n_halos >= ((int64_t)1 << 27)) return fail(AHF_ERR_INVALID, "n_halos above 2^27-1");
   if (p->n < 0) return fail(AHF_ERR_INVALID, "particle count < 0");
   if (p->n > 0 && (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz))
     return fail(AHF_ERR_INVALID, "coordinate or velocity array is NULL");
@@ -295,7 +292,8 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
     if (!std::isfinite(H.radius)) return fail(AHF_ERR_INVALID, "halo %lld: radius must be finite", (long long)h);
     if (H.count > 0) iv.emplace_back(H.offset, H.offset + H.count);
   }
-  std::sort(iv.begin(), iv.end());
+  // slots usually come in increasing order: sort only when they do not
+  if (!std::is_sorted(iv.begin(), iv.end())) std::sort(iv.begin(), iv.end());
   for (size_t i = 1; i < iv.size(); ++i)
     if (iv[i].first < iv[i - 1].second) return fail(AHF_ERR_INVALID, "haloes share candidate slots");
   return AHF_OK;
@@ -322,12 +320,16 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     cls[h] = k;
     P.n_class[k]++;
   }
+  // order: by class, largest first within a class (ties by input position),
+  // as one sort of packed keys (class | ~count | position)
+  std::vector<uint64_t> key((size_t)n_halos);
+  for (int64_t h = 0; h < n_halos; ++h) {
+    const uint64_t cnt = (uint64_t)std::min<int64_t>(halos[h].count, 0xffffffffll);
+    key[(size_t)h] = ((uint64_t)cls[h] << 60) | ((0xffffffffull - cnt) << 27) | (uint64_t)h;
+  }
+  std::sort(key.begin(), key.end());
   std::vector<int> order((size_t)n_halos);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    if (cls[a] != cls[b]) return cls[a] < cls[b];
-    return halos[a].count > halos[b].count;
-  });
+  for (int64_t k = 0; k < n_halos; ++k) order[(size_t)k] = (int)(key[(size_t)k] & ((1ull << 27) - 1));
   P.hd.resize((size_t)n_halos);
   long long gbase = 0;
   for (int64_t k = 0; k < n_halos; ++k) {

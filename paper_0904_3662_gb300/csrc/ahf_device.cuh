@@ -11,12 +11,28 @@
 // promise.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "ahf_internal.h"
 
 namespace ahf {
+
+// True the first time it is called for this kernel (its `mask`) on the
+// current device: function attributes persist for the process, so they are
+// set once rather than on every launch.
+inline bool first_use_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  return (mask.load(std::memory_order_acquire) & bit) == 0;
+}
+inline void mark_used_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) mask.fetch_or(1ull << dev, std::memory_order_release);
+}
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr uint32_t KEY_NONMEMBER = 0xffffffffu;   // sorts after every r >= 0
@@ -220,6 +236,80 @@ __device__ __forceinline__ void offset_of(const ParticlesDev& p, long long i, co
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = f32_from_fixcoord(f[k], H.frac);
   }
+}
+
+// One candidate's stored fields, loaded together so that a loop can issue
+// the loads of several candidates before using any of them (the particle
+// store is read-only for the whole call).
+template <int CT>
+struct Cand {
+  using E = typename std::conditional<CT == AHF_COORD_F64, double, float>::type;
+  E x, y, z, vx, vy, vz, m;
+};
+
+template <int CT>
+__device__ __forceinline__ void load_cand(const ParticlesDev& p, long long i, Cand<CT>& c) {
+  using E = typename Cand<CT>::E;
+  c.x = __ldg((const E*)p.x + i);
+  c.y = __ldg((const E*)p.y + i);
+  c.z = __ldg((const E*)p.z + i);
+  c.vx = __ldg((const E*)p.vx + i);
+  c.vy = __ldg((const E*)p.vy + i);
+  c.vz = __ldg((const E*)p.vz + i);
+  c.m = p.m ? __ldg((const E*)p.m + i) : (E)0;
+}
+
+template <int CT>
+__device__ __forceinline__ float cand_mass(const ParticlesDev& p, const Cand<CT>& c) {
+  return p.m ? (float)c.m : p.m0f;
+}
+
+template <int CT>
+__device__ __forceinline__ void cand_velocity(const Cand<CT>& c, float v[3]) {
+  v[0] = (float)c.vx;
+  v[1] = (float)c.vy;
+  v[2] = (float)c.vz;
+}
+
+// offset_of from loaded fields (same arithmetic, same result).
+template <int CT>
+__device__ __forceinline__ void cand_offset(const Cand<CT>& c, const HaloDev& H, float d[3], long long f[3]) {
+  if (CT != AHF_COORD_F64 && H.fast) {
+    d[0] = __fsub_rn((float)c.x, H.cf[0]);
+    d[1] = __fsub_rn((float)c.y, H.cf[1]);
+    d[2] = __fsub_rn((float)c.z, H.cf[2]);
+  } else {
+    if (CT == AHF_COORD_F64) {
+      f[0] = wrap_fix(fixcoord_from_double((double)c.x, H.frac) - H.cfix[0], H.boxfix);
+      f[1] = wrap_fix(fixcoord_from_double((double)c.y, H.frac) - H.cfix[1], H.boxfix);
+      f[2] = wrap_fix(fixcoord_from_double((double)c.z, H.frac) - H.cfix[2], H.boxfix);
+    } else {
+      f[0] = wrap_fix(fixcoord_from_float((float)c.x, H.frac) - H.cfix[0], H.boxfix);
+      f[1] = wrap_fix(fixcoord_from_float((float)c.y, H.frac) - H.cfix[1], H.boxfix);
+      f[2] = wrap_fix(fixcoord_from_float((float)c.z, H.frac) - H.cfix[2], H.boxfix);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = f32_from_fixcoord(f[k], H.frac);
+  }
+}
+
+// member_of from loaded fields (same decision).
+template <int CT>
+__device__ __forceinline__ bool cand_member(const Cand<CT>& c, const HaloDev& H, const float df[3],
+                                            const long long f[3]) {
+  const float r2f = fmaf(df[2], df[2], fmaf(df[1], df[1], df[0] * df[0]));
+  if (r2f < H.R2lo) return true;
+  if (r2f > H.R2hi) return false;
+  double dd[3];
+  if (CT != AHF_COORD_F64 && H.fast) {
+    dd[0] = (double)(float)c.x - (double)H.cf[0];
+    dd[1] = (double)(float)c.y - (double)H.cf[1];
+    dd[2] = (double)(float)c.z - (double)H.cf[2];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dd[k] = scale_pow2d((double)f[k], -H.frac);
+  }
+  return dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] <= H.R2;
 }
 
 // Member of the gather sphere: |d| <= R decided in FP64 arithmetic.  The

@@ -100,6 +100,7 @@ struct Smem {
   int c_removed, c_band;
   int k_first;
   float vb[3];
+  double rvir;                  // emit: the record's r_vir, for the profile rows
   uint32_t dtot[256];
   uint32_t dpre[256];
 };
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     const int hq = *Cl<CS>::at(&X.halo, 0);
     Cl<CS>::sync();
     if (hq >= L.n_halos) break;
-    const HaloDev H = L.halos[hq];
+    const HaloDev& H = L.halos[hq];
     const int n_cand = (int)H.count;
     const int chunk = n_cand > 0 ? (n_cand + CS - 1) / CS : 1;
     if (chunk > CAP) {    // the scheduler never does this; report, do not overrun
@@ -323,15 +324,17 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         }
         uint32_t key = KEY_NONMEMBER;
         if (ok) {
+          Cand<CT> c;
+          load_cand<CT>(L.p, pi, c);
           long long f[3];
           float df[3];
-          offset_of<CT>(L.p, pi, H, df, f);
-          if (member_of<CT>(L.p, pi, H, df, f)) {
+          cand_offset<CT>(c, H, df, f);
+          if (cand_member<CT>(c, H, df, f)) {
             const float r = radius_of(df);
             key = __float_as_uint(r);
-            const float m = load_mass<CT>(L.p, pi);
+            const float m = cand_mass<CT>(L.p, c);
             float v[3];
-            load_velocity<CT>(L.p, pi, v);
+            cand_velocity<CT>(c, v);
             mxm = max(mxm, __float_as_uint(fabsf(m)));
             mxr = max(mxr, __float_as_uint(fabsf(m * rinv_of(r, P.r_soft_f))));
 #pragma unroll
@@ -339,7 +342,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
             ++nmem;
           }
         }
-        if (key == KEY_NONMEMBER && L.out.removed_iter) L.out.removed_iter[slot] = -1;
+        // members start bound (removal overwrites with its iteration)
+        if (L.out.removed_iter) L.out.removed_iter[slot] = key == KEY_NONMEMBER ? -1 : 0;
         kA[i] = key;
         vA[i] = (uint32_t)j;
         orb |= key;
@@ -401,7 +405,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     float* wy = ex1;
     float* wz = ex2;
 
-    // ---- fill: sorted SoA and the exact sum m v of the members ----
+    // ---- fill: m and w = v + H d in the radial order, and the exact sum m v
+    // of the members (the sorted candidates re-read from the store, mostly L2)
+    const int p0 = tid * ipt;
     {
       long long smv[3] = {0, 0, 0};
       for (int p = tid; p < nmem_loc; p += NT) {
@@ -443,7 +449,6 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     __syncthreads();
 
     // per-thread exact sums of m, m/r and the alive count over its run
-    const int p0 = tid * ipt;
     long long tm_own = 0, tr_own = 0, tc_own = 0;
     for (int k = 0; k < ipt; ++k) {
       const int p = p0 + k;
@@ -484,6 +489,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       const float vb0 = S.vb[0], vb1 = S.vb[1], vb2 = S.vb[2];
       long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
+      uint32_t rmask = 0;                 // this thread's removals (bit k: position p0 + k)
+#pragma unroll 4
       for (int k = 0; k < ipt; ++k) {
         const int p = p0 + k;
         if (p < nmem_loc) {
@@ -500,23 +507,30 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
             if (fabsf(u2 - two_phi) < P.band_f * two_phi) ++nband;
             if (u2 > two_phi) {
               mm[q] = -m;
-              ++nrem;
-              const int j = (int)jj[q];
-              const long long slot = H.offset + j;
-              const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-              float v[3];
-              load_velocity<CT>(L.p, pi, v);
+              rmask |= 1u << k;
               rm += mfix;
               rq += rfix;
-              rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
-              rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
-              rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);
-              if (L.out.removed_iter) L.out.removed_iter[slot] = n_iter;
             }
             tm += mfix;
             tr += rfix;
           }
         }
+      }
+      // the removed: exact m v from the stored velocity, and their record
+      for (uint32_t b = rmask; b; b &= b - 1) {
+        const int k = __ffs(b) - 1;
+        const int q = sw(p0 + k, mask);
+        const float m = -mm[q];
+        const int j = (int)jj[q];
+        const long long slot = H.offset + j;
+        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+        float v[3];
+        load_velocity<CT>(L.p, pi, v);
+        rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
+        rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
+        rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);
+        if (L.out.removed_iter) L.out.removed_iter[slot] = n_iter;
+        ++nrem;
       }
       tm_own -= rm;
       tr_own -= rq;
@@ -601,7 +615,6 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
             const long long dst = H.offset + C_pre + tl;
             L.out.bound_idx[dst] = pi;
             if (L.out.phi) ((float*)L.out.phi)[dst] = phi;
-            if (L.out.removed_iter) L.out.removed_iter[slot] = 0;
             const int kq = sw((int)tl, mask);
             rc[kq] = r;
             mc[kq] = tm + mfix;
@@ -662,39 +675,45 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       // the CTA holding the crossing particle writes the record
       const int k = S.k_first;
       const bool owner = nb > 0 ? (k >= C_pre && k < C_pre + C_loc) : rank == 0;
-      if (tid == 0 && owner) {
-        ahf_result R;
-        R.n_bound = nb;
-        R.n_member = n_mem;
-        R.part_iter = part_iter;
-        R.n_band = n_band;
-        R.n_iter = n_iter;
-        R.k_vir = -1;
-        R.m_vir = 0.0;
-        R.r_vir = 0.0;
-        if (nb > 0) {
-          const int kl = (int)(k - C_pre);
-          // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
-          const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(kl, mask)], s_m);
-          const double rk = (double)rc[sw(kl, mask)];
-          if (k == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
-          if (mk < P.crit * rk * rk * rk) {
-            status |= AHF_HALO_RVIR_NONE;
-          } else {
-            R.k_vir = k;
-            R.m_vir = mk;
-            R.r_vir = cbrt(mk / P.crit);
+      if (owner) {
+        // the record, its FP64 parts spread over the first thread of four
+        // warps (one per SM sub-partition): the virial pair, and one bulk
+        // velocity component each
+        ahf_result* R = L.out.res + H.index;
+        if (tid == 0) {
+          long long kv = -1;
+          double mv = 0.0, rv = 0.0;
+          if (nb > 0) {
+            const int kl = (int)(k - C_pre);
+            // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
+            const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(kl, mask)], s_m);
+            const double rk = (double)rc[sw(kl, mask)];
+            if (k == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
+            if (mk < P.crit * rk * rk * rk) {
+              status |= AHF_HALO_RVIR_NONE;
+            } else {
+              kv = k;
+              mv = mk;
+              rv = cbrt(mk / P.crit);
+            }
           }
-          const double mt = double_from_fix(S.c_tot[0], s_m);
-          for (int c = 0; c < 3; ++c) R.vbulk[c] = double_from_fix(S.mv[c], s_v) / mt;
-        } else {
-          R.vbulk[0] = R.vbulk[1] = R.vbulk[2] = 0.0;
-        }
-        R.status = status;
-        L.out.res[H.index] = R;
-        if constexpr (CS > 1) {
-          X.rvir = R.r_vir;
-          X.has_rvir = 1;
+          R->n_bound = nb;
+          R->n_member = n_mem;
+          R->part_iter = part_iter;
+          R->n_band = n_band;
+          R->k_vir = kv;
+          R->n_iter = n_iter;
+          R->status = status;
+          R->m_vir = mv;
+          R->r_vir = rv;
+          S.rvir = rv;
+          if constexpr (CS > 1) {
+            X.rvir = rv;
+            X.has_rvir = 1;
+          }
+        } else if (tid == 32 || tid == 64 || tid == 96) {
+          const int c = tid / 32 - 1;
+          R->vbulk[c] = nb > 0 ? double_from_fix(S.mv[c], s_v) / double_from_fix(S.c_tot[0], s_m) : 0.0;
         }
       }
       if constexpr (CS > 1) {
@@ -764,13 +783,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       }
       if constexpr (CS == 1) {
         if (L.rows.prof) {
-          double r_vir = 0.0;
-          if (nb > 0) {
-            const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(k, mask)], s_m);
-            const double rk = (double)rc[sw(k, mask)];
-            if (!(mk < P.crit * rk * rk * rk)) r_vir = cbrt(mk / P.crit);
-          }
-          profile_rows(L.rows, H.index, rc, mc, [&](long long kk) { return sw((int)kk, mask); }, nb, r_vir, s_m,
+          __syncthreads();                        // S.rvir
+          profile_rows(L.rows, H.index, rc, mc, [&](long long kk) { return sw((int)kk, mask); }, nb, S.rvir, s_m,
                        P.G, unim ? &L.p.m0 : nullptr, tid, NT);
         }
       }
@@ -798,16 +812,20 @@ template <int NT, int CAP, int CT, int CS>
 cudaError_t launch_variant(const OnchipLaunch& L, int grid, cudaStream_t s) {
   auto k = unbind_kernel<NT, CAP, CT, CS>;
   constexpr size_t smem = dyn_bytes<NT, CAP>();
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if constexpr (CS == 1) {
-    k<<<grid, NT, smem, s>>>(L);
-    return cudaGetLastError();
-  } else {
+  static std::atomic<unsigned long long> attrs_set{0};
+  if (first_use_on_device(attrs_set)) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     if (CS > 8) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
+    mark_used_on_device(attrs_set);
+  }
+  if constexpr (CS == 1) {
+    k<<<grid, NT, smem, s>>>(L);
+    return cudaGetLastError();
+  } else {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);

@@ -402,8 +402,12 @@ template <int CT>
 cudaError_t launch_ct(const OnchipLaunch& L, int grid, cudaStream_t s) {
   auto k = warp_kernel<CT>;
   constexpr size_t smem = WARP_BYTES * WPB;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static std::atomic<unsigned long long> attrs_set{0};
+  if (first_use_on_device(attrs_set)) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mark_used_on_device(attrs_set);
+  }
   k<<<grid, WPB * 32, smem, s>>>(L);
   return cudaGetLastError();
 }
