@@ -267,27 +267,34 @@ def unbind_population(pop, params: Params, halos=None, member_idx=None,
 
 
 def _worker(args):
-    pop, params = args
-    out = unbind_population(pop, params)
-    return [(o["n_iter"], o["part_iter"], o["order"].shape[0]) for _, o in sorted(out.items())]
+    import time
+    pop, params, n_bins, r_min_frac = args
+    t0 = time.perf_counter()
+    out = unbind_population(pop, params, n_bins=n_bins, r_min_frac=r_min_frac)
+    dt = time.perf_counter() - t0
+    return [(o["n_iter"], o["part_iter"], o["order"].shape[0]) for _, o in sorted(out.items())], dt
 
 
-def unbind_population_parallel(pop, params: Params, halos, n_workers):
+def unbind_population_parallel(pop, params: Params, halos, n_workers, n_bins=0, r_min_frac=0.01, chunks=None):
     """The oracle over haloes spread across n_workers spawned processes
-    (the i-th listed halo goes to worker i % n_workers).  Returns
-    {h: (n_iter, part_iter, n_bound)}.  Used only to time the oracle as a
+    (the i-th listed halo goes to worker i % n_workers, unless `chunks`
+    gives each worker's haloes).  Returns
+    ({h: (n_iter, part_iter, n_bound)}, the longest worker's compute time in
+    seconds, process start-up excluded).  Used only to time the oracle as a
     CPU baseline; the arithmetic is unbind_population's."""
     import multiprocessing as mp
     halos = list(halos)
-    chunks = [c for c in (halos[i::n_workers] for i in range(n_workers)) if c]
+    if chunks is None:
+        chunks = [halos[i::n_workers] for i in range(n_workers)]
+    chunks = [list(c) for c in chunks if len(c)]
     ctx = mp.get_context("spawn")
     res = {}
     with ctx.Pool(len(chunks)) as pool:
-        parts = pool.map(_worker, [(_subset(pop, c), params) for c in chunks])
-    for c, part in zip(chunks, parts):
+        parts = pool.map(_worker, [(_subset(pop, c), params, n_bins, r_min_frac) for c in chunks])
+    for c, (part, _) in zip(chunks, parts):
         for h, stats in zip(c, part):
             res[h] = stats
-    return res
+    return res, max(dt for _, dt in parts)
 
 
 def _subset(pop, halos):

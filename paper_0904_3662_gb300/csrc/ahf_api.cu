@@ -66,6 +66,15 @@ struct Bump {
 
 void ahf::set_last_error_static(const char* msg) { g_last_ptr = msg; }
 
+void ahf::profile_bin_tables(int n, double f, double* t) {
+  for (int b = 0; b < n; ++b) t[b] = std::pow(f, 1.0 - (double)b / (double)n);
+  for (int b = 0; b < n; ++b) {
+    const double f0 = t[b], f1 = b + 1 < n ? t[b + 1] : 1.0;
+    t[n + b] = 1.0 / (4.0 * M_PI / 3.0 * (f1 * f1 * f1 - f0 * f0 * f0));
+    t[2 * n + b] = 1.0 / f1;
+  }
+}
+
 int ahf::set_last_error_fmt(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -474,7 +483,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
     int* queues = B.take<int>(16);
-    double* fac = B.take<double>(prof ? (size_t)n_bins : 0);
+    double* fac = B.take<double>(prof ? 3 * (size_t)n_bins : 0);
     if (G) dfac = fac;
     if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (unsigned long long*)(queues + 10); }
     if (n_grid) {
@@ -506,7 +515,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
-  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 8 * (size_t)n_bins + 256 : 0) +
+  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 24 * (size_t)n_bins + 256 : 0) +
                           (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
@@ -527,9 +536,9 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   AHF_CUDA(stage(hd, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos));
   AHF_CUDA(cudaMemsetAsync(queues, 0, 16 * sizeof(int), s));
   if (prof) {
-    std::vector<double> factor((size_t)n_bins);
-    for (int b = 0; b < n_bins; ++b) factor[(size_t)b] = std::pow(r_min_frac, 1.0 - (double)b / (double)n_bins);
-    AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * (size_t)n_bins));
+    std::vector<double> tab(3 * (size_t)n_bins);
+    profile_bin_tables(n_bins, r_min_frac, tab.data());
+    AHF_CUDA(stage(dfac, tab.data(), sizeof(double) * tab.size()));
   }
 
   OutputsDev O;
@@ -642,15 +651,15 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   const int n_chunks = (int)chunk_halo.size();
   int n_multi = 0;
   for (int64_t h = 0; h < n_halos; ++h) n_multi += halo_chunk0[(size_t)h + 1] - halo_chunk0[(size_t)h] > 1;
-  std::vector<double> factor((size_t)n_bins);
-  for (int b = 0; b < n_bins; ++b) factor[(size_t)b] = std::pow(r_min_frac, 1.0 - (double)b / (double)n_bins);
+  std::vector<double> factor(3 * (size_t)n_bins);
+  profile_bin_tables(n_bins, r_min_frac, factor.data());
   double* dfac = nullptr;
   auto layout = [&](Bump& B, ProfileLaunch* L, int** h0) {
     HaloDev* d = B.take<HaloDev>((size_t)n_halos);
     int* ch = B.take<int>((size_t)n_chunks + 1);
     long long* cs = B.take<long long>((size_t)n_chunks + 1);
     int* hc0 = B.take<int>((size_t)n_halos + 1);
-    double* fac = B.take<double>((size_t)n_bins);
+    double* fac = B.take<double>(3 * (size_t)n_bins);
     long long* acc = B.take<long long>((size_t)n_chunks * (2 + 2 * (size_t)n_bins) + 1);
     if (L) { L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0; dfac = fac; }
   };
@@ -677,7 +686,7 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   AHF_CUDA(stage(L.chunk_halo, chunk_halo.data(), sizeof(int) * (size_t)n_chunks));
   AHF_CUDA(stage(L.chunk_start, chunk_start.data(), sizeof(long long) * (size_t)n_chunks));
   AHF_CUDA(stage(hc0, halo_chunk0.data(), sizeof(int) * ((size_t)n_halos + 1)));
-  AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * (size_t)n_bins));
+  AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * factor.size()));
   if ((rc = pin_release(c, s))) return rc;
   L.edge_factor = dfac;
   L.n_multi = n_multi;

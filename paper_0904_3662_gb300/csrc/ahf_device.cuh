@@ -373,6 +373,18 @@ __device__ __forceinline__ bool le_edge(float r, float ef, double e) {
   return (double)r <= e;
 }
 
+// Profile columns from the per-bin tables (see profile_bin_tables): the shell
+// density M_bin / V_bin with V_bin = r_out^3 (4 pi / 3)(f_{b+1}^3 - f_b^3), and
+// v_circ = sqrt(G M(<= e_{b+1}) / e_{b+1}) with e_{b+1} = r_out f_{b+1}; the
+// divisions by r_out are one reciprocal per halo.
+__device__ __forceinline__ double shell_density(double m_bin, double inv_r3, const double* tab, int n, int b) {
+  return (m_bin * inv_r3) * tab[n + b];
+}
+__device__ __forceinline__ double circular_velocity(double G, double m_in, double inv_r, const double* tab, int n,
+                                                    int b) {
+  return sqrt(((G * m_in) * inv_r) * tab[2 * n + b]);
+}
+
 // Log-radial profile rows of one halo from its compacted bound set held on
 // chip: radii rc[idx(k)] ascending and inclusive exact masses mc[idx(k)]
 // (scale 2^-s_m), k < nb.  Row b covers (e_b, e_{b+1}], e_b = r_out f^(1-b/n),
@@ -388,6 +400,8 @@ __device__ void profile_rows(const ProfileRows& Q, int h, const float* rc, const
     return;
   }
   const double r_out = r_vir > 0.0 ? r_vir : (double)rc[idx(nb - 1)];
+  const double inv_r = 1.0 / r_out;
+  const double inv_r3 = inv_r * inv_r * inv_r;
   auto count_le = [&](double e) {
     const float ef = (float)e;
     long long lo = 0, hi = nb;            // first k with rc[k] > e
@@ -416,8 +430,8 @@ __device__ void profile_rows(const ProfileRows& Q, int h, const float* rc, const
     }
     out[4 * b + 0] = (double)(c1 - c0);
     out[4 * b + 1] = M1;
-    out[4 * b + 2] = Mshell / (4.0 * 3.14159265358979323846 / 3.0 * (e1 * e1 * e1 - e0 * e0 * e0));
-    out[4 * b + 3] = sqrt(G * M1 / e1);
+    out[4 * b + 2] = shell_density(Mshell, inv_r3, Q.factor, n, b);
+    out[4 * b + 3] = circular_velocity(G, M1, inv_r, Q.factor, n, b);
   }
 }
 

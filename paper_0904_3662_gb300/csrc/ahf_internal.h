@@ -100,9 +100,15 @@ int set_last_error_fmt(int code, const char *fmt, ...);
 // ---- launchers (defined in the .cu files) -----------------------------------
 
 // Profile rows requested from the unbinding kernels themselves.
+// Per-bin tables of a profile call (3 n doubles, from profile_bin_tables):
+//   [0, n)   f_b = f^(1 - b/n), the edge e_b = r_out f_b (e_n = r_out)
+//   [n, 2n)  1 / (4 pi / 3 (f_{b+1}^3 - f_b^3)): shell volume = r_out^3 / this
+//   [2n, 3n) 1 / f_{b+1}
+void profile_bin_tables(int n_bins, double r_min_frac, double *t);
+
 struct ProfileRows {
   double *prof;              // [n_halos][n_bins][4] (caller order), NULL = none
-  const double *factor;      // f^(1 - b/n), b = 0..n-1
+  const double *factor;      // the bin tables (3 n_bins doubles)
   int n_bins;
 };
 
@@ -187,7 +193,7 @@ struct ProfileLaunch {
   long long *chunk_acc;    // workspace: per chunk (inner mass, inner count, per bin count and mass)
   int *chunk_halo;         // chunk -> halo
   long long *chunk_start;  // chunk -> first position in the halo's bound list
-  const double *edge_factor;  // f^(1 - b/n), b = 0..n-1
+  const double *edge_factor;  // the bin tables (3 n_bins doubles)
   int n_chunks;
   int n_multi;             // haloes held by more than one chunk
 };

@@ -750,6 +750,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           Cl<CS>::sync();
           if (rank == 0) {
             double* out = L.rows.prof + (size_t)H.index * n * 4;
+            const double inv_r = 1.0 / r_out;
+            const double inv_r3 = inv_r * inv_r * inv_r;
             for (int b = tid; b < n; b += NT) {
               long long c0 = 0, c1 = 0, f0 = 0, f1 = 0;
               for (int r2 = 0; r2 < CS; ++r2) {
@@ -763,8 +765,6 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
                 out[4 * b + 0] = out[4 * b + 1] = out[4 * b + 2] = out[4 * b + 3] = 0.0;
                 continue;
               }
-              const double e0 = r_out * L.rows.factor[b];
-              const double e1 = b + 1 == n ? r_out : r_out * L.rows.factor[b + 1];
               double M1, Ms;
               if (unim) {
                 M1 = (double)c1 * L.p.m0;
@@ -775,8 +775,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
               }
               out[4 * b + 0] = (double)(c1 - c0);
               out[4 * b + 1] = M1;
-              out[4 * b + 2] = Ms / (4.0 * 3.14159265358979323846 / 3.0 * (e1 * e1 * e1 - e0 * e0 * e0));
-              out[4 * b + 3] = sqrt(P.G * M1 / e1);
+              out[4 * b + 2] = shell_density(Ms, inv_r3, L.rows.factor, n, b);
+              out[4 * b + 3] = circular_velocity(P.G, M1, inv_r, L.rows.factor, n, b);
             }
           }
         }

@@ -55,6 +55,8 @@ __device__ void write_rows(const ProfileLaunch& L, int h, const double* e, const
   __shared__ double carry;
   const int n = L.n_bins;
   double* out = L.prof + (size_t)h * n * 4;
+  const double inv_r = 1.0 / e[n];
+  const double inv_r3 = inv_r * inv_r * inv_r;
   if (threadIdx.x == 0) carry = inner;
   __syncthreads();
   for (int b0 = 0; b0 < n; b0 += PT) {
@@ -63,11 +65,10 @@ __device__ void write_rows(const ProfileLaunch& L, int h, const double* e, const
     const double inc = block_scan_incl(mb, wsum);
     const double run = carry + inc;
     if (b < n) {
-      const double lo = e[b], hi = e[b + 1];
       out[4 * b + 0] = (double)cnt[b];
       out[4 * b + 1] = run;
-      out[4 * b + 2] = mb / (4.0 * M_PI / 3.0 * (hi * hi * hi - lo * lo * lo));
-      out[4 * b + 3] = sqrt(L.prm.G * run / hi);
+      out[4 * b + 2] = shell_density(mb, inv_r3, L.edge_factor, n, b);
+      out[4 * b + 3] = circular_velocity(L.prm.G, run, inv_r, L.edge_factor, n, b);
     }
     __syncthreads();
     if (threadIdx.x == PT - 1) carry = run;

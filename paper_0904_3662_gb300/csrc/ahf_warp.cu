@@ -353,16 +353,12 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       }
     }
     kf = (int)__reduce_min_sync(FULL_MASK, (unsigned)kf);
+    // the record: lane 0 the virial pair, lanes 1-3 one bulk velocity
+    // component each (FP64 work in parallel rather than in sequence)
+    double r_vir_l = 0.0;
     if (lane == 0) {
-      ahf_result R;
-      R.n_bound = nb;
-      R.n_member = n_mem;
-      R.part_iter = part_iter;
-      R.n_band = n_band;
-      R.n_iter = n_iter;
-      R.k_vir = -1;
-      R.m_vir = 0.0;
-      R.r_vir = 0.0;
+      long long kv = -1;
+      double mvir = 0.0;
       if (nb > 0) {
         // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
         const double mk = unim ? (double)(kf + 1) * L.p.m0 : double_from_fix(mc[sw(kf, mask)], s_m);
@@ -371,26 +367,27 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
         if (mk < P.crit * rk * rk * rk) {
           status |= AHF_HALO_RVIR_NONE;
         } else {
-          R.k_vir = kf;
-          R.m_vir = mk;
-          R.r_vir = cbrt(mk / P.crit);
+          kv = kf;
+          mvir = mk;
+          r_vir_l = cbrt(mk / P.crit);
         }
-        const double mtd = double_from_fix(M_tot, s_m);
-        for (int c = 0; c < 3; ++c) R.vbulk[c] = double_from_fix(mv[c], s_v) / mtd;
-      } else {
-        R.vbulk[0] = R.vbulk[1] = R.vbulk[2] = 0.0;
       }
-      R.status = status;
-      L.out.res[H.index] = R;
+      ahf_result* R = L.out.res + H.index;
+      R->n_bound = nb;
+      R->n_member = n_mem;
+      R->part_iter = part_iter;
+      R->n_band = n_band;
+      R->k_vir = kv;
+      R->n_iter = n_iter;
+      R->status = status;
+      R->m_vir = mvir;
+      R->r_vir = r_vir_l;
+    } else if (lane < 4) {
+      const long long m = lane == 1 ? mv[0] : (lane == 2 ? mv[1] : mv[2]);
+      L.out.res[H.index].vbulk[lane - 1] = nb > 0 ? double_from_fix(m, s_v) / double_from_fix(M_tot, s_m) : 0.0;
     }
     if (L.rows.prof) {
-      // r_vir as the record has it (lane 0 computed it; recompute identically)
-      double r_vir = 0.0;
-      if (nb > 0) {
-        const double mk = unim ? (double)(kf + 1) * L.p.m0 : double_from_fix(mc[sw(kf, mask)], s_m);
-        const double rk = (double)rc[sw(kf, mask)];
-        if (!(mk < P.crit * rk * rk * rk)) r_vir = cbrt(mk / P.crit);
-      }
+      const double r_vir = __shfl_sync(FULL_MASK, r_vir_l, 0);
       profile_rows(L.rows, H.index, rc, mc, [&](long long k) { return sw((int)k, mask); }, nb, r_vir, s_m, P.G,
                    unim ? &L.p.m0 : nullptr, lane, 32);
     }

@@ -114,3 +114,32 @@ def _virial_band_ok(o, r, op, msg):
     raise AssertionError((msg, "virial crossing differs outside the band", k, o["k_vir"], int(r["status"]),
                           o["status"]))
 
+
+def check_profiles(pop, prm, res, prof, n_bins, f, halos=None):
+    """Profile rows against the oracle's: counts may move between
+    neighbouring bins only for particles within 2e-5 of an edge; masses
+    accordingly; shell density and v_circ to 1e-5 where no particle is on an
+    edge."""
+    hs = range(pop.n_halos) if halos is None else halos
+    ref = O.unbind_population(pop, oracle_params(prm), halos=hs, forced=None, n_bins=n_bins, r_min_frac=f)
+    for h in hs:
+        o = ref[h]
+        gp = prof[h]
+        if o["order"].shape[0] == 0:
+            assert np.all(gp == 0.0)
+            continue
+        r_out = float(res[h]["r_vir"]) if res[h]["r_vir"] > 0 else float(o["r"][-1])
+        edges = r_out * f ** (1.0 - np.arange(n_bins + 1) / n_bins)
+        edges[-1] = r_out
+        near = np.zeros(n_bins, dtype=np.int64)
+        for b in range(n_bins):
+            for e in (edges[b], edges[b + 1]):
+                near[b] += int(np.sum(np.abs(o["r"] / e - 1.0) < 2e-5))
+        # counts may move between neighbouring bins only for particles on an edge
+        assert np.all(np.abs(gp[:, 0] - o["profile"][:, 0]) <= near), (h, gp[:, 0], o["profile"][:, 0])
+        mp = float(o["m"].max())
+        cum_near = np.cumsum(near)
+        assert np.all(np.abs(gp[:, 1] - o["profile"][:, 1]) <= cum_near * mp + 1e-9 * o["profile"][:, 1] + 1e-6)
+        ok = near == 0
+        np.testing.assert_allclose(gp[ok, 2], o["profile"][ok, 2], rtol=1e-5)
+        np.testing.assert_allclose(gp[ok, 3], o["profile"][ok, 3], rtol=1e-5)

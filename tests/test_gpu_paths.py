@@ -9,7 +9,7 @@ import pytest
 from oracle import ahf_oracle as O
 from paper_0904_3662_gb300 import synth
 from tests.gpu_util import require_gpu, run_gpu
-from tests.parity import compare, oracle_params
+from tests.parity import check_profiles as _check_profiles, compare, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -170,31 +170,6 @@ def test_host_entry_point_with_profile():
     out = ctx.unbind_batch_host(parts, ahf.halos_from_population(pop), prm, n_bins=16, r_min_frac=0.02)
     compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
     _check_profiles(pop, prm, out["res"], out["prof"], 16, 0.02)
-
-
-def _check_profiles(pop, prm, res, prof, n_bins, f):
-    ref = O.unbind_population(pop, oracle_params(prm), forced=None, n_bins=n_bins, r_min_frac=f)
-    for h in range(pop.n_halos):
-        o = ref[h]
-        gp = prof[h]
-        if o["order"].shape[0] == 0:
-            assert np.all(gp == 0.0)
-            continue
-        r_out = float(res[h]["r_vir"]) if res[h]["r_vir"] > 0 else float(o["r"][-1])
-        edges = r_out * f ** (1.0 - np.arange(n_bins + 1) / n_bins)
-        edges[-1] = r_out
-        near = np.zeros(n_bins, dtype=np.int64)
-        for b in range(n_bins):
-            for e in (edges[b], edges[b + 1]):
-                near[b] += int(np.sum(np.abs(o["r"] / e - 1.0) < 2e-5))
-        # counts may move between neighbouring bins only for particles on an edge
-        assert np.all(np.abs(gp[:, 0] - o["profile"][:, 0]) <= near), (h, gp[:, 0], o["profile"][:, 0])
-        mp = float(o["m"].max())
-        cum_near = np.cumsum(near)
-        assert np.all(np.abs(gp[:, 1] - o["profile"][:, 1]) <= cum_near * mp + 1e-9 * o["profile"][:, 1] + 1e-6)
-        ok = near == 0
-        np.testing.assert_allclose(gp[ok, 2], o["profile"][ok, 2], rtol=1e-5)
-        np.testing.assert_allclose(gp[ok, 3], o["profile"][ok, 3], rtol=1e-5)
 
 
 def test_profile_batch_device():
