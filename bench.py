@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", dest="graphs", action="store_false",
+                    help="plain launches instead of CUDA graph replay in the timed steps")
     return ap.parse_args()
 
 
@@ -180,8 +182,8 @@ class ClockSampler:
 
 def class_of(counts):
     """Size class of each halo as the library's scheduler assigns it:
-    0 warp, 1-3 single-CTA shared-memory variants, 4-6 clusters of 4/8/16
-    CTAs, 7 the multi-CTA class."""
+    0 warp, 1-3 single-CTA shared-memory variants, 4-7 clusters of 2/4/8/16
+    CTAs, 8 the multi-CTA class."""
     from paper_0904_3662_gb300 import ahf
     caps = ahf.VARIANT_CAPS
     cls = np.full(counts.shape[0], len(caps))
@@ -198,7 +200,8 @@ def phase_bytes(pop, res, cls):
     nb = res["n_bound"].astype(np.float64)
     nm = res["n_member"].astype(np.float64)
     pit = res["part_iter"].astype(np.float64)
-    nv = 7
+    from paper_0904_3662_gb300 import ahf
+    nv = len(ahf.VARIANT_CAPS)
     out = np.zeros(nv + 4)
     for v in range(nv):
         s = cls == v
@@ -225,8 +228,8 @@ _DEV = "paper_0904_3662_gb300/csrc/ahf_device.cuh"
 _ONCHIP = ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", _DEV]
 _GRID = ["paper_0904_3662_gb300/csrc/ahf_grid.cu", _DEV]
 PHASE_SOURCES = {0: ["paper_0904_3662_gb300/csrc/ahf_warp.cu", _DEV], 1: _ONCHIP, 2: _ONCHIP, 3: _ONCHIP,
-                 4: _ONCHIP, 5: _ONCHIP, 6: _ONCHIP, 7: _GRID, 8: _GRID, 9: _GRID,
-                 10: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", _DEV]}
+                 4: _ONCHIP, 5: _ONCHIP, 6: _ONCHIP, 7: _ONCHIP, 8: _GRID, 9: _GRID, 10: _GRID,
+                 11: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", _DEV]}
 
 
 def measured_traffic(phase, workload):
@@ -367,8 +370,14 @@ def run_ahf(args):
     torch.cuda.synchronize()
     # steps back to back, as a caller streaming batches runs them: the host
     # prepares step i + 1 while the device runs step i; the phase events stay
-    # off here (reading them needs a host wait per step)
+    # off here (reading them needs a host wait per step).  The batch repeats,
+    # so its launches run as a CUDA graph (captured in an untimed step)
     ctx.set_option(ahf.OPT_TIMING, 0)
+    ctx.set_option(ahf.OPT_GRAPHS, 1 if args.graphs else 0)
+    for _ in range(2):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
@@ -382,6 +391,7 @@ def run_ahf(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     # the same steps again with per-phase events (one host wait per step) for
     # the per-kernel durations the roofline uses
+    ctx.set_option(ahf.OPT_GRAPHS, 0)
     ctx.set_option(ahf.OPT_TIMING, 1)
     for i in range(args.steps):
         flush.zero_()
@@ -414,7 +424,8 @@ def run_ahf(args):
             "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
             "config": {"workload": desc, "halos": pop.n_halos, "particles": pop.n_particles,
                        "particle_iterations_per_step": units, "l2": "flushed (256 MiB write) between steps",
-                       "parallelism": f"replicas x{world}, haloes independent, no collective"},
+                       "parallelism": f"replicas x{world}, haloes independent, no collective",
+                       "launch": "CUDA graph replay (AHF_OPT_GRAPHS)" if args.graphs else "plain launches"},
             "gpu_launches": launches, "roofline": roofline,
             "timed_wall_s": t_wall}
     clocks = clk.summary()
@@ -484,16 +495,25 @@ def time_e2e(ctx, pop, hal, prm, units, args):
     es = hp.x.dtype.itemsize
     h2d = 6 * n * es + (n * es if pop.m is not None else 0) + hal.nbytes
     d2h = out["res"].nbytes + out["bound_idx"].nbytes + out["phi"].nbytes + out["prof"].nbytes
-    for _ in range(max(1, args.warmup)):
-        ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
-    ts = []
-    for _ in range(max(3, args.steps // 2)):
-        t0 = time.perf_counter()
-        ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
-        ts.append(time.perf_counter() - t0)
-    s = float(np.mean(ts))
+    def timed():
+        for _ in range(max(1, args.warmup)):
+            ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            t0 = time.perf_counter()
+            ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
+            ts.append(time.perf_counter() - t0)
+        return float(np.mean(ts))
+    # default: inputs staged through device memory; then the kernels reading
+    # and writing the page-locked buffers in place, for comparison
+    ctx.set_option(ahf.OPT_HOST_DIRECT, 0)
+    s = timed()
+    ctx.set_option(ahf.OPT_HOST_DIRECT, 1)
+    s_direct = timed()
+    ctx.set_option(ahf.OPT_HOST_DIRECT, 0)
     return {"value": units / s, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": s * 1e3, "api": "ahf_unbind_batch_host (unbinding + profile, host buffers)"}
+            "ms_per_step": s * 1e3, "in_place_ms_per_step": s_direct * 1e3,
+            "api": "ahf_unbind_batch_host (unbinding + profile, page-locked host buffers, staged copies)"}
 
 
 def run_serve(args):

@@ -225,21 +225,36 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        it reports AHF_ERR_TIMEOUT (0 = give up at once)
  *   AHF_OPT_TIMING       1 = record CUDA events around every phase of the
  *                        following calls (read with ahf_get_stats), 0 = off
+ *   AHF_OPT_GRAPHS       1 = a batch whose haloes all take the on-chip classes
+ *                        runs its launches as a CUDA graph, captured once and
+ *                        replayed while the launch parameters (buffers, class
+ *                        sizes, grid shapes) repeat; 0 (default) = plain
+ *                        launches.  Ignored while AHF_OPT_TIMING is on.
+ *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
+ *                        arrays that are page-locked (cudaHostAlloc,
+ *                        cudaHostRegister) and write page-locked outputs in
+ *                        place through their mapped device addresses, with no
+ *                        staging buffer in device memory (for inputs too large
+ *                        to stage); 0 (default) = stage through device memory,
+ *                        which is faster: the kernels re-read candidates in
+ *                        radial order.  Pageable buffers are always staged.
  * Errors: AHF_ERR_INVALID (unknown option or value). */
 #define AHF_OPT_ONCHIP_MAX 1
 #define AHF_OPT_WAIT_LIMIT 2
 #define AHF_OPT_TIMING     3
+#define AHF_OPT_HOST_DIRECT 4
+#define AHF_OPT_GRAPHS     5
 
 /* Per-call statistics of the most recent unbinding or profile call.
  * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the
- * single-CTA shared-memory variants (1k / 4k / 8k slots), 4-6 the cluster
- * variants (4 / 8 / 16 CTAs, 32k / 64k / 128k slots), 7 the multi-CTA
- * class's gather + sort + fill, 8 its iterations, 9 its final pass, 10 the
- * profile.  phase_ms is device time between events recorded on the stream
+ * single-CTA shared-memory variants (1k / 4k / 8k slots), 4-7 the cluster
+ * variants (2 / 4 / 8 / 16 CTAs, 16k / 32k / 64k / 128k slots), 8 the
+ * multi-CTA class's gather + sort + fill, 9 its iterations, 10 its final
+ * pass, 11 the profile.  phase_ms is device time between events recorded on the stream
  * the phase ran on (valid only with AHF_OPT_TIMING on; -1 otherwise);
  * phase_halos / phase_candidates count the haloes and candidate slots each
  * phase covered. */
-#define AHF_N_PHASES 11
+#define AHF_N_PHASES 12
 typedef struct ahf_stats {
   int64_t launches;                    /* kernels launched by the call        */
   int64_t host_syncs;                  /* host synchronisations in the call   */
@@ -247,6 +262,8 @@ typedef struct ahf_stats {
   int64_t phase_halos[AHF_N_PHASES];
   int64_t phase_candidates[AHF_N_PHASES];
   double phase_ms[AHF_N_PHASES];
+  int64_t graph_launches;              /* CUDA graph launches by the call     */
+  int64_t graph_captures;              /* graphs captured (new launch key)    */
 } ahf_stats;
 
 /* Copy the statistics of the context's last call (waits for its device work

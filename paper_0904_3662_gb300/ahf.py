@@ -23,11 +23,11 @@ ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2,
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
-OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING = 1, 2, 3
-N_PHASES = 11
-PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster4_32k", "cluster8_64k", "cluster16_128k",
-               "grid_gather_sort", "grid_iterate", "grid_finish", "profile")
-VARIANT_CAPS = (512, 1024, 4096, 8192, 4 * 8192, 8 * 8192, 16 * 8192)
+OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS = 1, 2, 3, 4, 5
+N_PHASES = 12
+PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster2_16k", "cluster4_32k", "cluster8_64k",
+               "cluster16_128k", "grid_gather_sort", "grid_iterate", "grid_finish", "profile")
+VARIANT_CAPS = (512, 1024, 4096, 8192, 2 * 8192, 4 * 8192, 8 * 8192, 16 * 8192)
 
 HALO_DTYPE = np.dtype([("cx", "<f8"), ("cy", "<f8"), ("cz", "<f8"), ("radius", "<f8"),
                        ("offset", "<i8"), ("count", "<i8")])
@@ -69,7 +69,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("host_syncs", ctypes.c_int64),
                 ("grid_iterations", ctypes.c_int64),
                 ("phase_halos", ctypes.c_int64 * N_PHASES), ("phase_candidates", ctypes.c_int64 * N_PHASES),
-                ("phase_ms", ctypes.c_double * N_PHASES)]
+                ("phase_ms", ctypes.c_double * N_PHASES), ("graph_launches", ctypes.c_int64),
+                ("graph_captures", ctypes.c_int64)]
 
 
 _lib = None
@@ -229,7 +230,8 @@ class Context:
         _check(self.lib.ahf_get_stats(self._p, ctypes.byref(st)))
         return {"launches": st.launches, "host_syncs": st.host_syncs, "grid_iterations": st.grid_iterations,
                 "phase_halos": list(st.phase_halos), "phase_candidates": list(st.phase_candidates),
-                "phase_ms": list(st.phase_ms)}
+                "phase_ms": list(st.phase_ms), "graph_launches": st.graph_launches,
+                "graph_captures": st.graph_captures}
 
     def alloc_outputs(self, n_halos, n_slots, with_phi=True, with_removed=True, precision=PREC_MIXED):
         import torch

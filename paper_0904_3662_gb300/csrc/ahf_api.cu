@@ -91,7 +91,7 @@ namespace {
 // Shared-memory variants in size order: 0 = one warp per halo, 1-3 = one CTA
 // of 128 / 256 / 512 threads, 4-6 = clusters of 4 / 8 / 16 CTAs.  Phases
 // 0..NV-1 time them; then the multi-CTA class's three phases and the profile.
-constexpr int NV = 7;
+constexpr int NV = 8;
 constexpr int PH_GRID_SORT = NV, PH_GRID_ITER = NV + 1, PH_GRID_FINISH = NV + 2, PH_PROFILE = NV + 3;
 static_assert(PH_PROFILE + 1 == AHF_N_PHASES, "phase table");
 
@@ -139,13 +139,18 @@ struct ahf_ctx {
   size_t stage_bytes = 0;
   // per-call statistics and optional phase timing
   bool timing = false;
+  bool host_direct = false;          // host entry: use mapped page-locked buffers in place
+  bool graphs = false;               // on-chip launch sequence as a replayed CUDA graph
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture = nullptr;    // stream the graph is captured on
+  std::vector<unsigned char> graph_key;   // launch parameters the graph was captured with
   ahf_stats stats{};
   bool phase_used[AHF_N_PHASES] = {};
   cudaEvent_t ev0[AHF_N_PHASES] = {}, ev1[AHF_N_PHASES] = {};
   cudaStream_t side[NV] = {};    // one stream per shared-memory variant
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[NV] = {};
-  int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
+  int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
 };
 
 namespace {
@@ -564,37 +569,92 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if ((rc = pin_release(c, s))) return rc;
   // the on-chip variants run on side streams, largest first, concurrently
   // with the multi-CTA class on the caller's stream
-  AHF_CUDA(cudaEventRecord(c->fork, s));
-  int first = 0;
-  int used_side[NV] = {};
-  // clusters (the largest haloes) first, then the single-CTA and warp variants
+  struct VLaunch {
+    int v, grid, n;
+    long long cands;
+    OnchipLaunch L;
+  };
+  std::vector<VLaunch> vl;
   int first_of[NV];
   for (int v = 0, f = 0; v < NV; ++v) { first_of[v] = f; f += P.n_class[v]; }
+  // clusters (the largest haloes) first, then the single-CTA and warp variants
   for (int v = NV - 1; v >= 0; --v) {
     const int n = P.n_class[v];
     if (n == 0) continue;
-    OnchipLaunch L;
+    VLaunch x;
+    std::memset(&x, 0, sizeof x);        // padding too: the bytes form the graph key
+    x.v = v;
+    x.n = n;
+    OnchipLaunch& L = x.L;
     L.p = pd; L.frame = P.frame; L.prm = prd; L.out = O;
     L.halos = hd + first_of[v]; L.n_halos = n; L.queue = queues + v;
     L.rows.prof = (prof && v <= FUSED_MAX) ? prof : nullptr;
     L.rows.factor = dfac;
     L.rows.n_bins = n_bins;
-    long long cands = 0;
-    for (int k = 0; k < n; ++k) cands += P.hd[(size_t)first_of[v] + k].count;
-    const int grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
-    AHF_CUDA(cudaStreamWaitEvent(c->side[v], c->fork, 0));
-    if ((rc = phase_begin(c, v, c->side[v], n, cands))) return rc;
-    AHF_CUDA(launch_variant(L, v, grid, c->side[v]));
+    for (int k = 0; k < n; ++k) x.cands += P.hd[(size_t)first_of[v] + k].count;
+    x.grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
+    vl.push_back(x);
+  }
+  auto enqueue_onchip = [&](cudaStream_t o, bool join) -> int {
+    AHF_CUDA(cudaEventRecord(c->fork, o));
+    for (const VLaunch& x : vl) {
+      AHF_CUDA(cudaStreamWaitEvent(c->side[x.v], c->fork, 0));
+      int prc;
+      if ((prc = phase_begin(c, x.v, c->side[x.v], 0, 0))) return prc;
+      AHF_CUDA(launch_variant(x.L, x.v, x.grid, c->side[x.v]));
+      if ((prc = phase_end(c, x.v, c->side[x.v]))) return prc;
+      AHF_CUDA(cudaEventRecord(c->join[x.v], c->side[x.v]));
+    }
+    if (join)
+      for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(o, c->join[x.v], 0));
+    return AHF_OK;
+  };
+  for (const VLaunch& x : vl) {
     c->stats.launches += 1;
-    if ((rc = phase_end(c, v, c->side[v]))) return rc;
-    AHF_CUDA(cudaEventRecord(c->join[v], c->side[v]));
-    used_side[v] = 1;
+    c->phase_used[x.v] = true;
+    c->stats.phase_halos[x.v] += x.n;
+    c->stats.phase_candidates[x.v] += x.cands;
   }
-  if (n_grid) {
-    if ((rc = run_grid(c, G, prm, s))) return rc;
+  // a batch of on-chip haloes only can run as a CUDA graph, replayed while
+  // the launch parameters repeat (the descriptors staged above are inputs
+  // of the graph's kernels, not part of it)
+  if (c->graphs && !c->timing && n_grid == 0 && !vl.empty()) {
+    std::vector<unsigned char> key(vl.size() * sizeof(VLaunch));
+    std::memcpy(key.data(), vl.data(), key.size());
+    if (!c->graph_exec || key != c->graph_key) {
+      if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+      c->graph_key.clear();
+      // captured on the context's own stream (the caller's may be the legacy
+      // default stream, which cannot be captured); launched on the caller's
+      AHF_CUDA(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeRelaxed));
+      const int erc = enqueue_onchip(c->capture, true);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(c->capture, &g);
+      if (erc != AHF_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return erc != AHF_OK ? erc : fail(AHF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        c->graph_exec = nullptr;
+        cudaGetLastError();
+        return fail(AHF_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ie));
+      }
+      c->graph_key = key;
+      c->stats.graph_captures += 1;
+    }
+    AHF_CUDA(cudaGraphLaunch(c->graph_exec, s));
+    c->stats.graph_launches += 1;
+  } else {
+    if ((rc = enqueue_onchip(s, false))) return rc;
+    if (n_grid) {
+      if ((rc = run_grid(c, G, prm, s))) return rc;
+    }
+    for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
   }
-  for (int k = 0; k < NV; ++k)
-    if (used_side[k]) AHF_CUDA(cudaStreamWaitEvent(s, c->join[k], 0));
   if ((rc = end_call(c, s))) return rc;
   if (prof) {
     // rows of the haloes the fused variants did not cover
@@ -824,6 +884,19 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
 }
 
 // Host-memory form: stage the inputs in a device buffer, run, copy back.
+// The device address of a page-locked, mapped host buffer (cudaHostAlloc,
+// cudaHostRegister), or NULL for pageable memory.
+void* mapped_address(const void* host) {
+  if (!host) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
+}
+
 int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
               const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
               int32_t* removed_iter, int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s) {
@@ -857,35 +930,56 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   AHF_CUDA(cudaSetDevice(c->device));
   if (c->last_valid) AHF_CUDA(cudaStreamWaitEvent(s, c->last, 0));
   Bump B{c->stage, 0, c->stage_bytes};
+  // each buffer is used in place when it is page-locked and mapped (and the
+  // option allows), else staged through the context's device buffer
+  auto direct = [&](const void* h) -> void* { return c->host_direct ? mapped_address(h) : nullptr; };
   ahf_particles dp = *p;
   const void* src[7] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m};
   const void** dst[7] = {&dp.x, &dp.y, &dp.z, &dp.vx, &dp.vy, &dp.vz, &dp.m};
   for (int k = 0; k < 7; ++k) {
     if (!src[k]) continue;
     char* d = B.take<char>(n * es);
-    if (n) AHF_CUDA(cudaMemcpyAsync(d, src[k], n * es, cudaMemcpyHostToDevice, s));
+    if (void* m = direct(src[k])) {
+      d = (char*)m;
+    } else if (n) {
+      AHF_CUDA(cudaMemcpyAsync(d, src[k], n * es, cudaMemcpyHostToDevice, s));
+    }
     *dst[k] = d;
   }
   int64_t* dmi = nullptr;
   if (member_idx) {
     dmi = B.take<int64_t>((size_t)n_slots);
-    if (n_slots) AHF_CUDA(cudaMemcpyAsync(dmi, member_idx, (size_t)n_slots * 8, cudaMemcpyHostToDevice, s));
+    if (void* m = direct(member_idx)) dmi = (int64_t*)m;
+    else if (n_slots) AHF_CUDA(cudaMemcpyAsync(dmi, member_idx, (size_t)n_slots * 8, cudaMemcpyHostToDevice, s));
   }
+  // outputs: in place when mapped, else copied back after the kernels
+  void* m_out = n_halos ? direct(out) : nullptr;
+  void* m_bi = n_slots ? direct(bound_idx) : nullptr;
+  void* m_phi = (phi && n_slots) ? direct(phi) : nullptr;
+  void* m_ri = (removed_iter && n_slots) ? direct(removed_iter) : nullptr;
+  void* m_prof = (n_bins > 0 && n_halos) ? direct(prof) : nullptr;
   ahf_result* dout = B.take<ahf_result>((size_t)n_halos);
   int64_t* dbi = B.take<int64_t>((size_t)std::max<int64_t>(n_slots, 1));
   void* dphi = phi ? (void*)B.take<char>((size_t)std::max<int64_t>(n_slots, 1) * ps) : nullptr;
   int32_t* dri = removed_iter ? B.take<int32_t>((size_t)std::max<int64_t>(n_slots, 1)) : nullptr;
   double* dprof = n_bins > 0 ? B.take<double>((size_t)n_halos * n_bins * 4 + 1) : nullptr;
+  if (m_out) dout = (ahf_result*)m_out;
+  if (m_bi) dbi = (int64_t*)m_bi;
+  if (m_phi) dphi = m_phi;
+  if (m_ri) dri = (int32_t*)m_ri;
+  if (m_prof) dprof = (double*)m_prof;
   if ((rc = unbind_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, dphi, dri, s, n_bins, r_min_frac,
                         n_bins > 0 ? dprof : nullptr)))
     return rc;
-  if (n_halos) AHF_CUDA(cudaMemcpyAsync(out, dout, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
-  if (n_bins > 0 && n_halos)
+  if (n_halos && !m_out)
+    AHF_CUDA(cudaMemcpyAsync(out, dout, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
+  if (n_bins > 0 && n_halos && !m_prof)
     AHF_CUDA(cudaMemcpyAsync(prof, dprof, sizeof(double) * (size_t)n_halos * n_bins * 4, cudaMemcpyDeviceToHost, s));
   if (n_slots) {
-    AHF_CUDA(cudaMemcpyAsync(bound_idx, dbi, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, s));
-    if (phi) AHF_CUDA(cudaMemcpyAsync(phi, dphi, (size_t)n_slots * ps, cudaMemcpyDeviceToHost, s));
-    if (removed_iter) AHF_CUDA(cudaMemcpyAsync(removed_iter, dri, (size_t)n_slots * 4, cudaMemcpyDeviceToHost, s));
+    if (!m_bi) AHF_CUDA(cudaMemcpyAsync(bound_idx, dbi, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, s));
+    if (phi && !m_phi) AHF_CUDA(cudaMemcpyAsync(phi, dphi, (size_t)n_slots * ps, cudaMemcpyDeviceToHost, s));
+    if (removed_iter && !m_ri)
+      AHF_CUDA(cudaMemcpyAsync(removed_iter, dri, (size_t)n_slots * 4, cudaMemcpyDeviceToHost, s));
   }
   AHF_CUDA(cudaEventRecord(c->last, s));
   AHF_CUDA(cudaStreamSynchronize(s));
@@ -924,6 +1018,10 @@ int ahf_create(ahf_ctx** ctx, int device) {
       break;
     }
     if (cudaMallocHost(&c->flag_host, 16 * sizeof(int)) != cudaSuccess) { rc = fail(AHF_ERR_NOMEM, "pinned flags"); break; }
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(AHF_ERR_CUDA, "capture stream");
+      break;
+    }
     for (int k = 0; k < NV && rc == AHF_OK; ++k) {
       if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) != cudaSuccess)
@@ -951,6 +1049,8 @@ int ahf_destroy(ahf_ctx* c) {
   if (!c) return AHF_OK;
   cudaSetDevice(c->device);
   if (c->last_valid) cudaEventSynchronize(c->last);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->capture) cudaStreamDestroy(c->capture);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->err_dev) cudaFree(c->err_dev);
@@ -990,6 +1090,14 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "timing is 0 or 1");
       c->timing = value == 1;
       return AHF_OK;
+    case AHF_OPT_HOST_DIRECT:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "host_direct is 0 or 1");
+      c->host_direct = value == 1;
+      return AHF_OK;
+    case AHF_OPT_GRAPHS:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "graphs is 0 or 1");
+      c->graphs = value == 1;
+      return AHF_OK;
     default:
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
@@ -1001,6 +1109,8 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
     case AHF_OPT_ONCHIP_MAX: *value = c->onchip_max; return AHF_OK;
     case AHF_OPT_WAIT_LIMIT: *value = c->wait_limit; return AHF_OK;
     case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
+    case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
+    case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
     default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }

@@ -872,12 +872,13 @@ int max_grid_variant(int device) {
 }  // namespace
 
 // Variants: 0 = 1 CTA x 128 threads / 1024 slots, 1 = 1 x 256 / 4096,
-// 2 = 1 x 512 / 8192, 3/4/5 = clusters of 4/8/16 CTAs x 512 / 8192 slots.
+// 2 = 1 x 512 / 8192, 3/4/5/6 = clusters of 2/4/8/16 CTAs x 512 / 8192 slots.
 int onchip_cluster_size(int variant) {
   switch (variant) {
-    case 3: return 4;
-    case 4: return 8;
-    case 5: return 16;
+    case 3: return 2;
+    case 4: return 4;
+    case 5: return 8;
+    case 6: return 16;
     default: return 1;
   }
 }
@@ -887,9 +888,10 @@ int onchip_capacity(int variant) {
     case 0: return 1024;
     case 1: return 4096;
     case 2: return 8192;
-    case 3: return 4 * 8192;
-    case 4: return 8 * 8192;
-    case 5: return 16 * 8192;
+    case 3: return 2 * 8192;
+    case 4: return 4 * 8192;
+    case 5: return 8 * 8192;
+    case 6: return 16 * 8192;
     default: return 0;
   }
 }
@@ -899,9 +901,10 @@ int onchip_max_grid(int variant, int device) {
     case 0: return max_grid_variant<128, 1024, 1>(device);
     case 1: return max_grid_variant<256, 4096, 1>(device);
     case 2: return max_grid_variant<512, 8192, 1>(device);
-    case 3: return max_grid_variant<512, 8192, 4>(device);
-    case 4: return max_grid_variant<512, 8192, 8>(device);
-    case 5: return max_grid_variant<512, 8192, 16>(device);
+    case 3: return max_grid_variant<512, 8192, 2>(device);
+    case 4: return max_grid_variant<512, 8192, 4>(device);
+    case 5: return max_grid_variant<512, 8192, 8>(device);
+    case 6: return max_grid_variant<512, 8192, 16>(device);
     default: return 0;
   }
 }
@@ -915,11 +918,13 @@ cudaError_t launch_onchip(const OnchipLaunch& L, int variant, int grid, cudaStre
                        : launch_variant<256, 4096, AHF_COORD_F32_REL, 1>(L, grid, s);
     case 2: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 1>(L, grid, s)
                        : launch_variant<512, 8192, AHF_COORD_F32_REL, 1>(L, grid, s);
-    case 3: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 4>(L, grid, s)
+    case 3: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 2>(L, grid, s)
+                       : launch_variant<512, 8192, AHF_COORD_F32_REL, 2>(L, grid, s);
+    case 4: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 4>(L, grid, s)
                        : launch_variant<512, 8192, AHF_COORD_F32_REL, 4>(L, grid, s);
-    case 4: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 8>(L, grid, s)
+    case 5: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 8>(L, grid, s)
                        : launch_variant<512, 8192, AHF_COORD_F32_REL, 8>(L, grid, s);
-    case 5: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 16>(L, grid, s)
+    case 6: return f64 ? launch_variant<512, 8192, AHF_COORD_F64, 16>(L, grid, s)
                        : launch_variant<512, 8192, AHF_COORD_F32_REL, 16>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }

@@ -18,7 +18,7 @@ N_BINS, R_MIN_FRAC = 32, 0.01
 
 def _sample(counts, per_class=4, seed=7):
     """The largest halo of every size class and a few random ones."""
-    caps = [0, 512, 1024, 4096, 8192, 32768, 65536, 131072, 1 << 62]
+    caps = [0, 512, 1024, 4096, 8192, 16384, 32768, 65536, 131072, 1 << 62]
     rng = np.random.default_rng(seed)
     out = []
     for lo, hi in zip(caps[:-1], caps[1:]):

@@ -58,11 +58,12 @@ def test_multi_cta_class_f64_masses():
 
 
 def test_cluster_variants_all_sizes():
-    # haloes of 9k..125k candidates: clusters of 4, 8 and 16 CTAs
+    # haloes of 8k..125k candidates: clusters of 2, 4, 8 and 16 CTAs, at and
+    # around every class boundary
     rng = np.random.default_rng(31)
     from tests.test_gpu_paths import _pop_from_arrays
     pl, vl, cs, rs = [], [], [], []
-    for n in (8193, 9000, 20000, 32768, 32769, 50000, 65536, 65537, 90000, 125000):
+    for n in (8193, 9000, 16384, 16385, 20000, 32768, 32769, 50000, 65536, 65537, 90000, 125000):
         n_nfw = int(n * 0.87)
         p, v = synth.sample_nfw(rng, n_nfw, 10.0, 150.0)
         p2, v2 = synth.sample_uniform_sphere(rng, n - n_nfw, 300.0, 600.0)
@@ -72,7 +73,7 @@ def test_cluster_variants_all_sizes():
     out, prm, ctx, _ = run_gpu(pop)
     compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
     st = ctx.stats()
-    assert st["phase_halos"][4:7] == [4, 3, 3], st
+    assert st["phase_halos"][4:8] == [3, 3, 3, 3], st
 
 
 def test_cluster_and_grid_agree_bitwise():

@@ -172,6 +172,54 @@ def test_host_entry_point_with_profile():
     _check_profiles(pop, prm, out["res"], out["prof"], 16, 0.02)
 
 
+def _pinned(torch, a):
+    """A page-locked copy of a numpy array (same dtype and shape)."""
+    a = np.ascontiguousarray(a)
+    t = torch.from_numpy(a.reshape(-1).view(np.uint8)).pin_memory()
+    return t, t.numpy().view(a.dtype).reshape(a.shape)
+
+
+def test_host_entry_point_page_locked_in_place_and_staged():
+    # page-locked inputs and outputs used in place by the kernels, against the
+    # staged route and the device entry point: identical results
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=16, n_halos=40, n_lo=100, n_hi=40000, with_masses=True)
+    ctx = ahf.Context(0)
+    keep = []
+
+    def pin(a):
+        t, v = _pinned(torch, a)
+        keep.append(t)
+        return v
+    parts = ahf.Particles(pin(pop.x), pin(pop.y), pin(pop.z), pin(pop.vx), pin(pop.vy), pin(pop.vz), pin(pop.m),
+                          pop.m0, pop.coord_type)
+    prm = ahf.params_for(pop)
+    hal = ahf.halos_from_population(pop)
+    n = pop.n_particles
+    outs = []
+    for direct in (1, 0):
+        ctx.set_option(ahf.OPT_HOST_DIRECT, direct)
+        assert ctx.get_option(ahf.OPT_HOST_DIRECT) == direct
+        out = {"res": pin(np.zeros(pop.n_halos, dtype=ahf.RESULT_DTYPE)), "bound_idx": pin(np.zeros(n, np.int64)),
+               "phi": pin(np.zeros(n, np.float32)), "removed_iter": pin(np.zeros(n, np.int32)),
+               "prof": pin(np.zeros((pop.n_halos, 16, 4)))}
+        ctx.unbind_batch_host(parts, hal, prm, out=out, n_bins=16, r_min_frac=0.02)
+        outs.append({k: v.copy() for k, v in out.items()})
+    dev = ctx.unbind_profile_batch(ahf.particles_from_population(pop), hal, prm, n_bins=16, r_min_frac=0.02)
+    torch.cuda.synchronize()
+    res_d = ahf.results_to_numpy(dev["res"])
+    for o in outs:
+        assert o["res"].tobytes() == res_d.tobytes()
+        np.testing.assert_array_equal(o["removed_iter"], dev["removed_iter"].cpu().numpy())
+        np.testing.assert_array_equal(o["prof"], dev["prof"].cpu().numpy())
+        for h in range(pop.n_halos):
+            lo, nb = int(pop.offset[h]), int(res_d["n_bound"][h])
+            np.testing.assert_array_equal(o["bound_idx"][lo:lo + nb], dev["bound_idx"].cpu().numpy()[lo:lo + nb])
+            np.testing.assert_array_equal(o["phi"][lo:lo + nb], dev["phi"].cpu().numpy()[lo:lo + nb])
+    compare(pop, prm, outs[0]["res"], outs[0]["bound_idx"], outs[0]["phi"], outs[0]["removed_iter"])
+
+
 def test_profile_batch_device():
     torch = require_gpu()
     pop = synth.halo_batch(seed=15, n_halos=30, n_lo=100, n_hi=20000, with_masses=True)
@@ -263,3 +311,41 @@ def test_fused_profile_matches_standalone_and_oracle(with_masses):
         compare(pop, prm, res, fused["bound_idx"].cpu().numpy(), fused["phi"].cpu().numpy(),
                 fused["removed_iter"].cpu().numpy())
         _check_profiles(pop, prm, res, a, 20, 0.02)
+
+
+def test_graph_replay_matches_plain_launches():
+    # AHF_OPT_GRAPHS: captured once, replayed while the launch parameters
+    # repeat, recaptured when they change; results identical to plain launches
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pops = [synth.halo_batch(seed=71, n_halos=50, n_lo=100, n_hi=100_000),
+            synth.halo_batch(seed=72, n_halos=30, n_lo=100, n_hi=20_000)]
+    ctx = ahf.Context(0)
+    for pop in pops:
+        parts = ahf.particles_from_population(pop)
+        hal = ahf.halos_from_population(pop)
+        prm = ahf.params_for(pop)
+        ctx.set_option(ahf.OPT_GRAPHS, 0)
+        ref = ctx.unbind_profile_batch(parts, hal, prm, n_bins=16, r_min_frac=0.02)
+        torch.cuda.synchronize()
+        ctx.set_option(ahf.OPT_GRAPHS, 1)
+        out = ctx.alloc_outputs(pop.n_halos, pop.n_particles)
+        prof = torch.empty((pop.n_halos, 16, 4), dtype=torch.float64, device="cuda")
+        for call in range(3):
+            for k in ("bound_idx", "phi", "removed_iter", "res"):
+                out[k].zero_()
+            prof.zero_()
+            ctx.unbind_profile_batch(parts, hal, prm, n_bins=16, r_min_frac=0.02, out=out, prof=prof)
+            st = ctx.stats()
+            assert st["graph_launches"] == 1
+            assert st["graph_captures"] == (1 if call == 0 else 0), (call, st["graph_captures"])
+            torch.cuda.synchronize()
+            assert torch.equal(out["res"], ref["res"])
+            assert torch.equal(out["removed_iter"], ref["removed_iter"])
+            assert torch.equal(prof, ref["prof"])
+            res = ahf.results_to_numpy(ref["res"])
+            bi, bi_r = out["bound_idx"].cpu().numpy(), ref["bound_idx"].cpu().numpy()
+            for h in range(pop.n_halos):
+                lo, nb = int(pop.offset[h]), int(res["n_bound"][h])
+                np.testing.assert_array_equal(bi[lo:lo + nb], bi_r[lo:lo + nb])
+    ctx.set_option(ahf.OPT_GRAPHS, 0)
