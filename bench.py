@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace", action="store_true",
+                    help="after timing, one traced step: per-halo phase times of the on-chip kernels")
     ap.add_argument("--no-graphs", dest="graphs", action="store_false",
                     help="plain launches instead of CUDA graph replay in the timed steps")
     return ap.parse_args()
@@ -430,6 +432,16 @@ def run_ahf(args):
             "timed_wall_s": t_wall}
     clocks = clk.summary()
     line["clocks"] = clocks
+    if args.trace:
+        from paper_0904_3662_gb300 import trace_report
+        ctx.set_option(ahf.OPT_TIMING, 0)
+        ctx.set_option(ahf.OPT_TRACE, 1)
+        flush.zero_()
+        step()
+        summary = trace_report.summarize(ctx.trace(pop.n_halos))
+        ctx.set_option(ahf.OPT_TRACE, 0)
+        line["trace"] = summary
+        log("trace (us):\n" + trace_report.table(summary))
 
     log(f"timed {args.steps} steps: {ms:.3f} ms/step, {value:.4g} {METRIC}")
     if rank == 0 and not args.no_plain:

@@ -230,6 +230,8 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        replayed while the launch parameters (buffers, class
  *                        sizes, grid shapes) repeat; 0 (default) = plain
  *                        launches.  Ignored while AHF_OPT_TIMING is on.
+ *   AHF_OPT_TRACE        1 = the on-chip kernels of the following calls record
+ *                        per-halo timestamps (read with ahf_get_trace), 0 = off
  *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
  *                        arrays that are page-locked (cudaHostAlloc,
  *                        cudaHostRegister) and write page-locked outputs in
@@ -244,6 +246,7 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
 #define AHF_OPT_TIMING     3
 #define AHF_OPT_HOST_DIRECT 4
 #define AHF_OPT_GRAPHS     5
+#define AHF_OPT_TRACE      6
 
 /* Per-call statistics of the most recent unbinding or profile call.
  * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the
@@ -265,6 +268,18 @@ typedef struct ahf_stats {
   int64_t graph_launches;              /* CUDA graph launches by the call     */
   int64_t graph_captures;              /* graphs captured (new launch key)    */
 } ahf_stats;
+
+/* Per-halo trace of the last unbinding call made with AHF_OPT_TRACE on: for
+ * every halo (caller's order) AHF_TRACE_FIELDS int64 values,
+ *   0 start, 1 gathered, 2 sorted, 3 filled, 4 iterated, 5 done
+ *     (device global timer, ns, read by the halo's first thread),
+ *   6 the SM that ran the halo's first thread,
+ *   7 variant (the phase index of ahf_stats) + 256 * iterations.
+ * Haloes of the multi-CTA class have all fields 0.  Waits for the call's
+ * device work.  Errors: AHF_ERR_INVALID (NULL, n_halos not the last call's,
+ * tracing was off), AHF_ERR_CUDA. */
+#define AHF_TRACE_FIELDS 8
+int ahf_get_trace(ahf_ctx *ctx, int64_t *host, int64_t n_halos);
 
 /* Copy the statistics of the context's last call (waits for its device work
  * when timing is on).  Errors: AHF_ERR_INVALID (NULL), AHF_ERR_CUDA. */

@@ -40,6 +40,11 @@ Readings where the paper is silent (each listed in the design notes):
    M_k the inclusive mass) with M_k < Delta rho (4 pi/3) r_{k+1}^3, with
    r_{N+1} = infinity, and r_vir = (3 M_k / (4 pi Delta rho))^(1/3).
 
+Integral properties (Sect. 3.1, Sect. 3.2): the spin parameter and the
+energies of the material within r_vir, the rotation curve's peak, and the
+cross-identification of two catalogues by xi = N_shared^2 / (N_1 N_2); the
+readings are in halo_properties and match_catalogs.
+
 Pins: see tests/test_oracle_pins.py (brute force, Appendix A's integral
 evaluated literally, analytic uniform-sphere and truncated-NFW potentials,
 idempotence, the virial identity, invariances, special cases).
@@ -244,8 +249,75 @@ def profile(r_sorted, m_sorted, r_vir, n_bins, r_min_frac, G):
     return out
 
 
+def halo_properties(d, v, m, phi, k_vir, params: Params):
+    """Integral properties of a halo's bound set (Sect. 3.1's spin parameter,
+    lambda = J sqrt|E| / (G M^(5/2)) after Peebles 1969; the rotation curve's
+    peak).
+
+    d, v, m: offsets from the centre, velocities and masses of the bound set
+    in radial order (FP64); phi: its potential from the final iteration;
+    k_vir: index of the last particle inside r_vir (-1: no r_vir).
+
+    The material within r_vir is the first k_vir + 1 particles (the whole set
+    when there is no r_vir).  Over it: M = sum m; v_bar = sum m v / M;
+    u = v - v_bar + H d (the unbinding's frame); J = sum m d x u;
+    K = sum m |u|^2 / 2; U = sum m phi / 2; E = K + U; and the circular
+    velocity v_c(r_i) = sqrt(G M(<= r_i) / r_i), whose maximum is v_max at r_max
+    (the first radius reaching it).  Returns a dict of those values and n."""
+    d, v, m, phi = _f64(d), _f64(v), _f64(m), _f64(phi)
+    n = d.shape[0] if k_vir < 0 else k_vir + 1
+    out = dict(n=int(n), M=0.0, J=np.zeros(3), K=0.0, U=0.0, E=0.0, lam=0.0, v_max=0.0, r_max=0.0)
+    if n == 0:
+        return out
+    d, v, m, phi = d[:n], v[:n], m[:n], phi[:n]
+    M = float(m.sum())
+    vbar = (m[:, None] * v).sum(axis=0) / M
+    u = v - vbar[None, :] + params.H * d
+    J = (m[:, None] * np.cross(d, u)).sum(axis=0)
+    K = 0.5 * float((m * (u * u).sum(axis=1)).sum())
+    U = 0.5 * float((m * phi).sum())
+    E = K + U
+    lam = float(np.sqrt((J * J).sum()) * math.sqrt(abs(E)) / (params.G * M ** 2.5))
+    r = np.sqrt((d * d).sum(axis=1))
+    m_in = np.cumsum(m)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        vc = np.where(r > 0.0, np.sqrt(params.G * m_in / r), 0.0)
+    i = int(np.argmax(vc))
+    out.update(M=M, J=J, K=K, U=U, E=E, lam=lam, v_max=float(vc[i]), r_max=float(r[i]))
+    return out
+
+
+def match_catalogs(lists_a, lists_b):
+    """Cross-identification of two halo catalogues (Sect. 3.2): for every halo
+    of the first, the halo of the second maximising xi = N_shared^2 / (N_1 N_2),
+    N_shared the particles the two have in common and N_1, N_2 their sizes.
+    lists_a, lists_b: sequences of particle-id arrays (one per halo).  Returns
+    (best, shared, xi) arrays over the first catalogue; best = -1 and xi = 0
+    when a halo shares no particle (ties: the lower index of the second
+    catalogue)."""
+    owner = {}
+    for b, ids in enumerate(lists_b):
+        for i in np.asarray(ids).tolist():
+            owner.setdefault(i, []).append(b)
+    n_a = len(lists_a)
+    best = np.full(n_a, -1, dtype=np.int64)
+    shared = np.zeros(n_a, dtype=np.int64)
+    xi = np.zeros(n_a)
+    for a, ids in enumerate(lists_a):
+        count = {}
+        for i in np.asarray(ids).tolist():
+            for b in owner.get(i, ()):
+                count[b] = count.get(b, 0) + 1
+        n1 = len(ids)
+        for b in sorted(count):
+            x = count[b] ** 2 / (n1 * len(lists_b[b]))
+            if x > xi[a]:
+                best[a], shared[a], xi[a] = b, count[b], x
+    return best, shared, xi
+
+
 def unbind_population(pop, params: Params, halos=None, member_idx=None,
-                      forced=None, n_bins=0, r_min_frac=0.01):
+                      forced=None, n_bins=0, r_min_frac=0.01, properties=False):
     """Run the oracle over haloes of a population (all of them by default).
 
     forced: optional per-candidate-slot removal iterations (flat, aligned
@@ -262,6 +334,8 @@ def unbind_population(pop, params: Params, halos=None, member_idx=None,
         o["bound_idx"] = pidx[o["order"]]
         if n_bins > 0:
             o["profile"] = profile(o["r"], m[o["order"]], o["r_vir"], n_bins, r_min_frac, p.G)
+        if properties:
+            o["props"] = halo_properties(d[o["order"]], v[o["order"]], m[o["order"]], o["phi"], o["k_vir"], p)
         res[h] = o
     return res
 

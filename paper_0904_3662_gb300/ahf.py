@@ -23,7 +23,8 @@ ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2,
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
-OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS = 1, 2, 3, 4, 5
+OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE = 1, 2, 3, 4, 5, 6
+TRACE_FIELDS = 8
 N_PHASES = 12
 PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster2_16k", "cluster4_32k", "cluster8_64k",
                "cluster16_128k", "grid_gather_sort", "grid_iterate", "grid_finish", "profile")
@@ -41,7 +42,7 @@ EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_un
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
            "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch",
            "ahf_serve_create", "ahf_serve_submit", "ahf_serve_poll", "ahf_serve_stats", "ahf_serve_counters",
-           "ahf_serve_reset_stats", "ahf_serve_destroy")
+           "ahf_serve_reset_stats", "ahf_serve_destroy", "ahf_get_trace")
 SERVE_MAX_COUNT = 131072
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
 
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.ahf_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     lib.ahf_sync.argtypes = [vp]
+    lib.ahf_get_trace.argtypes = [vp, vp, i64]
     lib.ahf_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_Params),
                                      i32, ctypes.c_double]
     lib.ahf_serve_submit.argtypes = [vp, ctypes.POINTER(_Particles), vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -232,6 +234,13 @@ class Context:
                 "phase_halos": list(st.phase_halos), "phase_candidates": list(st.phase_candidates),
                 "phase_ms": list(st.phase_ms), "graph_launches": st.graph_launches,
                 "graph_captures": st.graph_captures}
+
+    def trace(self, n_halos):
+        """Per-halo trace of the last call made with OPT_TRACE on:
+        (n_halos, TRACE_FIELDS) int64 (see ahf_get_trace)."""
+        t = np.zeros((n_halos, TRACE_FIELDS), dtype=np.int64)
+        _check(self.lib.ahf_get_trace(self._p, t.ctypes.data, int(n_halos)))
+        return t
 
     def alloc_outputs(self, n_halos, n_slots, with_phi=True, with_removed=True, precision=PREC_MIXED):
         import torch

@@ -141,6 +141,10 @@ struct ahf_ctx {
   bool timing = false;
   bool host_direct = false;          // host entry: use mapped page-locked buffers in place
   bool graphs = false;               // on-chip launch sequence as a replayed CUDA graph
+  bool trace = false;                // per-halo timestamps from the on-chip kernels
+  long long* trace_dev = nullptr;    // [n][AHF_TRACE_FIELDS] of the last traced call
+  int64_t trace_cap = 0;             // haloes trace_dev holds
+  int64_t trace_n = -1;              // haloes of the last traced call (-1: none)
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t capture = nullptr;    // stream the graph is captured on
   std::vector<unsigned char> graph_key;   // launch parameters the graph was captured with
@@ -567,6 +571,21 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     c->stats.launches += 2;
   }
   if ((rc = pin_release(c, s))) return rc;
+  if (c->trace) {
+    if (c->trace_cap < n_halos) {
+      if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
+      if (c->trace_dev) cudaFree(c->trace_dev);
+      c->trace_dev = nullptr;
+      c->trace_cap = 0;
+      if (cudaMalloc(&c->trace_dev, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AHF_ERR_NOMEM, "trace buffer");
+      }
+      c->trace_cap = n_halos;
+    }
+    AHF_CUDA(cudaMemsetAsync(c->trace_dev, 0, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos, s));
+    c->trace_n = n_halos;
+  }
   // the on-chip variants run on side streams, largest first, concurrently
   // with the multi-CTA class on the caller's stream
   struct VLaunch {
@@ -577,8 +596,13 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   std::vector<VLaunch> vl;
   int first_of[NV];
   for (int v = 0, f = 0; v < NV; ++v) { first_of[v] = f; f += P.n_class[v]; }
-  // clusters (the largest haloes) first, then the single-CTA and warp variants
-  for (int v = NV - 1; v >= 0; --v) {
+  // launch order (the block scheduler serves earlier launches first): the
+  // clusters (largest haloes) first, then the single-CTA variants of 8k and
+  // 4k slots, then the warp variant, whose haloes run longer than the 1k
+  // variant's, then that one
+  constexpr int kOrder[NV] = {7, 6, 5, 4, 3, 2, 0, 1};
+  for (int oi = 0; oi < NV; ++oi) {
+    const int v = kOrder[oi];
     const int n = P.n_class[v];
     if (n == 0) continue;
     VLaunch x;
@@ -591,6 +615,8 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     L.rows.prof = (prof && v <= FUSED_MAX) ? prof : nullptr;
     L.rows.factor = dfac;
     L.rows.n_bins = n_bins;
+    L.trace = c->trace ? c->trace_dev : nullptr;
+    L.variant = v;
     for (int k = 0; k < n; ++k) x.cands += P.hd[(size_t)first_of[v] + k].count;
     x.grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
     vl.push_back(x);
@@ -1051,6 +1077,7 @@ int ahf_destroy(ahf_ctx* c) {
   if (c->last_valid) cudaEventSynchronize(c->last);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->capture) cudaStreamDestroy(c->capture);
+  if (c->trace_dev) cudaFree(c->trace_dev);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->err_dev) cudaFree(c->err_dev);
@@ -1098,6 +1125,10 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "graphs is 0 or 1");
       c->graphs = value == 1;
       return AHF_OK;
+    case AHF_OPT_TRACE:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "trace is 0 or 1");
+      c->trace = value == 1;
+      return AHF_OK;
     default:
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
@@ -1111,6 +1142,7 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
     case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
     case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
+    case AHF_OPT_TRACE: *value = c->trace ? 1 : 0; return AHF_OK;
     default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }
@@ -1150,6 +1182,21 @@ int ahf_unbind_batch_host(ahf_ctx* c, const ahf_particles* p, const ahf_halo* ha
   std::lock_guard<std::mutex> g(c->mu);
   return host_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, n_bins, r_min_frac,
                    prof, (cudaStream_t)stream);
+}
+
+int ahf_get_trace(ahf_ctx* c, int64_t* host, int64_t n_halos) {
+  if (!c || !host) return fail(AHF_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->trace_n < 0) return fail(AHF_ERR_INVALID, "no traced call (AHF_OPT_TRACE was off)");
+  if (n_halos != c->trace_n)
+    return fail(AHF_ERR_INVALID, "n_halos %lld differs from the traced call's %lld", (long long)n_halos,
+                (long long)c->trace_n);
+  AHF_CUDA(cudaSetDevice(c->device));
+  if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
+  if (n_halos)
+    AHF_CUDA(cudaMemcpy(host, c->trace_dev, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos,
+                        cudaMemcpyDeviceToHost));
+  return AHF_OK;
 }
 
 int ahf_get_stats(ahf_ctx* c, ahf_stats* out) {

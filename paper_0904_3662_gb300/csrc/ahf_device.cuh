@@ -435,6 +435,25 @@ __device__ void profile_rows(const ProfileRows& Q, int h, const float* rc, const
   }
 }
 
+// ---- per-halo trace (AHF_OPT_TRACE) ------------------------------------------------
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int sm_id() {
+  int s;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+  return s;
+}
+
+// Record trace field f of halo h (no-op when tracing is off).
+__device__ __forceinline__ void trace_mark(long long* trace, int h, int f) {
+  if (trace) trace[(size_t)h * AHF_TRACE_FIELDS + f] = global_ns();
+}
+
 // ---- warp / block scans ---------------------------------------------------------
 
 template <typename T>

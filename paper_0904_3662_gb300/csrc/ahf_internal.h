@@ -121,6 +121,8 @@ struct OnchipLaunch {
   int n_halos;
   int *queue;            // work counter (zeroed by the launcher)
   ProfileRows rows;      // rows.prof == NULL: no profile from this launch
+  long long *trace;      // [halo index][AHF_TRACE_FIELDS] or NULL
+  int variant;           // phase index of this class (for the trace)
 };
 
 // Warp class: one warp per halo of at most warp_capacity() candidates.

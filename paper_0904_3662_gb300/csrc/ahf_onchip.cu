@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     Cl<CS>::sync();
     if (hq >= L.n_halos) break;
     const HaloDev& H = L.halos[hq];
+    if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 0);
     const int n_cand = (int)H.count;
     const int chunk = n_cand > 0 ? (n_cand + CS - 1) / CS : 1;
     if (chunk > CAP) {    // the scheduler never does this; report, do not overrun
@@ -395,9 +396,11 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     const bool unim = L.p.m == nullptr;                  // every particle has mass m0
     const long long m0fix = fix_from_float(L.p.m0f, s_m);
 
+    if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
     const int which = cluster_radix_sort<NT, IPT, CS>(kA, vA, kB, vB, hist, S, X, nloc, chunk,
                                                       S.or_bits ^ S.and_bits, mask, rank);
+    if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 2);
     float* rr = (float*)(which ? kB : kA);         // radius, sorted, swizzled
     uint32_t* jj = which ? vB : vA;                // candidate position
     float* mm = (float*)(which ? kA : kB);         // mass; sign bit = removed
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     }
     __syncthreads();
 
+    if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 3);
     // per-thread exact sums of m, m/r and the alive count over its run
     long long tm_own = 0, tr_own = 0, tc_own = 0;
     for (int k = 0; k < ipt; ++k) {
@@ -585,6 +589,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     if (n_alive == 0) status |= AHF_HALO_EMPTY;
     else if (!converged) status |= AHF_HALO_NOT_CONVERGED;
 
+    if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 4);
     // ---- emit: bound list, phi, compacted (r, inclusive M) for the virial search ----
     float* rc = wx;                       // reuse: w is no longer needed
     long long* mc = (long long*)ex1;      // ex1 and ex2 are contiguous
@@ -788,6 +793,12 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
                        P.G, unim ? &L.p.m0 : nullptr, tid, NT);
         }
       }
+    }
+    if (tid == 0 && rank == 0 && L.trace) {
+      long long* t = L.trace + (size_t)H.index * AHF_TRACE_FIELDS;
+      t[5] = global_ns();
+      t[6] = sm_id();
+      t[7] = L.variant + 256ll * n_iter;
     }
     Cl<CS>::sync();
   }

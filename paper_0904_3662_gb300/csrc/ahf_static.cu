@@ -163,6 +163,8 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   L.out.res = out; L.out.bound_idx = (long long*)bound_idx; L.out.phi = phi; L.out.removed_iter = removed_iter;
   L.out.member_idx = (const long long*)member_idx; L.out.n_slots = n_slots; L.out.err = counters + 8;
   L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.n_bins = 0;
+  L.trace = nullptr;
+  L.variant = 0;
   // variants in the order the descriptors were staged; each class is its own queue
   int base = 0;
   for (int v = 0; v < 3; ++v) {

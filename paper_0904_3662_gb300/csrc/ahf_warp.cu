@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     hq = __shfl_sync(FULL_MASK, hq, 0);
     if (hq >= L.n_halos) break;
     const HaloDev H = L.halos[hq];
+    if (lane == 0) trace_mark(L.trace, H.index, 0);
     const int n_cand = (int)H.count;
     if (n_cand > WARP_CAP) {       // the scheduler never does this; report, do not overrun
       if (lane == 0) atomicOr(L.out.err, ERR_CAPACITY);
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     const bool unim = L.p.m == nullptr;                  // every particle has mass m0
     const long long m0fix = fix_from_float(L.p.m0f, s_m);
 
+    if (lane == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
     const int which = warp_radix_sort(kA, vA, kB, vB, hist, n_cand, orb ^ andb, mask, lane);
     float* rr = (float*)(which ? kB : kA);
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     float* wy = ex1;
     float* wz = ex2;
 
+    if (lane == 0) trace_mark(L.trace, H.index, 2);
     // ---- fill ----
     long long mv[3] = {0, 0, 0};
     for (int p = lane; p < n_mem; p += 32) {
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       }
     }
 
+    if (lane == 0) trace_mark(L.trace, H.index, 3);
     // ---- iterate (Appendix A) ----
     int n_iter = 0, status = 0;
     long long part_iter = 0, n_band = 0;
@@ -297,6 +301,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     if (n_alive == 0) status |= AHF_HALO_EMPTY;
     else if (!converged) status |= AHF_HALO_NOT_CONVERGED;
 
+    if (lane == 0) trace_mark(L.trace, H.index, 4);
     // ---- emit ----
     float* rc = wx;
     long long* mc = (long long*)ex1;      // ex1 and ex2 are contiguous
@@ -390,6 +395,12 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       const double r_vir = __shfl_sync(FULL_MASK, r_vir_l, 0);
       profile_rows(L.rows, H.index, rc, mc, [&](long long k) { return sw((int)k, mask); }, nb, r_vir, s_m, P.G,
                    unim ? &L.p.m0 : nullptr, lane, 32);
+    }
+    if (lane == 0 && L.trace) {
+      long long* t = L.trace + (size_t)H.index * AHF_TRACE_FIELDS;
+      t[5] = global_ns();
+      t[6] = sm_id();
+      t[7] = L.variant + 256ll * n_iter;
     }
     __syncwarp();
   }

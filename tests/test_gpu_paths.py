@@ -349,3 +349,38 @@ def test_graph_replay_matches_plain_launches():
                 lo, nb = int(pop.offset[h]), int(res["n_bound"][h])
                 np.testing.assert_array_equal(bi[lo:lo + nb], bi_r[lo:lo + nb])
     ctx.set_option(ahf.OPT_GRAPHS, 0)
+
+
+def test_trace_fields_and_results_unchanged():
+    # AHF_OPT_TRACE: monotone phase timestamps for every on-chip halo, its
+    # variant and iteration count; zeros for the multi-CTA class; results
+    # identical to an untraced call
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=73, n_halos=60, n_lo=100, n_hi=200_000)
+    ctx = ahf.Context(0)
+    parts = ahf.particles_from_population(pop)
+    hal = ahf.halos_from_population(pop)
+    prm = ahf.params_for(pop)
+    ref = ctx.unbind_batch(parts, hal, prm)
+    torch.cuda.synchronize()
+    with pytest.raises(ahf.AHFError):
+        ctx.trace(pop.n_halos)                      # nothing traced yet
+    ctx.set_option(ahf.OPT_TRACE, 1)
+    out = ctx.unbind_batch(parts, hal, prm)
+    tr = ctx.trace(pop.n_halos)
+    ctx.set_option(ahf.OPT_TRACE, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(out["res"], ref["res"]) and torch.equal(out["removed_iter"], ref["removed_iter"])
+    res = ahf.results_to_numpy(out["res"])
+    caps = ahf.VARIANT_CAPS
+    for h in range(pop.n_halos):
+        n = int(pop.count[h])
+        v = next((k for k, c in enumerate(caps) if n <= c), None)
+        if v is None:
+            assert np.all(tr[h] == 0)
+            continue
+        assert np.all(np.diff(tr[h, :6]) >= 0) and tr[h, 0] > 0, tr[h]
+        assert tr[h, 7] & 255 == v and tr[h, 7] >> 8 == res["n_iter"][h]
+    with pytest.raises(ahf.AHFError):
+        ctx.trace(pop.n_halos + 1)

@@ -75,3 +75,37 @@ def test_mutant_is_caught(name, func, old, new, monkeypatch):
         except Exception:           # assertion or numerical blow-up both count
             failed.append(pin.__name__)
     assert failed, f"mutant {name} passed every pin"
+
+
+from tests import test_oracle_props as props_pins
+
+PROPS_MUTANTS = [
+    ("props_no_half_kinetic", "halo_properties", "K = 0.5 * float(", "K = 1.0 * float("),
+    ("props_no_half_potential", "halo_properties", "U = 0.5 * float(", "U = float("),
+    ("props_no_bulk", "halo_properties", "u = v - vbar[None, :] + params.H * d", "u = v + params.H * d"),
+    ("props_cross_transposed", "halo_properties", "np.cross(d, u)", "np.cross(u, d)"),
+    ("props_mass_power", "halo_properties", "M ** 2.5", "M ** 1.5"),
+    ("props_exclusive_mass_vc", "halo_properties", "m_in = np.cumsum(m)", "m_in = np.cumsum(m) - m"),
+    ("props_virial_off_by_one", "halo_properties", "n = d.shape[0] if k_vir < 0 else k_vir + 1",
+     "n = d.shape[0] if k_vir < 0 else k_vir"),
+    ("match_xi_unsquared", "match_catalogs", "x = count[b] ** 2 / (n1 * len(lists_b[b]))",
+     "x = count[b] / (n1 * len(lists_b[b]))"),
+    ("match_tie_to_higher", "match_catalogs", "if x > xi[a]:", "if x >= xi[a]:"),
+]
+
+PROPS_PINS = [props_pins.test_two_particle_worked_example, props_pins.test_solid_body_rotation,
+              props_pins.test_uniform_sphere_energy_and_rotation_curve, props_pins.test_nfw_rotation_curve_peak,
+              props_pins.test_invariances_and_virial_selection, props_pins.test_match_catalogs_cases]
+
+
+@pytest.mark.parametrize("name,func,old,new", PROPS_MUTANTS, ids=[m[0] for m in PROPS_MUTANTS])
+def test_properties_mutant_is_caught(name, func, old, new, monkeypatch):
+    mod = _mutant_module(func, old, new, monkeypatch)
+    monkeypatch.setattr(props_pins, "O", mod)
+    failed = []
+    for pin in PROPS_PINS:
+        try:
+            pin()
+        except Exception:
+            failed.append(pin.__name__)
+    assert failed, f"mutant {name} passed every pin"
