@@ -322,6 +322,48 @@ int ahf_unbind_batch_static(const ahf_particles *p, const ahf_halo *halos, int64
                             const int64_t *member_idx, const ahf_params *prm, ahf_result *out,
                             int64_t *bound_idx, void *phi, int32_t *removed_iter, void *stream);
 
+/* ---- integral properties and catalogue matching --------------------------- */
+
+/* Integral properties of the bound sets an unbinding call produced (Sect.
+ * 3.1: the spin parameter lambda = J sqrt|E| / (G M^(5/2)); the rotation
+ * curve's peak).  Over the material within r_vir -- the first k_vir + 1
+ * particles of a halo's bound list, or the whole bound list when the halo has
+ * no r_vir -- with d the offset from the centre (FP64, minimum image),
+ * v_bar = sum m v / M, u = v - v_bar + H d (the unbinding's frame):
+ *   M = sum m, J = sum m d x u, K = sum m |u|^2 / 2, U = sum m phi / 2
+ *   (phi: the unbinding's output), E = K + U,
+ *   v_c(r_i) = sqrt(G M(<= r_i) / r_i) along the radial order, v_max its
+ *   maximum and r_max the first radius reaching it.
+ *   p, halos, n_halos, member_idx, prm   as passed to ahf_unbind_batch
+ *   res, bound_idx, phi                  its outputs (device; phi float in
+ *                                        the mixed mode, double in FP64)
+ *   props   device double [n_halos][AHF_PROP_FIELDS]:
+ *           0 n used, 1 M, 2-4 J, 5 K, 6 U, 7 E, 8 lambda, 9 v_max, 10 r_max,
+ *           11 1 if the set was cut at r_vir, else 0
+ * Sums are FP64 in a fixed order (repeatable bit for bit).  Empty haloes give
+ * zero rows.  Errors: AHF_ERR_INVALID, AHF_ERR_NOMEM, AHF_ERR_CUDA. */
+#define AHF_PROP_FIELDS 12
+int ahf_halo_properties(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos, int64_t n_halos,
+                        const int64_t *member_idx, const ahf_params *prm, const ahf_result *res,
+                        const int64_t *bound_idx, const void *phi, double *props, void *stream);
+
+/* Cross-identification of two catalogues (Sect. 3.2): for every halo a of
+ * the first, the halo b of the second maximising xi = N_shared^2 / (N_a N_b),
+ * N_shared the particle ids the two have in common (ties: the lower b).
+ * Catalogue X holds halo k's ids at ids_x[off_x[k] .. off_x[k] + cnt_x[k]);
+ * ids lie in [0, n_ids), are distinct within a halo, and each id belongs to
+ * at most one halo of the second catalogue (pass exclusive membership lists).
+ * All arrays are device memory.  Outputs over the first catalogue (device):
+ * best (-1: no shared id), shared, xi (0 when best is -1).  The context's
+ * workspace holds one int per id.  Problems the device finds (an id out of
+ * range, an id in two haloes of the second catalogue, a halo meeting more
+ * than 2048 haloes, whose best is then -2) are reported by ahf_sync as
+ * AHF_ERR_INVALID.  Errors: AHF_ERR_INVALID, AHF_ERR_NOMEM, AHF_ERR_CUDA. */
+int ahf_match_catalogs(ahf_ctx *ctx, int64_t n_ids, const int64_t *ids_a, const int64_t *off_a,
+                       const int64_t *cnt_a, int64_t n_a, const int64_t *ids_b, const int64_t *off_b,
+                       const int64_t *cnt_b, int64_t n_b, int64_t *best, int64_t *shared, double *xi,
+                       void *stream);
+
 /* ---- serving: continuous batching of one-halo requests --------------------
  *
  * For callers that produce candidate haloes over time rather than as one

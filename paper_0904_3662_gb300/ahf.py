@@ -42,7 +42,9 @@ EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_un
            "ahf_unbind_batch_host", "ahf_unbind_plain", "ahf_profile_batch", "ahf_set_option",
            "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch",
            "ahf_serve_create", "ahf_serve_submit", "ahf_serve_poll", "ahf_serve_stats", "ahf_serve_counters",
-           "ahf_serve_reset_stats", "ahf_serve_destroy", "ahf_get_trace")
+           "ahf_serve_reset_stats", "ahf_serve_destroy", "ahf_get_trace", "ahf_halo_properties",
+           "ahf_match_catalogs")
+PROP_FIELDS = 12
 SERVE_MAX_COUNT = 131072
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
 
@@ -104,6 +106,9 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     lib.ahf_sync.argtypes = [vp]
     lib.ahf_get_trace.argtypes = [vp, vp, i64]
+    lib.ahf_halo_properties.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
+                                        vp, vp, vp, vp, vp]
+    lib.ahf_match_catalogs.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]
     lib.ahf_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_Params),
                                      i32, ctypes.c_double]
     lib.ahf_serve_submit.argtypes = [vp, ctypes.POINTER(_Particles), vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -234,6 +239,33 @@ class Context:
                 "phase_halos": list(st.phase_halos), "phase_candidates": list(st.phase_candidates),
                 "phase_ms": list(st.phase_ms), "graph_launches": st.graph_launches,
                 "graph_captures": st.graph_captures}
+
+    def halo_properties(self, parts: Particles, halos, params: Params, out, member_idx=None, stream=None):
+        """ahf_halo_properties over the outputs `out` of an unbinding call:
+        device double (n_halos, PROP_FIELDS)."""
+        import torch
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        props = torch.empty((len(halos), PROP_FIELDS), dtype=torch.float64, device=torch.device("cuda", self.device))
+        pc, prc = parts.c(), params.c()
+        _check(self.lib.ahf_halo_properties(
+            self._p, ctypes.byref(pc), halos.ctypes.data, len(halos),
+            None if member_idx is None else member_idx.data_ptr(), ctypes.byref(prc), out["res"].data_ptr(),
+            out["bound_idx"].data_ptr(), out["phi"].data_ptr(), props.data_ptr(), _stream_ptr(stream)))
+        return props
+
+    def match_catalogs(self, n_ids, ids_a, off_a, cnt_a, ids_b, off_b, cnt_b, stream=None):
+        """ahf_match_catalogs on device int64 tensors: (best, shared, xi)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n_a, n_b = int(off_a.shape[0]), int(off_b.shape[0])
+        best = torch.empty(max(n_a, 1), dtype=torch.int64, device=dev)
+        shared = torch.empty(max(n_a, 1), dtype=torch.int64, device=dev)
+        xi = torch.empty(max(n_a, 1), dtype=torch.float64, device=dev)
+        _check(self.lib.ahf_match_catalogs(
+            self._p, int(n_ids), ids_a.data_ptr(), off_a.data_ptr(), cnt_a.data_ptr(), n_a, ids_b.data_ptr(),
+            off_b.data_ptr(), cnt_b.data_ptr(), n_b, best.data_ptr(), shared.data_ptr(), xi.data_ptr(),
+            _stream_ptr(stream)))
+        return best[:n_a], shared[:n_a], xi[:n_a]
 
     def trace(self, n_halos):
         """Per-halo trace of the last call made with OPT_TRACE on:

@@ -910,6 +910,116 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
 }
 
 // Host-memory form: stage the inputs in a device buffer, run, copy back.
+int props_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const int64_t* member_idx,
+               const ahf_params* prm, const ahf_result* res, const int64_t* bound_idx, const void* phi, double* props,
+               cudaStream_t s) {
+  int rc = validate(p, halos, n_halos, prm, res, bound_idx);
+  if (rc) return rc;
+  if (n_halos > 0 && (!phi || !props)) return fail(AHF_ERR_INVALID, "phi and props must not be NULL");
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  if ((rc = validate_slots(halos, n_halos, n_slots, member_idx != nullptr))) return rc;
+  if (n_halos == 0) return AHF_OK;
+  // descriptors in the caller's order; chunks over each halo's slots (an
+  // upper bound of its bound list; chunks past the list do no work)
+  std::vector<HaloDev> hd((size_t)n_halos);
+  for (int64_t h = 0; h < n_halos; ++h) fill_halo_dev(halos[h], p->coord_type, prm->box, (int)h, hd[(size_t)h]);
+  std::vector<int> chunk_halo, halo_chunk0((size_t)n_halos + 1);
+  std::vector<long long> chunk_start;
+  for (int64_t h = 0; h < n_halos; ++h) {
+    halo_chunk0[(size_t)h] = (int)chunk_halo.size();
+    for (long long o = 0; o < halos[h].count; o += PROPS_CHUNK) {
+      chunk_halo.push_back((int)h);
+      chunk_start.push_back(o);
+    }
+  }
+  halo_chunk0[(size_t)n_halos] = (int)chunk_halo.size();
+  const int n_chunks = (int)chunk_halo.size();
+  PropsLaunch L{};
+  int* hc0 = nullptr;
+  auto layout = [&](Bump& B, bool set) {
+    HaloDev* d = B.take<HaloDev>((size_t)n_halos);
+    int* ch = B.take<int>((size_t)n_chunks + 1);
+    long long* cs = B.take<long long>((size_t)n_chunks + 1);
+    int* h0 = B.take<int>((size_t)n_halos + 1);
+    double* part = B.take<double>((size_t)n_chunks * PROPS_PART + 1);
+    if (set) { L.halos = d; L.chunk_halo = ch; L.chunk_start = cs; hc0 = h0; L.part = part; }
+  };
+  Bump sizing{nullptr, 0, 0};
+  layout(sizing, false);
+  if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
+  if ((rc = begin_call(c, s))) return rc;
+  Bump B{c->ws, 0, c->ws_bytes};
+  layout(B, true);
+  char* pin = nullptr;
+  if ((rc = pin_acquire(c, sizing.used + 4096, &pin))) return rc;
+  size_t po = 0;
+  auto stage = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    po = align_up(po, 256);
+    std::memcpy(pin + po, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, pin + po, bytes, cudaMemcpyHostToDevice, s);
+    po += bytes;
+    return e;
+  };
+  AHF_CUDA(stage((void*)L.halos, hd.data(), sizeof(HaloDev) * (size_t)n_halos));
+  AHF_CUDA(stage((void*)L.chunk_halo, chunk_halo.data(), sizeof(int) * (size_t)n_chunks));
+  AHF_CUDA(stage((void*)L.chunk_start, chunk_start.data(), sizeof(long long) * (size_t)n_chunks));
+  AHF_CUDA(stage(hc0, halo_chunk0.data(), sizeof(int) * ((size_t)n_halos + 1)));
+  if ((rc = pin_release(c, s))) return rc;
+  L.p = to_dev(p);
+  L.frame.box = prm->box;
+  L.G = prm->G;
+  L.H = prm->H;
+  L.n_halos = (int)n_halos;
+  L.res = res;
+  L.bound_idx = (const long long*)bound_idx;
+  L.phi = phi;
+  L.phi_f64 = prm->precision == AHF_PREC_FP64 ? 1 : 0;
+  L.halo_chunk0 = hc0;
+  L.n_chunks = n_chunks;
+  L.props = props;
+  AHF_CUDA(launch_properties(L, s));
+  reset_stats(c);
+  c->stats.launches = (n_chunks > 0 ? 2 : 0) + 1;
+  return end_call(c, s);
+}
+
+int match_impl(ahf_ctx* c, int64_t n_ids, const int64_t* ids_a, const int64_t* off_a, const int64_t* cnt_a,
+               int64_t n_a, const int64_t* ids_b, const int64_t* off_b, const int64_t* cnt_b, int64_t n_b,
+               int64_t* best, int64_t* shared, double* xi, cudaStream_t s) {
+  if (n_ids < 0 || n_a < 0 || n_b < 0) return fail(AHF_ERR_INVALID, "negative size");
+  if (n_ids >= ((int64_t)1 << 40)) return fail(AHF_ERR_INVALID, "n_ids above 2^40");
+  if (n_a > 0x7fffffff || n_b > 0x7fffffff) return fail(AHF_ERR_INVALID, "catalogue above 2^31-1 haloes");
+  if (n_a > 0 && (!ids_a || !off_a || !cnt_a || !best || !shared || !xi))
+    return fail(AHF_ERR_INVALID, "first catalogue or outputs NULL");
+  if (n_b > 0 && (!ids_b || !off_b || !cnt_b)) return fail(AHF_ERR_INVALID, "second catalogue NULL");
+  if (n_a == 0) return AHF_OK;
+  Bump sizing{nullptr, 0, 0};
+  sizing.take<int>((size_t)std::max<int64_t>(n_ids, 1));
+  int rc;
+  if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
+  if ((rc = begin_call(c, s))) return rc;
+  Bump B{c->ws, 0, c->ws_bytes};
+  MatchLaunch L{};
+  L.label = B.take<int>((size_t)std::max<int64_t>(n_ids, 1));
+  if (n_ids) AHF_CUDA(cudaMemsetAsync(L.label, 0xff, sizeof(int) * (size_t)n_ids, s));
+  L.n_ids = n_ids;
+  L.ids_a = (const long long*)ids_a; L.off_a = (const long long*)off_a; L.cnt_a = (const long long*)cnt_a;
+  L.n_a = (int)n_a;
+  L.ids_b = (const long long*)ids_b; L.off_b = (const long long*)off_b; L.cnt_b = (const long long*)cnt_b;
+  L.n_b = (int)n_b;
+  L.err = c->err_dev;
+  L.best = (long long*)best; L.shared = (long long*)shared; L.xi = xi;
+  AHF_CUDA(launch_match(L, s));
+  reset_stats(c);
+  c->stats.launches = (n_b > 0 ? 1 : 0) + 1;
+  return end_call(c, s);
+}
+
 // The device address of a page-locked, mapped host buffer (cudaHostAlloc,
 // cudaHostRegister), or NULL for pageable memory.
 void* mapped_address(const void* host) {
@@ -1158,6 +1268,9 @@ int ahf_sync(ahf_ctx* c) {
   if (e & ERR_TIMEOUT) return fail(AHF_ERR_TIMEOUT, "a bounded device wait gave up");
   if (e & ERR_BAD_INDEX) return fail(AHF_ERR_INVALID, "a member index was out of range");
   if (e & ERR_CAPACITY) return fail(AHF_ERR_INVALID, "a halo exceeded its size class");
+  if (e & ERR_ID_RANGE) return fail(AHF_ERR_INVALID, "a catalogue particle id was out of range");
+  if (e & ERR_SHARED_ID) return fail(AHF_ERR_INVALID, "a particle id is in two haloes of the second catalogue");
+  if (e & ERR_MATCH_TABLE) return fail(AHF_ERR_INVALID, "a halo met more than 2048 haloes of the second catalogue");
   return AHF_OK;
 }
 
@@ -1182,6 +1295,23 @@ int ahf_unbind_batch_host(ahf_ctx* c, const ahf_particles* p, const ahf_halo* ha
   std::lock_guard<std::mutex> g(c->mu);
   return host_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, n_bins, r_min_frac,
                    prof, (cudaStream_t)stream);
+}
+
+int ahf_halo_properties(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                        const int64_t* member_idx, const ahf_params* prm, const ahf_result* res,
+                        const int64_t* bound_idx, const void* phi, double* props, void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return props_impl(c, p, halos, n_halos, member_idx, prm, res, bound_idx, phi, props, (cudaStream_t)stream);
+}
+
+int ahf_match_catalogs(ahf_ctx* c, int64_t n_ids, const int64_t* ids_a, const int64_t* off_a, const int64_t* cnt_a,
+                       int64_t n_a, const int64_t* ids_b, const int64_t* off_b, const int64_t* cnt_b, int64_t n_b,
+                       int64_t* best, int64_t* shared, double* xi, void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return match_impl(c, n_ids, ids_a, off_a, cnt_a, n_a, ids_b, off_b, cnt_b, n_b, best, shared, xi,
+                    (cudaStream_t)stream);
 }
 
 int ahf_get_trace(ahf_ctx* c, int64_t* host, int64_t n_halos) {

@@ -203,4 +203,46 @@ constexpr int PROFILE_CHUNK = 4096;
 int profile_max_bins();
 cudaError_t launch_profile(const ProfileLaunch &L, const int *halo_chunk0, cudaStream_t s);
 
+// Integral properties of bound sets (spin parameter, energies, rotation-curve
+// peak), chunked like the profile: per chunk partial moments, a second pass
+// for the inclusive-mass prefix, then one combine per halo.
+constexpr int PROPS_CHUNK = 4096;
+constexpr int PROPS_PART = 20;           // doubles of per-chunk partials
+struct PropsLaunch {
+  ParticlesDev p;
+  FrameDev frame;
+  double G, H;
+  const HaloDev *halos;                  // caller order
+  int n_halos;
+  const ahf_result *res;
+  const long long *bound_idx;            // particle indices, radial order per halo
+  const void *phi;                       // float (mixed) or double (FP64) per slot
+  int phi_f64;
+  const int *chunk_halo;
+  const long long *chunk_start;
+  const int *halo_chunk0;                // [n_halos + 1]
+  int n_chunks;
+  double *part;                          // [n_chunks][PROPS_PART]
+  double *props;                         // [n_halos][AHF_PROP_FIELDS]
+};
+cudaError_t launch_properties(const PropsLaunch &L, cudaStream_t s);
+
+// Cross-identification of two catalogues by xi = N_shared^2 / (N_1 N_2).
+constexpr int MATCH_TABLE = 2048;        // distinct second-catalogue haloes one halo may meet
+constexpr int ERR_ID_RANGE = 8;          // a particle id outside [0, n_ids)
+constexpr int ERR_SHARED_ID = 16;        // a particle in two haloes of the second catalogue
+constexpr int ERR_MATCH_TABLE = 32;      // a halo met more than MATCH_TABLE haloes
+struct MatchLaunch {
+  long long n_ids;
+  const long long *ids_a, *off_a, *cnt_a;
+  int n_a;
+  const long long *ids_b, *off_b, *cnt_b;
+  int n_b;
+  int *label;                            // [n_ids] workspace
+  int *err;
+  long long *best, *shared;
+  double *xi;
+};
+cudaError_t launch_match(const MatchLaunch &L, cudaStream_t s);
+
 }  // namespace ahf
