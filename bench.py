@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--properties", action="store_true",
+                    help="also time ahf_halo_properties and ahf_match_catalogs on the step's outputs")
     ap.add_argument("--trace", action="store_true",
                     help="after timing, one traced step: per-halo phase times of the on-chip kernels")
     ap.add_argument("--no-graphs", dest="graphs", action="store_false",
@@ -432,6 +434,9 @@ def run_ahf(args):
             "timed_wall_s": t_wall}
     clocks = clk.summary()
     line["clocks"] = clocks
+    if rank == 0 and args.properties:
+        line["properties"] = time_properties(ctx, parts, hal, prm, pop, stream, flush)
+        log(f"properties {line['properties']['properties_ms']:.3f} ms, matching {line['properties']['match_ms']:.3f} ms")
     if args.trace:
         from paper_0904_3662_gb300 import trace_report
         ctx.set_option(ahf.OPT_TIMING, 0)
@@ -462,6 +467,38 @@ def run_ahf(args):
         print(json.dumps(line))
     barrier(world)
     return 0
+
+
+def time_properties(ctx, parts, hal, prm, pop, stream, flush, steps=5):
+    """ahf_halo_properties over the step's outputs, and ahf_match_catalogs of
+    the catalogue with itself (device time per call, after a warm-up)."""
+    import torch
+    from paper_0904_3662_gb300 import ahf
+    out = ctx.unbind_batch(parts, hal, prm, stream=stream)
+    torch.cuda.synchronize()
+    res = ahf.results_to_numpy(out["res"])
+    off = torch.from_numpy(pop.offset.astype(np.int64)).cuda()
+    cnt = torch.from_numpy(res["n_bound"].astype(np.int64)).cuda()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+    t_p = timed(lambda: ctx.halo_properties(parts, hal, prm, out, stream=stream))
+    t_m = timed(lambda: ctx.match_catalogs(pop.n_particles, out["bound_idx"], off, cnt, out["bound_idx"], off, cnt,
+                                           stream=stream))
+    return {"properties_ms": t_p, "match_ms": t_m,
+            "what": "ahf_halo_properties on the batch's bound sets; ahf_match_catalogs of the catalogue with itself"}
 
 
 def time_plain(ctx, parts, hal, prm, out, stream, units, flush, steps=2):

@@ -87,7 +87,24 @@ typedef struct ahf_params {
                         |(|u|^2 - 2|phi|) / 2|phi|| < band (default 1e-5)      */
   int32_t max_iter;  /* iteration cap (>= 1)                                    */
   int32_t precision; /* AHF_PREC_MIXED or AHF_PREC_FP64                         */
+  int32_t variant;   /* AHF_VAR_* bits (0: the method as described above)       */
+  int32_t reserved;  /* must be 0                                               */
 } ahf_params;
+
+/* ---- method variants (ahf_params.variant) ---------------------------------
+ * AHF_VAR_VBULK_INITIAL: the escape test uses the bulk velocity of the
+ *   initial member set in every iteration instead of the current set's.
+ * AHF_VAR_RETRUNCATE: after the unbinding converges, each halo with an r_vir
+ *   is cut to its bound particles within r_vir and unbound again (Appendix A
+ *   truncates the potential at r_vir).  Records, bound lists, phi and profile
+ *   rows describe the second pass; removed_iter keeps the first pass's
+ *   removals (candidates outside r_vir or removed by the second pass appear
+ *   only as missing from the bound list).  The call then reads the first
+ *   pass's records back to the host (it synchronises `stream` once).
+ *   ahf_unbind_batch, ahf_unbind_profile_batch and ahf_unbind_batch_host
+ *   only. */
+#define AHF_VAR_VBULK_INITIAL 1
+#define AHF_VAR_RETRUNCATE    2
 
 typedef struct ahf_particles {
   /* Structure-of-arrays particle store, n entries each.  Element type is
@@ -98,6 +115,11 @@ typedef struct ahf_particles {
   int64_t n;
   int32_t coord_type;
   int32_t reserved;  /* must be 0 */
+  /* Specific thermal energy of gas (SPH) particles, velocity^2 units, 0 for
+     collisionless ones; NULL = none.  With it the escape test is
+     |u|^2 + 2 u_th > 2|phi| (Sect. 2.1: the thermal energy of gas particles
+     counts in the unbinding), and every halo takes the multi-CTA class. */
+  const void *u_th;
 } ahf_particles;
 
 typedef struct ahf_halo {
@@ -300,7 +322,8 @@ int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
  *
  * Limits: n_halos <= AHF_STATIC_MAX_HALOS and every halo's count <=
  * AHF_STATIC_MAX_COUNT; larger requests return AHF_ERR_INVALID before any
- * work is enqueued.  Only AHF_PREC_MIXED.
+ * work is enqueued.  Only AHF_PREC_MIXED, no gas (u_th), and of the
+ * variants only AHF_VAR_VBULK_INITIAL.
  *
  * Scratch: the halo descriptors and work counters live in one fixed array
  * in device memory (about 3.8 MiB) that every GPU loading the library holds
@@ -397,6 +420,7 @@ int ahf_serve_create(ahf_serve **s, int device, size_t hbm_cap_bytes, const ahf_
  * [offset, offset + count) of p (count <= AHF_SERVE_MAX_COUNT).  The
  * candidates are copied before the call returns, so the caller may reuse p.
  * On success *req_id identifies the request.  Never blocks on the GPU.
+ * Requests carry no gas thermal energies (u_th must be NULL).
  * Errors: AHF_ERR_INVALID, AHF_ERR_NOMEM, AHF_ERR_FULL (no room in the ring
  * now: poll completed requests and retry). */
 int ahf_serve_submit(ahf_serve *s, const ahf_particles *p, const ahf_halo *halo, uint64_t *req_id);

@@ -74,6 +74,8 @@ class Params:
     box: float = 0.0
     max_iter: int = 100
     band: float = 1e-5
+    vbulk_initial: bool = False   # variant: v_bulk of the initial set in every iteration
+    retruncate: bool = False      # variant: unbind again within r_vir (second pass)
 
 
 def _f64(a):
@@ -88,6 +90,16 @@ def recentre(x, y, z, centre, box):
         d = np.where(d > half, d - box, d)
         d = np.where(d < -half, d + box, d)
     return d
+
+
+def gas_energy(pop, h, member_idx=None):
+    """The candidates' specific thermal energies (FP64), or None without gas."""
+    if getattr(pop, "u_th", None) is None:
+        return None
+    lo = int(pop.offset[h])
+    hi = lo + int(pop.count[h])
+    pidx = np.arange(lo, hi, dtype=np.int64) if member_idx is None else np.asarray(member_idx[lo:hi], np.int64)
+    return _f64(pop.u_th[pidx])
 
 
 def gather_sphere(pop, h, member_idx=None):
@@ -155,10 +167,13 @@ def virial(r, m, delta_rho):
     return r_vir, m_vir, k, status
 
 
-def unbind_halo(d, v, m, inside, params: Params, forced=None):
+def unbind_halo(d, v, m, inside, params: Params, forced=None, u_th=None):
     """Iterative unbinding of one halo (Appendix A; Sect. 2.1).
 
     d, v, m: FP64 candidates (in candidate order); inside: gather-sphere mask.
+    u_th: optional per-candidate specific thermal energy (gas particles): the
+    escape test becomes |u|^2 + 2 u_th > 2|phi| (Sect. 2.1: the thermal energy
+    of SPH gas particles counts in the unbinding).
     forced: optional per-candidate removal iteration (0 = never) used only for
     particles whose escape margin |(|u|^2 - 2|phi|) / 2|phi|| is below
     params.band (replay of another implementation's in-band decisions).
@@ -182,12 +197,15 @@ def unbind_halo(d, v, m, inside, params: Params, forced=None):
         n_iter += 1
         part_iter += int(alive.shape[0])
         ma = m[alive]
-        vbulk = (ma[:, None] * v[alive]).sum(axis=0) / ma.sum()
+        if n_iter == 1 or not params.vbulk_initial:
+            vbulk = (ma[:, None] * v[alive]).sum(axis=0) / ma.sum()
         # integrate along the radially ordered list (ties by candidate position)
         order = alive[np.lexsort((alive, r[alive]))]
         phi = potential_sorted(r[order], m[order], params.G, params.r_soft)
         u = v[order] - vbulk[None, :] + params.H * d[order]
         u2 = (u * u).sum(axis=1)
+        if u_th is not None:
+            u2 = u2 + 2.0 * u_th[order]
         two_phi = 2.0 * np.abs(phi)
         unbound = u2 > two_phi
         with np.errstate(divide="ignore", invalid="ignore"):
@@ -223,6 +241,26 @@ def unbind_halo(d, v, m, inside, params: Params, forced=None):
                 removed_iter=removed_iter, n_member=n_member, n_iter=n_iter,
                 part_iter=part_iter, n_band=n_band, status=status, vbulk=vbulk,
                 r_vir=r_vir, m_vir=m_vir, k_vir=k_vir)
+
+
+def retruncate_halo(o1, d, v, m, params: Params, u_th=None):
+    """Variant: Appendix A truncates the potential at r_vir; after the
+    unbinding converges, the bound particles within r_vir (all of them when
+    there is no r_vir) are unbound again as a new halo.  The result is the
+    second pass's, with the first pass's per-candidate removal iterations
+    (candidates the second pass drops are visible only in the bound list)."""
+    cand = o1["order"]
+    if cand.shape[0] == 0:
+        return o1
+    inside = np.ones(cand.shape[0], dtype=bool)
+    if o1["r_vir"] > 0.0:
+        dc = d[cand]
+        r2 = dc[:, 0] * dc[:, 0] + dc[:, 1] * dc[:, 1] + dc[:, 2] * dc[:, 2]
+        inside = r2 <= o1["r_vir"] * o1["r_vir"]       # the gather sphere's test, radius r_vir
+    o2 = unbind_halo(d[cand], v[cand], m[cand], inside, params, None, None if u_th is None else u_th[cand])
+    o2["order"] = cand[o2["order"]]
+    o2["removed_iter"] = o1["removed_iter"]
+    return o2
 
 
 def profile(r_sorted, m_sorted, r_vir, n_bins, r_min_frac, G):
@@ -330,7 +368,10 @@ def unbind_population(pop, params: Params, halos=None, member_idx=None,
         pidx, d, v, m, inside = gather_sphere(pop, h, member_idx)
         lo = int(pop.offset[h])
         fz = None if forced is None else np.asarray(forced[lo:lo + pidx.shape[0]])
-        o = unbind_halo(d, v, m, inside, p, fz)
+        uth = gas_energy(pop, h, member_idx)
+        o = unbind_halo(d, v, m, inside, p, fz, uth)
+        if p.retruncate:
+            o = retruncate_halo(o, d, v, m, p, uth)
         o["bound_idx"] = pidx[o["order"]]
         if n_bins > 0:
             o["profile"] = profile(o["r"], m[o["order"]], o["r_vir"], n_bins, r_min_frac, p.G)
@@ -380,6 +421,8 @@ def _subset(pop, halos):
     for a in ("x", "y", "z", "vx", "vy", "vz"):
         setattr(sub, a, getattr(pop, a)[idx])
     sub.m = None if pop.m is None else pop.m[idx]
+    if getattr(pop, "u_th", None) is not None:
+        sub.u_th = pop.u_th[idx]
     cnt = pop.count[halos]
     sub.count = cnt.copy()
     sub.offset = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)

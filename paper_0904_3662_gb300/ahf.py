@@ -23,6 +23,7 @@ ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2,
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
+VAR_VBULK_INITIAL, VAR_RETRUNCATE = 1, 2
 OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE = 1, 2, 3, 4, 5, 6
 TRACE_FIELDS = 8
 N_PHASES = 12
@@ -58,14 +59,15 @@ class AHFError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("H", ctypes.c_double), ("delta_rho", ctypes.c_double),
                 ("r_soft", ctypes.c_double), ("box", ctypes.c_double), ("band", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Particles(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
                 ("m", ctypes.c_void_p), ("m0", ctypes.c_double), ("n", ctypes.c_int64),
-                ("coord_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("coord_type", ctypes.c_int32), ("reserved", ctypes.c_int32), ("u_th", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -140,10 +142,11 @@ class Params:
     band: float = 1e-5
     max_iter: int = 100
     precision: int = PREC_MIXED
+    variant: int = 0
 
     def c(self):
         return _Params(self.G, self.H, self.delta_rho, self.r_soft, self.box, self.band,
-                       self.max_iter, self.precision)
+                       self.max_iter, self.precision, self.variant, 0)
 
 
 def halo_array(centre, radius, offset, count):
@@ -170,6 +173,7 @@ class Particles:
     m: object = None
     m0: float = 0.0
     coord_type: int = COORD_F32_REL
+    u_th: object = None       # gas: specific thermal energy per particle, or None
 
     @property
     def n(self):
@@ -183,7 +187,7 @@ class Particles:
                 return a.ctypes.data
             return a.data_ptr()
         return _Particles(ptr(self.x), ptr(self.y), ptr(self.z), ptr(self.vx), ptr(self.vy), ptr(self.vz),
-                          ptr(self.m), float(self.m0), self.n, int(self.coord_type), 0)
+                          ptr(self.m), float(self.m0), self.n, int(self.coord_type), 0, ptr(self.u_th))
 
 
 def _stream_ptr(stream):
@@ -447,8 +451,9 @@ def particles_from_population(pop, device="cuda"):
     def t(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(device)
     m = None if pop.m is None else t(pop.m)
+    u = None if getattr(pop, "u_th", None) is None else t(pop.u_th)
     return Particles(t(pop.x), t(pop.y), t(pop.z), t(pop.vx), t(pop.vy), t(pop.vz), m, float(pop.m0),
-                     int(pop.coord_type))
+                     int(pop.coord_type), u)
 
 
 def halos_from_population(pop):

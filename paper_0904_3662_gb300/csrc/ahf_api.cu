@@ -141,6 +141,8 @@ struct ahf_ctx {
   bool timing = false;
   bool host_direct = false;          // host entry: use mapped page-locked buffers in place
   bool graphs = false;               // on-chip launch sequence as a replayed CUDA graph
+  void* aux = nullptr;               // second-pass member lists (AHF_VAR_RETRUNCATE)
+  size_t aux_bytes = 0;
   bool trace = false;                // per-halo timestamps from the on-chip kernels
   long long* trace_dev = nullptr;    // [n][AHF_TRACE_FIELDS] of the last traced call
   int64_t trace_cap = 0;             // haloes trace_dev holds
@@ -285,6 +287,9 @@ int validate(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, con
   if (prm->max_iter < 1) return fail(AHF_ERR_INVALID, "max_iter must be >= 1");
   if (prm->precision != AHF_PREC_MIXED && prm->precision != AHF_PREC_FP64)
     return fail(AHF_ERR_INVALID, "unknown precision mode %d", prm->precision);
+  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE))
+    return fail(AHF_ERR_INVALID, "unknown variant bits %d", prm->variant);
+  if (prm->reserved != 0) return fail(AHF_ERR_INVALID, "params.reserved must be 0");
   if (!(prm->G > 0.0) || !std::isfinite(prm->G)) return fail(AHF_ERR_INVALID, "G must be > 0");
   if (!std::isfinite(prm->H)) return fail(AHF_ERR_INVALID, "H must be finite");
   if (!(prm->delta_rho > 0.0) || !std::isfinite(prm->delta_rho)) return fail(AHF_ERR_INVALID, "delta_rho must be > 0");
@@ -331,8 +336,9 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   for (int64_t h = 0; h < n_halos; ++h) {
     const int64_t n = halos[h].count;
     int k = NV;
-    // the all-FP64 mode runs in the multi-CTA class only
-    if (prm->precision == AHF_PREC_MIXED)
+    // the all-FP64 mode and gas (thermal energy per particle) run in the
+    // multi-CTA class only
+    if (prm->precision == AHF_PREC_MIXED && !p->u_th)
       for (int v = 0; v < NV; ++v)
         if (n <= caps[v]) { k = v; break; }
     cls[h] = k;
@@ -361,20 +367,26 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   return AHF_OK;
 }
 
+// (the device structs are zeroed first: their bytes, padding included, are
+// part of the graph key)
 ParamsDev to_dev(const ahf_params* prm) {
   ParamsDev d;
+  std::memset(&d, 0, sizeof d);
   d.G = prm->G; d.H = prm->H; d.delta_rho = prm->delta_rho; d.r_soft = prm->r_soft; d.band = prm->band;
   d.Gf = (float)prm->G; d.Hf = (float)prm->H; d.r_soft_f = (float)prm->r_soft; d.band_f = (float)prm->band;
   d.crit = prm->delta_rho * (4.0 * M_PI / 3.0);
   d.crit_f = (float)d.crit;
   d.max_iter = prm->max_iter;
   d.precision = prm->precision;
+  d.vbulk_initial = (prm->variant & AHF_VAR_VBULK_INITIAL) ? 1 : 0;
   return d;
 }
 
 ParticlesDev to_dev(const ahf_particles* p) {
   ParticlesDev d;
+  std::memset(&d, 0, sizeof d);
   d.x = p->x; d.y = p->y; d.z = p->z; d.vx = p->vx; d.vy = p->vy; d.vz = p->vz; d.m = p->m;
+  d.u_th = p->u_th;
   d.m0 = p->m0; d.m0f = (float)p->m0; d.coord_type = p->coord_type; d.n = p->n;
   return d;
 }
@@ -455,7 +467,7 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
 // and single-CTA variants form the rows from the bound set they hold on chip;
 // haloes of the cluster and multi-CTA classes get theirs from the profile
 // kernels afterwards.
-int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                 const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
                 int32_t* removed_iter, cudaStream_t s, int32_t n_bins = 0, double r_min_frac = 0.0,
                 double* prof = nullptr) {
@@ -504,6 +516,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       uint32_t* vb = B.take<uint32_t>(nf);
       char* wm = B.take<char>(nf * 4 * es);
       char* r = B.take<char>(nf * es);
+      char* uth = B.take<char>(p->u_th ? nf * es : 0);
       long long* mc = B.take<long long>(nf);
       char* rcp = B.take<char>(nf * es);
       int2* trg = B.take<int2>((size_t)n_tiles);
@@ -515,6 +528,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       long long* pre = B.take<long long>((size_t)n_tiles * 3);
       if (G) {
         G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
+        G->uth = p->u_th ? uth : nullptr;
         G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
         G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
       }
@@ -551,6 +565,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   }
 
   OutputsDev O;
+  std::memset(&O, 0, sizeof O);
   O.res = out; O.bound_idx = (long long*)bound_idx; O.phi = phi; O.removed_iter = removed_iter;
   O.member_idx = (const long long*)member_idx; O.n_slots = n_slots; O.err = c->err_dev;
   const ParticlesDev pd = to_dev(p);
@@ -575,6 +590,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     if (c->trace_cap < n_halos) {
       if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
       if (c->trace_dev) cudaFree(c->trace_dev);
+  if (c->aux) cudaFree(c->aux);
       c->trace_dev = nullptr;
       c->trace_cap = 0;
       if (cudaMalloc(&c->trace_dev, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos) != cudaSuccess) {
@@ -806,6 +822,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
                int32_t* removed_iter, cudaStream_t s) {
   int rc = validate(p, halos, n_halos, prm, out, bound_idx);
   if (rc) return rc;
+  if (prm->variant & AHF_VAR_RETRUNCATE) return fail(AHF_ERR_INVALID, "the plain path has no AHF_VAR_RETRUNCATE");
   int64_t n_slots = p->n;
   if (member_idx) {
     n_slots = 0;
@@ -830,6 +847,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     uint32_t* vb = B.take<uint32_t>(nf);
     char* wm = B.take<char>(nf * 4 * es);
     char* r = B.take<char>(nf * es);
+    char* uth = B.take<char>(p->u_th ? nf * es : 0);
     long long* mc = B.take<long long>(nf);
     char* rcp = B.take<char>(nf * es);
     int2* trg = B.take<int2>((size_t)max_tiles);
@@ -842,6 +860,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     if (G) {
       G->halos = hd; G->any_active = words + 8; G->key_or_and = (unsigned long long*)(words + 10);
       G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
+      G->uth = p->u_th ? uth : nullptr;
       G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
       G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
     }
@@ -1020,6 +1039,55 @@ int match_impl(ahf_ctx* c, int64_t n_ids, const int64_t* ids_a, const int64_t* o
   return end_call(c, s);
 }
 
+// The unbinding, with AHF_VAR_RETRUNCATE as a second pass over each halo's
+// first-pass bound particles within its r_vir (the first pass's bound lists
+// become the second pass's member lists).
+int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
+                int32_t* removed_iter, cudaStream_t s, int32_t n_bins = 0, double r_min_frac = 0.0,
+                double* prof = nullptr) {
+  if (!prm || !(prm->variant & AHF_VAR_RETRUNCATE))
+    return unbind_pass(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, s, n_bins,
+                       r_min_frac, prof);
+  ahf_params p1 = *prm;
+  p1.variant &= ~AHF_VAR_RETRUNCATE;
+  int rc = unbind_pass(c, p, halos, n_halos, member_idx, &p1, out, bound_idx, phi, removed_iter, s);
+  if (rc || n_halos == 0) return rc;
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  // the first pass's bound lists (particle indices) as member lists
+  const size_t need = sizeof(int64_t) * (size_t)std::max<int64_t>(n_slots, 1);
+  if (need > c->aux_bytes) {
+    if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
+    if (c->aux) cudaFree(c->aux);
+    c->aux = nullptr;
+    c->aux_bytes = 0;
+    if (cudaMalloc(&c->aux, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AHF_ERR_NOMEM, "second-pass member lists (%zu bytes)", need);
+    }
+    c->aux_bytes = need;
+  }
+  int64_t* members = (int64_t*)c->aux;
+  std::vector<ahf_result> r1((size_t)n_halos);
+  if (n_slots) AHF_CUDA(cudaMemcpyAsync(members, bound_idx, (size_t)n_slots * 8, cudaMemcpyDeviceToDevice, s));
+  AHF_CUDA(cudaMemcpyAsync(r1.data(), out, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
+  AHF_CUDA(cudaStreamSynchronize(s));
+  c->stats.host_syncs += 1;
+  std::vector<ahf_halo> h2(halos, halos + n_halos);
+  for (int64_t h = 0; h < n_halos; ++h) {
+    h2[(size_t)h].count = r1[(size_t)h].n_bound;
+    if (r1[(size_t)h].r_vir > 0.0) h2[(size_t)h].radius = r1[(size_t)h].r_vir;
+  }
+  // the second pass: records, bound lists, phi and rows; removed_iter stays
+  ahf_particles p2 = *p;
+  return unbind_pass(c, &p2, h2.data(), n_halos, members, &p1, out, bound_idx, phi, nullptr, s, n_bins,
+                     r_min_frac, prof);
+}
+
 // The device address of a page-locked, mapped host buffer (cudaHostAlloc,
 // cudaHostRegister), or NULL for pageable memory.
 void* mapped_address(const void* host) {
@@ -1047,6 +1115,7 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   const size_t n = (size_t)p->n;
   const size_t ps = prm->precision == AHF_PREC_FP64 ? 8 : 4;
   const size_t bytes = align_up(6 * n * es, 256) * 1 + align_up(p->m ? n * es : 0, 256) +
+                       align_up(p->u_th ? n * es : 0, 256) +
                        align_up(member_idx ? (size_t)n_slots * 8 : 0, 256) + align_up(sizeof(ahf_result) * (size_t)n_halos, 256) +
                        align_up((size_t)n_slots * 8, 256) + align_up(phi ? (size_t)n_slots * ps : 0, 256) +
                        align_up(removed_iter ? (size_t)n_slots * 4 : 0, 256) +
@@ -1070,9 +1139,9 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   // option allows), else staged through the context's device buffer
   auto direct = [&](const void* h) -> void* { return c->host_direct ? mapped_address(h) : nullptr; };
   ahf_particles dp = *p;
-  const void* src[7] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m};
-  const void** dst[7] = {&dp.x, &dp.y, &dp.z, &dp.vx, &dp.vy, &dp.vz, &dp.m};
-  for (int k = 0; k < 7; ++k) {
+  const void* src[8] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u_th};
+  const void** dst[8] = {&dp.x, &dp.y, &dp.z, &dp.vx, &dp.vy, &dp.vz, &dp.m, &dp.u_th};
+  for (int k = 0; k < 8; ++k) {
     if (!src[k]) continue;
     char* d = B.take<char>(n * es);
     if (void* m = direct(src[k])) {
@@ -1188,6 +1257,7 @@ int ahf_destroy(ahf_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->capture) cudaStreamDestroy(c->capture);
   if (c->trace_dev) cudaFree(c->trace_dev);
+  if (c->aux) cudaFree(c->aux);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->err_dev) cudaFree(c->err_dev);

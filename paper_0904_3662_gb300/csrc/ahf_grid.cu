@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(T) g_fill(GridLaunch L) {
       q.w = m;
       wm[g] = q;
       rr[g] = real_of(key[g], R());
+      if (L.uth) ((R*)L.uth)[g] = (R)(CT == AHF_COORD_F64 ? __ldg((const double*)L.p.u_th + pi)
+                                                         : (double)__ldg((const float*)L.p.u_th + pi));
 #pragma unroll
       for (int a = 0; a < 3; ++a) smv[a] += fix_real(mul_rn(m, v[a]), s_v);
     }
@@ -522,12 +524,15 @@ __global__ void __launch_bounds__(256) g_tile_scan(GridLaunch L, int final_pass)
     S.t_tot = carry[1];
     S.n_alive = carry[2];
     if (!final_pass) {
-      if (sizeof(R) == 4) {
-        const float mt = float_from_fix(carry[0], S.s_m);
-        for (int a = 0; a < 3; ++a) S.vbulk[a] = float_from_fix(S.mv[a], S.s_mv) / mt;
-      } else {
-        const double mt = double_from_fix(carry[0], S.s_m);
-        for (int a = 0; a < 3; ++a) S.vbulk_d[a] = double_from_fix(S.mv[a], S.s_mv) / mt;
+      // v_bulk of the current set (of the initial set with AHF_VAR_VBULK_INITIAL)
+      if (S.n_iter == 0 || !L.prm.vbulk_initial) {
+        if (sizeof(R) == 4) {
+          const float mt = float_from_fix(carry[0], S.s_m);
+          for (int a = 0; a < 3; ++a) S.vbulk[a] = float_from_fix(S.mv[a], S.s_mv) / mt;
+        } else {
+          const double mt = double_from_fix(carry[0], S.s_m);
+          for (int a = 0; a < 3; ++a) S.vbulk_d[a] = double_from_fix(S.mv[a], S.s_mv) / mt;
+        }
       }
       S.removed = 0;
       S.rem_m = 0;
@@ -580,6 +585,7 @@ __global__ void __launch_bounds__(T) g_apply(GridLaunch L, int iter) {
   // pass 1: thread totals over its IPT consecutive elements
   V4 wmv[IPT];
   R rv[IPT];
+  const R* uth = (const R*)L.uth;
   long long a = 0, b = 0;
 #pragma unroll
   for (int q = 0; q < IPT; ++q) {
@@ -611,7 +617,8 @@ __global__ void __launch_bounds__(T) g_apply(GridLaunch L, int iter) {
       const long long rfix = fix_real(m * ri, s_r);
       const R phi = phi_real(from_fix<R>(M, s_m), ri, from_fix<R>(Ttot - Pp, s_r), P);
       const R ux = wmv[q].x - vb[0], uy = wmv[q].y - vb[1], uz = wmv[q].z - vb[2];
-      const R u2 = fma(uz, uz, fma(uy, uy, ux * ux));
+      R u2 = fma(uz, uz, fma(uy, uy, ux * ux));
+      if (uth) u2 += (R)2 * uth[g0 + q];              // gas: |u|^2 + 2 u_th (Sect. 2.1)
       const R two_phi = (R)-2 * phi;
       if (fabs(u2 - two_phi) < band * two_phi) ++nband;
       if (u2 > two_phi) {

@@ -12,6 +12,7 @@ namespace ahf {
 // Device-side view of the caller's particle store.
 struct ParticlesDev {
   const void *x, *y, *z, *vx, *vy, *vz, *m;
+  const void *u_th;    // gas: specific thermal energy per particle, or NULL
   double m0;
   float m0f;
   int coord_type;
@@ -50,6 +51,7 @@ struct ParamsDev {
   double crit;         // delta_rho * 4 pi / 3
   int max_iter;
   int precision;
+  int vbulk_initial;   // AHF_VAR_VBULK_INITIAL: v_bulk of the initial set throughout
 };
 
 struct OutputsDev {
@@ -155,6 +157,7 @@ struct GridLaunch {
   uint32_t *val_x;         // the sorted candidate positions
   void *wm;                // (w.x, w.y, w.z, m), m's sign bit = removed: float4 / 4 doubles
   void *r;                 // radius: float / double
+  void *uth;               // gas: thermal energy in radial order (float / double), or NULL
   long long *mc;           // compacted inclusive mass (final pass)
   void *rc;                // compacted radius (final pass): float / double
   // tiles

@@ -478,10 +478,13 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       cluster_scan_totals<NT, CS>(S, X, rank);
       if (tid == 0) {
         // v_bulk = sum m v / sum m of the current set, from the exact sums
-        const float mt = float_from_fix(S.c_tot[0], s_m);
-        S.vb[0] = float_from_fix(S.mv[0], s_v) / mt;
-        S.vb[1] = float_from_fix(S.mv[1], s_v) / mt;
-        S.vb[2] = float_from_fix(S.mv[2], s_v) / mt;
+        // (with AHF_VAR_VBULK_INITIAL the first iteration's value is kept)
+        if (n_iter == 1 || !P.vbulk_initial) {
+          const float mt = float_from_fix(S.c_tot[0], s_m);
+          S.vb[0] = float_from_fix(S.mv[0], s_v) / mt;
+          S.vb[1] = float_from_fix(S.mv[1], s_v) / mt;
+          S.vb[2] = float_from_fix(S.mv[2], s_v) / mt;
+        }
         S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
         S.acc_n = 0;
         S.acc_band = 0;

@@ -284,6 +284,9 @@ int check_params(const ahf_params* prm) {
   if (prm->max_iter < 1) return set_last_error_fmt(AHF_ERR_INVALID, "max_iter < 1");
   if (prm->precision != AHF_PREC_MIXED && prm->precision != AHF_PREC_FP64)
     return set_last_error_fmt(AHF_ERR_INVALID, "unknown precision %d", prm->precision);
+  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE))
+    return set_last_error_fmt(AHF_ERR_INVALID, "unknown variant bits %d", prm->variant);
+  if (prm->reserved != 0) return set_last_error_fmt(AHF_ERR_INVALID, "params.reserved must be 0");
   return AHF_OK;
 }
 
@@ -382,6 +385,7 @@ int ahf_serve_submit(ahf_serve* s, const ahf_particles* p, const ahf_halo* h, ui
   if (s->n_arr == 6 && p->m0 != s->m0)
     return set_last_error_fmt(AHF_ERR_INVALID, "m0 %g differs from the instance's %g", p->m0, s->m0);
   if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz) return set_last_error_fmt(AHF_ERR_INVALID, "NULL array");
+  if (p->u_th) return set_last_error_fmt(AHF_ERR_INVALID, "serving takes no gas thermal energies (u_th)");
   if (h->offset < 0 || h->count < 0 || h->offset + h->count > p->n)
     return set_last_error_fmt(AHF_ERR_INVALID, "halo slots [%lld, %lld) outside the %lld particles",
                               (long long)h->offset, (long long)(h->offset + h->count), (long long)p->n);

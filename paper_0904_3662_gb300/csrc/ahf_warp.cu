@@ -240,16 +240,20 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     long long part_iter = 0, n_band = 0;
     int n_alive = n_mem;
     bool converged = false;
+    float vb0 = 0.0f, vb1 = 0.0f, vb2 = 0.0f;
     while (n_alive > 0 && n_iter < P.max_iter) {
       ++n_iter;
       part_iter += n_alive;
       long long M_tot, T_tot;
       long long tm = warp_excl(tm_own, lane, M_tot);
       long long tr = warp_excl(tr_own, lane, T_tot);
-      const float mt = float_from_fix(M_tot, s_m);
-      const float vb0 = float_from_fix(mv[0], s_v) / mt;
-      const float vb1 = float_from_fix(mv[1], s_v) / mt;
-      const float vb2 = float_from_fix(mv[2], s_v) / mt;
+      // v_bulk of the current set (of the initial set with AHF_VAR_VBULK_INITIAL)
+      if (n_iter == 1 || !P.vbulk_initial) {
+        const float mt = float_from_fix(M_tot, s_m);
+        vb0 = float_from_fix(mv[0], s_v) / mt;
+        vb1 = float_from_fix(mv[1], s_v) / mt;
+        vb2 = float_from_fix(mv[2], s_v) / mt;
+      }
       long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
       for (int k = 0; k < ipt; ++k) {

@@ -146,6 +146,7 @@ class Population:
     count: np.ndarray           # (H,)   int64
     r200: np.ndarray            # (H,)   float64, generator metadata
     conc: np.ndarray            # (H,)   float64, generator metadata
+    u_th: np.ndarray | None = None   # specific thermal energy (km/s)^2 of gas particles, 0 elsewhere
 
     @property
     def n_particles(self) -> int:
@@ -300,6 +301,17 @@ def precision_sweep(seed=SEED_BASE + 4, n_halos=100_000, n_lo=100, n_hi=100_000)
     return halo_batch(seed=seed, n_halos=n_halos, n_lo=n_lo, n_hi=n_hi,
                       cont_frac=0.10, coord_type=COORD_F64,
                       name=f"sweep_{n_halos}_nfw_{n_lo}-{n_hi}_cont10_f64")
+
+
+def with_gas(pop, frac=0.3, u_max=5e4, seed=SEED_BASE + 7):
+    """A copy of pop in which a random fraction of the particles are gas with
+    a specific thermal energy uniform on [0, u_max) (km/s)^2 (the others 0),
+    stored in the coordinates' precision."""
+    rng = np.random.default_rng(seed)
+    n = pop.n_particles
+    gas = rng.uniform(0.0, 1.0, n) < frac
+    u = np.where(gas, rng.uniform(0.0, u_max, n), 0.0).astype(pop.x.dtype)
+    return dataclasses.replace(pop, u_th=u, name=pop.name + f"_gas{int(frac * 100)}")
 
 
 def serving_stream(seed=SEED_BASE + 5, n_requests=50_000, rate_hz=10_000.0,

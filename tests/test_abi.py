@@ -38,8 +38,8 @@ def test_binding_lists_every_symbol():
 
 def test_struct_layouts():
     from paper_0904_3662_gb300 import ahf
-    assert ctypes.sizeof(ahf._Params) == 6 * 8 + 2 * 4
-    assert ctypes.sizeof(ahf._Particles) == 7 * 8 + 8 + 8 + 2 * 4
+    assert ctypes.sizeof(ahf._Params) == 6 * 8 + 4 * 4
+    assert ctypes.sizeof(ahf._Particles) == 7 * 8 + 8 + 8 + 2 * 4 + 8
     assert ahf.HALO_DTYPE.itemsize == 48
     assert ahf.RESULT_DTYPE.itemsize == 88
     assert ahf.RESULT_DTYPE.fields["m_vir"][1] == 48
