@@ -345,6 +345,27 @@ int ahf_unbind_batch_static(const ahf_particles *p, const ahf_halo *halos, int64
                             const int64_t *member_idx, const ahf_params *prm, ahf_result *out,
                             int64_t *bound_idx, void *phi, int32_t *removed_iter, void *stream);
 
+/* ---- hosts and subhaloes ------------------------------------------------------ */
+
+/* Unbinding in dependency order (Sect. 2.1): parent[h] is the host of halo h
+ * (-1: a field halo); haloes are unbound deepest level first, and a halo's
+ * candidates lose the particles that any of its descendants bound (the
+ * paper's option of not including subhaloes in their hosts; particles a
+ * subhalo does not bind remain its host's candidates).  After each level a
+ * particle's owner is the halo of that level that bound it (the highest
+ * index if several did); a candidate is dropped from halo h when its owner
+ * descends from h.  Haloes share particles through member lists (their slots
+ * stay distinct).  Same buffers and results as ahf_unbind_batch, dropped
+ * candidates reported like those outside the sphere (removed_iter -1).  The
+ * call reads each level's kept-candidate counts back to the host (one
+ * stream synchronisation per level).  Not with AHF_VAR_RETRUNCATE.
+ * Errors: those of ahf_unbind_batch; AHF_ERR_INVALID for parent indices out
+ * of range or forming a cycle. */
+int ahf_unbind_hierarchy(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos, int64_t n_halos,
+                         const int64_t *parent, const int64_t *member_idx, const ahf_params *prm,
+                         ahf_result *out, int64_t *bound_idx, void *phi, int32_t *removed_iter,
+                         void *stream);
+
 /* ---- integral properties and catalogue matching --------------------------- */
 
 /* Integral properties of the bound sets an unbinding call produced (Sect.

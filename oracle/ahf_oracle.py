@@ -381,6 +381,64 @@ def unbind_population(pop, params: Params, halos=None, member_idx=None,
     return res
 
 
+def halo_depths(parent):
+    """Depth of every halo in the forest given by parent (-1: none); raises
+    ValueError on an index out of range or a cycle."""
+    parent = np.asarray(parent, dtype=np.int64)
+    n = parent.shape[0]
+    depth = np.full(n, -1, dtype=np.int64)
+    for h in range(n):
+        chain, k = [], h
+        while k >= 0 and depth[k] < 0:
+            if k in chain or parent[k] >= n or parent[k] < -1:
+                raise ValueError("parent indices must form a forest")
+            chain.append(k)
+            k = int(parent[k])
+        base = -1 if k < 0 else int(depth[k])
+        for i, c in enumerate(reversed(chain)):
+            depth[c] = base + 1 + i
+    return depth
+
+
+def unbind_hierarchy(pop, params: Params, parent, member_idx=None, forced=None):
+    """Hosts and subhaloes in dependency order (Sect. 2.1): subhaloes are
+    unbound before their hosts, and a host's candidates lose the particles
+    that any of its descendants bound (the paper's option of not including
+    subhaloes in their hosts; particles a subhalo does not bind stay the
+    host's candidates).  Haloes are taken deepest level first; within a level
+    independently, after which each particle's owner becomes the halo of that
+    level that bound it (the highest index if several did).  A candidate is
+    dropped from halo h when its owner descends from h.  Returns {h: result}
+    as unbind_population does (excluded candidates count as outside the
+    sphere: removed_iter -1).  forced: as for unbind_population."""
+    parent = np.asarray(parent, dtype=np.int64)
+    depth = halo_depths(parent)
+    p = dataclasses.replace(params, box=pop.box)
+    owner = {}
+
+    def descends(t, h):
+        while t >= 0:
+            t = int(parent[t])
+            if t == h:
+                return True
+        return False
+    res = {}
+    for d in sorted(set(depth.tolist()), reverse=True):
+        level = [h for h in range(len(parent)) if depth[h] == d]
+        for h in level:
+            pidx, dd, v, m, inside = gather_sphere(pop, h, member_idx)
+            keep = np.array([not descends(owner.get(int(q), -1), h) for q in pidx], dtype=bool)
+            lo = int(pop.offset[h])
+            fz = None if forced is None else np.asarray(forced[lo:lo + pidx.shape[0]])
+            o = unbind_halo(dd, v, m, inside & keep, p, fz, gas_energy(pop, h, member_idx))
+            o["bound_idx"] = pidx[o["order"]]
+            res[h] = o
+        for h in level:                      # ascending: the highest index of a level wins
+            for q in res[h]["bound_idx"].tolist():
+                owner[q] = h
+    return res
+
+
 def _worker(args):
     import time
     pop, params, n_bins, r_min_frac = args

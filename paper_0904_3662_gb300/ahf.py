@@ -44,7 +44,7 @@ EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_un
            "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch",
            "ahf_serve_create", "ahf_serve_submit", "ahf_serve_poll", "ahf_serve_stats", "ahf_serve_counters",
            "ahf_serve_reset_stats", "ahf_serve_destroy", "ahf_get_trace", "ahf_halo_properties",
-           "ahf_match_catalogs")
+           "ahf_match_catalogs", "ahf_unbind_hierarchy")
 PROP_FIELDS = 12
 SERVE_MAX_COUNT = 131072
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
     lib.ahf_unbind_batch_host.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     lib.ahf_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.ahf_unbind_batch_static.argtypes = sig[1:]
+    lib.ahf_unbind_hierarchy.argtypes = sig[:4] + [vp] + sig[4:]
     lib.ahf_unbind_profile_batch.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     if hasattr(lib, "ahf_profile_batch"):
         lib.ahf_profile_batch.argtypes = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params),
@@ -308,6 +309,28 @@ class Context:
                   None if out["phi"] is None else out["phi"].data_ptr(),
                   None if out["removed_iter"] is None else out["removed_iter"].data_ptr(),
                   _stream_ptr(stream)))
+        return out
+
+    def unbind_hierarchy(self, parts: Particles, halos, parent, params: Params, member_idx=None, out=None,
+                         with_phi=True, with_removed=True, stream=None):
+        """ahf_unbind_hierarchy: hosts after their subhaloes, each host without
+        the particles its descendants bound.  parent: host index per halo
+        (-1 for none)."""
+        halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+        parent = np.ascontiguousarray(parent, dtype=np.int64)
+        if parent.shape != (len(halos),):
+            raise ValueError("parent needs one entry per halo")
+        n_slots = n_slots_of(halos, parts.n, member_idx)
+        if out is None:
+            out = self.alloc_outputs(len(halos), n_slots, with_phi, with_removed, params.precision)
+        pc, prc = parts.c(), params.c()
+        _check(self.lib.ahf_unbind_hierarchy(
+            self._p, ctypes.byref(pc), halos.ctypes.data, len(halos), parent.ctypes.data,
+            None if member_idx is None else member_idx.data_ptr(), ctypes.byref(prc),
+            out["res"].data_ptr(), out["bound_idx"].data_ptr(),
+            None if out["phi"] is None else out["phi"].data_ptr(),
+            None if out["removed_iter"] is None else out["removed_iter"].data_ptr(),
+            _stream_ptr(stream)))
         return out
 
     def unbind_profile_batch(self, parts: Particles, halos, params: Params, n_bins=32, r_min_frac=0.01,

@@ -141,6 +141,8 @@ struct ahf_ctx {
   bool timing = false;
   bool host_direct = false;          // host entry: use mapped page-locked buffers in place
   bool graphs = false;               // on-chip launch sequence as a replayed CUDA graph
+  void* hier = nullptr;              // hierarchy scratch (owners, compacted member lists)
+  size_t hier_bytes = 0;
   void* aux = nullptr;               // second-pass member lists (AHF_VAR_RETRUNCATE)
   size_t aux_bytes = 0;
   bool trace = false;                // per-halo timestamps from the on-chip kernels
@@ -591,6 +593,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
       if (c->trace_dev) cudaFree(c->trace_dev);
   if (c->aux) cudaFree(c->aux);
+  if (c->hier) cudaFree(c->hier);
       c->trace_dev = nullptr;
       c->trace_cap = 0;
       if (cudaMalloc(&c->trace_dev, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos) != cudaSuccess) {
@@ -1039,6 +1042,25 @@ int match_impl(ahf_ctx* c, int64_t n_ids, const int64_t* ids_a, const int64_t* o
   return end_call(c, s);
 }
 
+// Depth of every halo in the forest parent describes; -1 on a bad index or a
+// cycle.
+int forest_depths(const int64_t* parent, int64_t n, std::vector<int>& depth) {
+  depth.assign((size_t)n, -1);
+  std::vector<int64_t> chain;
+  for (int64_t h = 0; h < n; ++h) {
+    chain.clear();
+    int64_t k = h;
+    while (k >= 0 && depth[(size_t)k] < 0) {
+      if (parent[k] < -1 || parent[k] >= n || (int64_t)chain.size() > n) return -1;
+      chain.push_back(k);
+      k = parent[k];
+    }
+    int base = k < 0 ? -1 : depth[(size_t)k];
+    for (size_t i = chain.size(); i-- > 0;) depth[(size_t)chain[i]] = ++base;
+  }
+  return 0;
+}
+
 // The unbinding, with AHF_VAR_RETRUNCATE as a second pass over each halo's
 // first-pass bound particles within its r_vir (the first pass's bound lists
 // become the second pass's member lists).
@@ -1063,6 +1085,7 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if (need > c->aux_bytes) {
     if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
     if (c->aux) cudaFree(c->aux);
+  if (c->hier) cudaFree(c->hier);
     c->aux = nullptr;
     c->aux_bytes = 0;
     if (cudaMalloc(&c->aux, need) != cudaSuccess) {
@@ -1086,6 +1109,109 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   ahf_particles p2 = *p;
   return unbind_pass(c, &p2, h2.data(), n_halos, members, &p1, out, bound_idx, phi, nullptr, s, n_bins,
                      r_min_frac, prof);
+}
+
+int hier_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const int64_t* parent,
+              const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
+              int32_t* removed_iter, cudaStream_t s) {
+  int rc = validate(p, halos, n_halos, prm, out, bound_idx);
+  if (rc) return rc;
+  if (n_halos > 0 && !parent) return fail(AHF_ERR_INVALID, "parent must not be NULL");
+  if (prm->variant & AHF_VAR_RETRUNCATE) return fail(AHF_ERR_INVALID, "no AHF_VAR_RETRUNCATE in a hierarchy");
+  std::vector<int> depth;
+  if (forest_depths(parent, n_halos, depth)) return fail(AHF_ERR_INVALID, "parent indices must form a forest");
+  int max_depth = 0;
+  for (int d : depth) max_depth = std::max(max_depth, d);
+  if (n_halos == 0 || max_depth == 0)
+    return unbind_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, s);
+  int64_t n_slots = p->n;
+  if (member_idx) {
+    n_slots = 0;
+    for (int64_t h = 0; h < n_halos; ++h) n_slots = std::max<int64_t>(n_slots, halos[h].offset + halos[h].count);
+  }
+  if ((rc = validate_slots(halos, n_halos, n_slots, member_idx != nullptr))) return rc;
+  // scratch outside the workspace (the levels' unbinding calls lay that out anew)
+  Bump sz{nullptr, 0, 0};
+  auto layout = [&](Bump& B, HierLaunch* L, int** lvl, int** anc) {
+    long long* owner = B.take<long long>((size_t)std::max<int64_t>(p->n, 1));
+    long long* mem = B.take<long long>((size_t)std::max<int64_t>(n_slots, 1));
+    long long* cmap = B.take<long long>((size_t)std::max<int64_t>(n_slots, 1));
+    int* rem = B.take<int>((size_t)std::max<int64_t>(n_slots, 1));
+    ahf_result* rl = B.take<ahf_result>((size_t)n_halos);
+    ahf_halo* hd = B.take<ahf_halo>((size_t)n_halos);
+    int* lv = B.take<int>((size_t)n_halos);
+    int* an = B.take<int>((size_t)n_halos);
+    long long* kept = B.take<long long>((size_t)n_halos);
+    if (L) {
+      L->owner = owner; L->members = mem; L->cand_map = cmap; L->rem_level = rem; L->res_level = rl;
+      L->halos = hd; L->level = lv; L->anc = an; L->kept = kept;
+      *lvl = lv; *anc = an;
+    }
+  };
+  layout(sz, nullptr, nullptr, nullptr);
+  if (sz.used + 4096 > c->hier_bytes) {
+    if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
+    if (c->hier) cudaFree(c->hier);
+    c->hier = nullptr;
+    c->hier_bytes = 0;
+    if (cudaMalloc(&c->hier, sz.used + 4096) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AHF_ERR_NOMEM, "hierarchy scratch of %zu bytes", sz.used + 4096);
+    }
+    c->hier_bytes = sz.used + 4096;
+  }
+  Bump B{(char*)c->hier, 0, c->hier_bytes};
+  HierLaunch L{};
+  int* d_level = nullptr;
+  int* d_anc = nullptr;
+  layout(B, &L, &d_level, &d_anc);
+  L.member_idx = (const long long*)member_idx;
+  L.n_particles = p->n;
+  L.res = out;
+  L.removed_iter = removed_iter;
+  L.bound_idx = (const long long*)bound_idx;
+  AHF_CUDA(cudaSetDevice(c->device));
+  if (c->last_valid) AHF_CUDA(cudaStreamWaitEvent(s, c->last, 0));
+  if (p->n) AHF_CUDA(cudaMemsetAsync(L.owner, 0xff, sizeof(long long) * (size_t)p->n, s));
+  AHF_CUDA(cudaMemcpyAsync((void*)L.halos, halos, sizeof(ahf_halo) * (size_t)n_halos, cudaMemcpyHostToDevice, s));
+  std::vector<int> level, anc((size_t)n_halos);
+  std::vector<long long> kept;
+  std::vector<ahf_halo> lh;
+  int64_t launches = 0, syncs = 0;
+  for (int d = max_depth; d >= 0; --d) {
+    level.clear();
+    for (int64_t h = 0; h < n_halos; ++h)
+      if (depth[(size_t)h] == d) level.push_back((int)h);
+    if (level.empty()) continue;
+    for (int64_t t = 0; t < n_halos; ++t) {
+      int64_t a = t;
+      while (a >= 0 && depth[(size_t)a] > d) a = parent[a];
+      anc[(size_t)t] = depth[(size_t)t] > d ? (int)a : -1;
+    }
+    const int nl = (int)level.size();
+    AHF_CUDA(cudaMemcpyAsync(d_level, level.data(), sizeof(int) * (size_t)nl, cudaMemcpyHostToDevice, s));
+    AHF_CUDA(cudaMemcpyAsync(d_anc, anc.data(), sizeof(int) * (size_t)n_halos, cudaMemcpyHostToDevice, s));
+    L.rank = max_depth - d;
+    AHF_CUDA(launch_hier_compact(L, nl, s));
+    kept.assign((size_t)nl, 0);
+    AHF_CUDA(cudaMemcpyAsync(kept.data(), L.kept, sizeof(long long) * (size_t)nl, cudaMemcpyDeviceToHost, s));
+    AHF_CUDA(cudaStreamSynchronize(s));
+    ++syncs;
+    lh.resize((size_t)nl);
+    for (int i = 0; i < nl; ++i) {
+      lh[(size_t)i] = halos[level[(size_t)i]];
+      lh[(size_t)i].count = kept[(size_t)i];
+    }
+    if ((rc = unbind_impl(c, p, lh.data(), nl, (const int64_t*)L.members, prm, (ahf_result*)L.res_level, bound_idx, phi,
+                          removed_iter ? (int32_t*)L.rem_level : nullptr, s)))
+      return rc;
+    launches += c->stats.launches;
+    AHF_CUDA(launch_hier_scatter(L, nl, s));
+    launches += 2;
+  }
+  c->stats.launches = launches;
+  c->stats.host_syncs += syncs;
+  return end_call(c, s);
 }
 
 // The device address of a page-locked, mapped host buffer (cudaHostAlloc,
@@ -1258,6 +1384,7 @@ int ahf_destroy(ahf_ctx* c) {
   if (c->capture) cudaStreamDestroy(c->capture);
   if (c->trace_dev) cudaFree(c->trace_dev);
   if (c->aux) cudaFree(c->aux);
+  if (c->hier) cudaFree(c->hier);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->err_dev) cudaFree(c->err_dev);
@@ -1365,6 +1492,15 @@ int ahf_unbind_batch_host(ahf_ctx* c, const ahf_particles* p, const ahf_halo* ha
   std::lock_guard<std::mutex> g(c->mu);
   return host_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, n_bins, r_min_frac,
                    prof, (cudaStream_t)stream);
+}
+
+int ahf_unbind_hierarchy(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
+                         const int64_t* parent, const int64_t* member_idx, const ahf_params* prm, ahf_result* out,
+                         int64_t* bound_idx, void* phi, int32_t* removed_iter, void* stream) {
+  if (!c) return fail(AHF_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  return hier_impl(c, p, halos, n_halos, parent, member_idx, prm, out, bound_idx, phi, removed_iter,
+                   (cudaStream_t)stream);
 }
 
 int ahf_halo_properties(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,

@@ -230,6 +230,27 @@ struct PropsLaunch {
 };
 cudaError_t launch_properties(const PropsLaunch &L, cudaStream_t s);
 
+// Hosts and subhaloes in dependency order: the kernels around each level.
+struct HierLaunch {
+  const ahf_halo *halos;           // device copy of the caller's descriptors
+  const int *level;                // caller indices of this level's haloes
+  const long long *member_idx;     // caller's member list or NULL
+  long long n_particles;
+  long long *owner;                // [n_particles]: level rank << 32 | halo, -1 none
+  const int *anc;                  // [n_halos]: ancestor on this level, -1
+  long long *members;              // [n_slots] compacted member lists
+  long long *cand_map;             // [n_slots] compacted position -> candidate slot
+  long long *kept;                 // [n_level] kept candidates
+  const ahf_result *res_level;     // [n_level]
+  ahf_result *res;                 // caller's records
+  const int *rem_level;            // [n_slots] removal iterations by compacted slot
+  int *removed_iter;               // caller's, or NULL
+  const long long *bound_idx;      // caller's
+  int rank;                        // 0 for the deepest level, growing outwards
+};
+cudaError_t launch_hier_compact(const HierLaunch &L, int n_level, cudaStream_t s);
+cudaError_t launch_hier_scatter(const HierLaunch &L, int n_level, cudaStream_t s);
+
 // Cross-identification of two catalogues by xi = N_shared^2 / (N_1 N_2).
 constexpr int MATCH_TABLE = 2048;        // distinct second-catalogue haloes one halo may meet
 constexpr int ERR_ID_RANGE = 8;          // a particle id outside [0, n_ids)

@@ -38,13 +38,17 @@ def oracle_params(p):
 
 
 def compare(pop, params, res, bound_idx, phi, removed_iter, halos=None, member_idx=None,
-            check_phi=True, phi_rtol=PHI_RTOL, vir_rtol=VIR_RTOL, exact_order=False):
+            check_phi=True, phi_rtol=PHI_RTOL, vir_rtol=VIR_RTOL, exact_order=False, parent=None):
     """res: numpy RESULT_DTYPE array; bound_idx/phi/removed_iter: host numpy
-    arrays over the candidate slots.  Returns summary statistics; raises
+    arrays over the candidate slots; parent: compare with the hierarchical
+    unbinding of that forest.  Returns summary statistics; raises
     AssertionError on a mismatch."""
     hs = range(pop.n_halos) if halos is None else halos
     op = oracle_params(params)
-    ref = O.unbind_population(pop, op, halos=hs, member_idx=member_idx, forced=removed_iter)
+    if parent is None:
+        ref = O.unbind_population(pop, op, halos=hs, member_idx=member_idx, forced=removed_iter)
+    else:
+        ref = O.unbind_hierarchy(pop, op, parent, member_idx=member_idx, forced=removed_iter)
     worst_phi = 0.0
     worst_vir = 0.0
     n_band = 0

@@ -139,3 +139,94 @@ def test_gas_thermal_energy_in_the_escape_test():
     mm = np.full(500, 1e8)
     hotcloud = O.unbind_halo(dd, np.zeros_like(dd), mm, np.ones(500, bool), prm, u_th=np.full(500, 1e7))
     assert hotcloud["status"] & O.EMPTY and hotcloud["n_iter"] == 1
+
+
+def _host_with_subhaloes(seed=5):
+    """A host NFW halo with three subhaloes (one holding a sub-subhalo), as a
+    population whose haloes share particles through member lists: slots are
+    distinct, particles are not.  Returns (pop, member_idx, parent)."""
+    rng = np.random.default_rng(seed)
+    parts_p, parts_v = [], []
+    p, v = synth.sample_nfw(rng, 20000, 10.0, 200.0)
+    parts_p.append(p)
+    parts_v.append(v)
+    subs = [((80.0, 0.0, 0.0), (150.0, 0.0, 0.0), 800), ((0.0, 110.0, 0.0), (0.0, -120.0, 40.0), 600),
+            ((-70.0, -70.0, 0.0), (60.0, 60.0, 0.0), 500)]
+    centres = [(0.0, 0.0, 0.0)]
+    for c, vb, n in subs:
+        p, v = synth.sample_nfw(rng, n, 12.0, 25.0, trunc=1.0)
+        parts_p.append(p + np.array(c))
+        parts_v.append(v + np.array(vb))
+        centres.append(c)
+    # a sub-subhalo inside the second subhalo
+    c2 = (5.0, 112.0, 3.0)
+    p, v = synth.sample_nfw(rng, 150, 12.0, 8.0, trunc=1.0)
+    parts_p.append(p + np.array(c2))
+    parts_v.append(v + np.array(subs[1][1]) + np.array([0.0, 0.0, 30.0]))
+    centres.append(c2)
+    pos = np.concatenate(parts_p)
+    vel = np.concatenate(parts_v)
+    n = pos.shape[0]
+    radii = [400.0, 40.0, 55.0, 49.0, 10.0]
+    parent = [-1, 0, 0, 0, 2]
+    members, offsets, counts = [], [], []
+    for c, R in zip(centres, radii):
+        d = pos - np.array(c)
+        sel = np.nonzero((d * d).sum(axis=1) <= (1.2 * R) ** 2)[0]
+        offsets.append(sum(counts))
+        counts.append(len(sel))
+        members.append(sel)
+    member_idx = np.concatenate(members).astype(np.int64)
+    f = np.float32
+    pop = synth.Population(name="host_with_subhaloes", coord_type=synth.COORD_F32_REL,
+                           x=pos[:, 0].astype(f), y=pos[:, 1].astype(f), z=pos[:, 2].astype(f),
+                           vx=vel[:, 0].astype(f), vy=vel[:, 1].astype(f), vz=vel[:, 2].astype(f),
+                           m=None, m0=synth.PARTICLE_MASS, box=0.0, centre=np.array(centres),
+                           radius=np.array(radii), offset=np.array(offsets, np.int64),
+                           count=np.array(counts, np.int64), r200=np.zeros(5), conc=np.zeros(5))
+    return pop, member_idx, np.array(parent)
+
+
+def test_hierarchy_depths_and_forest_checks():
+    assert O.halo_depths([-1, 0, 1, -1, 3, 0]).tolist() == [0, 1, 2, 0, 1, 1]
+    for bad in ([1, 0], [0], [-1, 5], [-2]):
+        try:
+            O.halo_depths(bad)
+        except ValueError:
+            continue
+        raise AssertionError(bad)
+
+
+def test_hierarchy_excludes_what_subhaloes_bound():
+    pop, mi, parent = _host_with_subhaloes()
+    prm = O.Params()
+    hier = O.unbind_hierarchy(pop, prm, parent, member_idx=mi)
+    flat = O.unbind_population(pop, prm, member_idx=mi)
+    # the deepest haloes are unbound exactly as on their own
+    for h in (1, 3, 4):
+        np.testing.assert_array_equal(hier[h]["bound_idx"], flat[h]["bound_idx"])
+    # a subhalo with a sub-subhalo loses that one's bound particles
+    sub_sub = set(hier[4]["bound_idx"].tolist())
+    assert sub_sub and not sub_sub & set(hier[2]["bound_idx"].tolist())
+    # the host keeps none of its descendants' bound particles, but can bind
+    # what a subhalo removed
+    taken = set()
+    for h in (1, 2, 3, 4):
+        taken |= set(hier[h]["bound_idx"].tolist())
+    host = set(hier[0]["bound_idx"].tolist())
+    assert not host & taken
+    removed_by_subs = set()
+    for h in (1, 2, 3):
+        lo, n = int(pop.offset[h]), int(pop.count[h])
+        ri = hier[h]["removed_iter"]
+        removed_by_subs |= set(mi[lo:lo + n][ri > 0].tolist())
+    assert host & removed_by_subs
+    # excluded candidates count as outside the host's sphere
+    lo, n = int(pop.offset[0]), int(pop.count[0])
+    excluded = np.isin(mi[lo:lo + n], sorted(taken))
+    assert np.all(hier[0]["removed_iter"][excluded] == -1)
+    assert hier[0]["n_member"] == flat[0]["n_member"] - int(excluded.sum())
+    # without parents the hierarchy is the flat unbinding
+    none = O.unbind_hierarchy(pop, prm, np.full(5, -1), member_idx=mi)
+    for h in range(5):
+        np.testing.assert_array_equal(none[h]["bound_idx"], flat[h]["bound_idx"])
