@@ -592,8 +592,6 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     if (c->trace_cap < n_halos) {
       if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
       if (c->trace_dev) cudaFree(c->trace_dev);
-  if (c->aux) cudaFree(c->aux);
-  if (c->hier) cudaFree(c->hier);
       c->trace_dev = nullptr;
       c->trace_cap = 0;
       if (cudaMalloc(&c->trace_dev, sizeof(long long) * AHF_TRACE_FIELDS * (size_t)n_halos) != cudaSuccess) {
@@ -1085,7 +1083,6 @@ int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   if (need > c->aux_bytes) {
     if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
     if (c->aux) cudaFree(c->aux);
-  if (c->hier) cudaFree(c->hier);
     c->aux = nullptr;
     c->aux_bytes = 0;
     if (cudaMalloc(&c->aux, need) != cudaSuccess) {
