@@ -269,6 +269,7 @@ struct Plan {
   std::vector<HaloDev> hd;     // reordered: class 0, 1, 2 (on-chip), then grid class
   int n_class[NV + 1] = {};     // 0..NV-1 shared-memory variants, NV multi-CTA
   long long grid_flat = 0;
+  long long onchip_flat = 0;     // candidates of the on-chip classes (their records)
   FrameDev frame;
 };
 
@@ -357,15 +358,17 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   std::vector<int> order((size_t)n_halos);
   for (int64_t k = 0; k < n_halos; ++k) order[(size_t)k] = (int)(key[(size_t)k] & ((1ull << 27) - 1));
   P.hd.resize((size_t)n_halos);
-  long long gbase = 0;
+  long long gbase = 0, rbase = 0;
   for (int64_t k = 0; k < n_halos; ++k) {
     const int h = order[k];
     const ahf_halo& H = halos[h];
     HaloDev& d = P.hd[k];
     fill_halo_dev(H, p->coord_type, prm->box, h, d);
     if (cls[h] == NV) { d.gbase = gbase; gbase += H.count; }
+    else { d.gbase = rbase; rbase += H.count; }
   }
   P.grid_flat = gbase;
+  P.onchip_flat = rbase;
   return AHF_OK;
 }
 
@@ -503,11 +506,13 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
 
   // workspace layout (must match the Bump sequence below)
   double* dfac = nullptr;
+  float4* drec = nullptr;
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
     int* queues = B.take<int>(16);
     double* fac = B.take<double>(prof ? 3 * (size_t)n_bins : 0);
-    if (G) dfac = fac;
+    float4* rec = B.take<float4>(2 * (size_t)P.onchip_flat);
+    if (G) { dfac = fac; drec = P.onchip_flat ? rec : nullptr; }
     if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (unsigned long long*)(queues + 10); }
     if (n_grid) {
       const size_t es = fp64 ? 8 : 4;
@@ -634,6 +639,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     L.rows.n_bins = n_bins;
     L.trace = c->trace ? c->trace_dev : nullptr;
     L.variant = v;
+    L.rec = drec;
     for (int k = 0; k < n; ++k) x.cands += P.hd[(size_t)first_of[v] + k].count;
     x.grid = (int)std::min<long long>(variant_grid_for(v, n), c->variant_grid[v]);
     vl.push_back(x);

@@ -238,6 +238,55 @@ __device__ __forceinline__ void offset_of(const ParticlesDev& p, long long i, co
   }
 }
 
+// Ask the copy engine to bring bytes [begin, end) of an array into L2
+// (cp.async.bulk.prefetch, 16-byte granules): the range is rounded inwards,
+// so nothing outside the array is named.  A hint only; it returns at once.
+__device__ __forceinline__ void prefetch_l2(const void* base, unsigned long long begin, unsigned long long end) {
+  unsigned long long a = ((unsigned long long)base + begin + 15ull) & ~15ull;
+  const unsigned long long e = ((unsigned long long)base + end) & ~15ull;
+  while (a < e) {
+    const unsigned long long n = e - a < (1ull << 20) ? e - a : (1ull << 20);
+    unsigned long long g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(a));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"((unsigned)n) : "memory");
+    a += n;
+  }
+}
+
+// Thread t < 8 of a group prefetches one input array over candidate slots
+// [lo, hi) of a halo: the member list when there is one (the particles are
+// then scattered), else the coordinate, velocity and mass arrays.
+template <int CT>
+__device__ __forceinline__ void prefetch_candidates(const ParticlesDev& p, const long long* member_idx, long long lo,
+                                                    long long hi, int t) {
+  if (t >= 8 || hi <= lo) return;
+  if (member_idx) {
+    if (t == 0) prefetch_l2(member_idx, 8ull * lo, 8ull * hi);
+    return;
+  }
+  const void* arr[8] = {p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m, nullptr};
+  const unsigned long long es = CT == AHF_COORD_F64 ? 8ull : 4ull;
+  if (arr[t]) prefetch_l2(arr[t], es * lo, es * hi);
+}
+
+// Candidate records (OnchipLaunch::rec): written once by the gather, read
+// back in radial order by the fill and the removals.  Plain (coherent)
+// accesses: in a cluster another CTA may have written the record, which the
+// cluster barrier between gather and fill (release / acquire) makes visible.
+__device__ __forceinline__ void put_record(float4* r, const float d[3], float m, const float v[3]) {
+  r[0] = make_float4(d[0], d[1], d[2], m);
+  r[1] = make_float4(v[0], v[1], v[2], 0.0f);
+}
+__device__ __forceinline__ void get_record(const float4* r, float d[3], float& m, float v[3]) {
+  const float4 a = r[0], b = r[1];
+  d[0] = a.x; d[1] = a.y; d[2] = a.z; m = a.w;
+  v[0] = b.x; v[1] = b.y; v[2] = b.z;
+}
+__device__ __forceinline__ void get_velocity_record(const float4* r, float v[3]) {
+  const float4 b = r[1];
+  v[0] = b.x; v[1] = b.y; v[2] = b.z;
+}
+
 // One candidate's stored fields, loaded together so that a loop can issue
 // the loads of several candidates before using any of them (the particle
 // store is read-only for the whole call).

@@ -28,7 +28,8 @@ struct HaloDev {
   float R2lo, R2hi;    // float bounds of R^2 that settle membership without FP64
   long long offset;    // first candidate slot
   long long count;     // candidate slots
-  long long gbase;     // first position in the multi-CTA class's flat arrays
+  long long gbase;     // first position in the class's flat arrays (the multi-CTA
+                       // class's work arrays, the on-chip classes' candidate records)
   long long boxfix;    // periodic box in this halo's 2^-frac units (0 = none)
   int frac;            // fractional bits of this halo's fixed-point offsets
   int index;           // caller's halo index
@@ -125,6 +126,12 @@ struct OnchipLaunch {
   ProfileRows rows;      // rows.prof == NULL: no profile from this launch
   long long *trace;      // [halo index][AHF_TRACE_FIELDS] or NULL
   int variant;           // phase index of this class (for the trace)
+  // candidate records, two per candidate from 2 * halos[k].gbase on:
+  // (d_x, d_y, d_z, m) and (v_x, v_y, v_z, 0) as the gather computed them,
+  // read back in radial order by the fill and the removals (two 16-byte
+  // loads in place of seven scattered 4-byte ones).  NULL: both read the
+  // particle store again.
+  float4 *rec;
 };
 
 // Warp class: one warp per halo of at most warp_capacity() candidates.

@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     }
     const int lo = rank * chunk;
     const int nloc = max(0, min(n_cand - lo, chunk));
+    prefetch_candidates<CT>(L.p, L.out.member_idx, H.offset + lo, H.offset + lo + nloc, tid);
     if (tid == 0) {
       S.or_bits = 0u; S.and_bits = 0xffffffffu;
       S.max_m = 0u; S.max_mr = 0u; S.max_mv = 0u;
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
             const float m = cand_mass<CT>(L.p, c);
             float v[3];
             cand_velocity<CT>(c, v);
+            if (L.rec) put_record(L.rec + 2 * (H.gbase + j), df, m, v);
             mxm = max(mxm, __float_as_uint(fabsf(m)));
             mxr = max(mxr, __float_as_uint(fabsf(m * rinv_of(r, P.r_soft_f))));
 #pragma unroll
@@ -416,14 +418,17 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       for (int p = tid; p < nmem_loc; p += NT) {
         const int q = sw(p, mask);
         const int j = (int)jj[q];
-        const long long slot = H.offset + j;
-        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-        long long f[3];
-        float dfl[3];
-        offset_of<CT>(L.p, pi, H, dfl, f);
-        float v[3];
-        load_velocity<CT>(L.p, pi, v);
-        const float m = load_mass<CT>(L.p, pi);
+        float dfl[3], v[3], m;
+        if (L.rec) {
+          get_record(L.rec + 2 * (H.gbase + j), dfl, m, v);
+        } else {
+          const long long slot = H.offset + j;
+          const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+          long long f[3];
+          offset_of<CT>(L.p, pi, H, dfl, f);
+          load_velocity<CT>(L.p, pi, v);
+          m = load_mass<CT>(L.p, pi);
+        }
         mm[q] = m;
         wx[q] = fmaf(P.Hf, dfl[0], v[0]);
         wy[q] = fmaf(P.Hf, dfl[1], v[1]);
@@ -530,9 +535,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         const float m = -mm[q];
         const int j = (int)jj[q];
         const long long slot = H.offset + j;
-        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
         float v[3];
-        load_velocity<CT>(L.p, pi, v);
+        if (L.rec) get_velocity_record(L.rec + 2 * (H.gbase + j), v);
+        else load_velocity<CT>(L.p, L.out.member_idx ? L.out.member_idx[slot] : slot, v);
         rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
         rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
         rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);

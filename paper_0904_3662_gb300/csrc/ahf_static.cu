@@ -170,6 +170,7 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.n_bins = 0;
   L.trace = nullptr;
   L.variant = 0;
+  L.rec = nullptr;                  // no scratch for records: the fill re-reads the particle store
   // variants in the order the descriptors were staged; each class is its own queue
   int base = 0;
   for (int v = 0; v < 3; ++v) {

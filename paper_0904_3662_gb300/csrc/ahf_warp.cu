@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       if (lane == 0) atomicOr(L.out.err, ERR_CAPACITY);
       continue;
     }
+    prefetch_candidates<CT>(L.p, L.out.member_idx, H.offset, H.offset + n_cand, lane);
 
     // ---- gather ----
     uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u;
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
           const float m = load_mass<CT>(L.p, pi);
           float v[3];
           load_velocity<CT>(L.p, pi, v);
+          if (L.rec) put_record(L.rec + 2 * (H.gbase + i), df, m, v);
           mxm = max(mxm, __float_as_uint(fabsf(m)));
           mxr = max(mxr, __float_as_uint(fabsf(m * rinv_of(r, P.r_soft_f))));
 #pragma unroll
@@ -202,14 +204,17 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     for (int p = lane; p < n_mem; p += 32) {
       const int q = sw(p, mask);
       const int j = (int)jj[q];
-      const long long slot = H.offset + j;
-      const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-      long long f[3];
-      float dfl[3];
-      offset_of<CT>(L.p, pi, H, dfl, f);
-      float v[3];
-      load_velocity<CT>(L.p, pi, v);
-      const float m = load_mass<CT>(L.p, pi);
+      float dfl[3], v[3], m;
+      if (L.rec) {
+        get_record(L.rec + 2 * (H.gbase + j), dfl, m, v);
+      } else {
+        const long long slot = H.offset + j;
+        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+        long long f[3];
+        offset_of<CT>(L.p, pi, H, dfl, f);
+        load_velocity<CT>(L.p, pi, v);
+        m = load_mass<CT>(L.p, pi);
+      }
       mm[q] = m;
       wx[q] = fmaf(P.Hf, dfl[0], v[0]);
       wy[q] = fmaf(P.Hf, dfl[1], v[1]);
@@ -274,9 +279,9 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
               mm[q] = -m;
               ++nrem;
               const long long slot = H.offset + (long long)jj[q];
-              const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
               float v[3];
-              load_velocity<CT>(L.p, pi, v);
+              if (L.rec) get_velocity_record(L.rec + 2 * (H.gbase + (long long)jj[q]), v);
+              else load_velocity<CT>(L.p, L.out.member_idx ? L.out.member_idx[slot] : slot, v);
               rm += mfix;
               rq += rfix;
               rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
