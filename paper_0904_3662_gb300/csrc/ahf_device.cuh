@@ -269,6 +269,152 @@ __device__ __forceinline__ void prefetch_candidates(const ParticlesDev& p, const
   if (arr[t]) prefetch_l2(arr[t], es * lo, es * hi);
 }
 
+// ---- radial sort of one CTA's (or one warp's) candidates ----------------------
+
+// Shared-memory position of element p when each thread holds mask + 1
+// consecutive elements: conflict-free for per-thread runs and warp stripes.
+__device__ __forceinline__ int run_swizzle(int p, int mask) { return p ^ ((p >> 5) & mask); }
+
+// 32-bit words of shared memory count_sort needs for NT threads (counters,
+// then segment bases).
+__host__ __device__ constexpr int count_sort_words(int nt) { return 8 * nt + 2 * nt; }
+
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NT == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Stable LSD radix sort, 5-bit digits, of n (key, value) pairs held by NT
+// threads (a CTA, or one warp for NT = 32) in runs: thread t holds positions
+// [t ipt, t ipt + ipt) at run_swizzle(p, mask), ipt = mask + 1 <= IPT.  Only
+// the bits of `diff` (keys agree elsewhere) are sorted.  Keys equal to
+// KEY_NONMEMBER become `sub` on the way (a key above every member's, so that
+// the non-members do not widen the digit range).
+//
+// Ranking is by counting, not by matching lanes: every thread counts the
+// digits of its run in its own byte counters (word row*NT + t, row = digit &
+// 7, byte = digit >> 3: conflict-free), one exclusive scan over the counters
+// in (row, thread) order, four bytes at once, gives every (digit, thread)
+// its first position.  The order is digit-major because a byte holds the
+// digit's high part.  Ties keep their run order: the sort is stable.
+// Returns 0 if the result is in (kA, vA), 1 if in (kB, vB).
+template <int NT, int IPT>
+__device__ int count_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, uint32_t* aux, uint32_t* wtot,
+                          int n, int mask, uint32_t diff, uint32_t sub, int t) {
+  static_assert(IPT <= 16 && IPT % 4 == 0, "byte counters hold at most 16 per thread");
+  if (diff == 0u) return 0;
+  const int lo = __ffs(diff) - 1, hi = 31 - __clz(diff);
+  const int ipt = mask + 1;
+  const int lane = t & 31;
+  uint32_t* cnt = aux;                                   // [8][NT] byte counters
+  uint2* seg = reinterpret_cast<uint2*>(aux + 8 * NT);   // [NT] bases of 8-word segments
+  uint32_t *kin = kA, *vin = vA, *kout = kB, *vout = vB;
+  const int base = t * ipt;
+  for (int shift = lo; shift <= hi; shift += 5) {
+    // count (each thread touches only its own counters here)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) cnt[w * NT + t] = 0u;
+    uint32_t rk[IPT / 4];                                // rank among the run's equal digits
+#pragma unroll
+    for (int i = 0; i < IPT / 4; ++i) rk[i] = 0u;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (k < ipt && base + k < n) {
+        const int q = run_swizzle(base + k, mask);
+        uint32_t key = kin[q];
+        if (shift == lo && key == KEY_NONMEMBER) {
+          key = sub;
+          kin[q] = key;
+        }
+        const uint32_t v = (key >> shift) & 31u;
+        const int wi = (int)(v & 7u) * NT + t;
+        const uint32_t sh = 8u * (v >> 3);
+        const uint32_t c = cnt[wi];
+        rk[k >> 2] |= ((c >> sh) & 0xffu) << (8 * (k & 3));
+        cnt[wi] = c + (1u << sh);
+      }
+    }
+    group_sync<NT>();
+    // rake: thread t scans counter words [8t, 8t + 8) (in (row, thread)
+    // order), leaving exclusive prefixes; bytes stay below 8 * 16
+    uint4* c4 = reinterpret_cast<uint4*>(cnt) + 2 * t;
+    const uint4 x0 = c4[0], x1 = c4[1];
+    uint32_t s = 0;
+    uint4 y0, y1;
+    y0.x = s; s += x0.x; y0.y = s; s += x0.y; y0.z = s; s += x0.z; y0.w = s; s += x0.w;
+    y1.x = s; s += x1.x; y1.y = s; s += x1.y; y1.z = s; s += x1.z; y1.w = s; s += x1.w;
+    c4[0] = y0;
+    c4[1] = y1;
+    // exclusive scan of the segment sums over the threads, in 16-bit lanes:
+    // a holds bytes 0 and 2, b bytes 1 and 3
+    const uint32_t a = (s & 0xffu) | (((s >> 16) & 0xffu) << 16);
+    const uint32_t b = ((s >> 8) & 0xffu) | (((s >> 24) & 0xffu) << 16);
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t xa = __shfl_up_sync(FULL_MASK, ia, o), xb = __shfl_up_sync(FULL_MASK, ib, o);
+      if (lane >= o) {
+        ia += xa;
+        ib += xb;
+      }
+    }
+    uint32_t ta, tb, pa = 0u, pb = 0u;
+    if constexpr (NT == 32) {
+      ta = __shfl_sync(FULL_MASK, ia, 31);
+      tb = __shfl_sync(FULL_MASK, ib, 31);
+    } else {
+      const int warp = t >> 5;
+      if (lane == 31) {
+        wtot[2 * warp] = ia;
+        wtot[2 * warp + 1] = ib;
+      }
+      __syncthreads();
+      ta = 0u;
+      tb = 0u;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) {
+        const uint32_t xa = wtot[2 * w], xb = wtot[2 * w + 1];
+        if (w < warp) {
+          pa += xa;
+          pb += xb;
+        }
+        ta += xa;
+        tb += xb;
+      }
+    }
+    // digit-major: the high part (byte) 0 first, then 1, 2, 3
+    const uint32_t t0 = ta & 0xffffu, t1 = tb & 0xffffu, t2 = ta >> 16;
+    seg[t] = make_uint2(pa + ia - a + ((t0 + t1) << 16), pb + ib - b + (t0 | ((t0 + t1 + t2) << 16)));
+    group_sync<NT>();
+    // scatter to the first position of (digit, thread) plus the run rank
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (k < ipt && base + k < n) {
+        const int q = run_swizzle(base + k, mask);
+        const uint32_t key = kin[q], val = vin[q];
+        const uint32_t v = (key >> shift) & 31u;
+        const int wi = (int)(v & 7u) * NT + t;
+        const uint32_t hi2 = v >> 3;
+        const uint2 sg = seg[wi >> 3];
+        const uint32_t half = (hi2 & 1u) ? sg.y : sg.x;
+        const uint32_t pos = ((half >> (16u * (hi2 >> 1))) & 0xffffu) + ((cnt[wi] >> (8u * hi2)) & 0xffu) +
+                             ((rk[k >> 2] >> (8 * (k & 3))) & 0xffu);
+        if (pos < (uint32_t)n) {               // always (a permutation of [0, n)); guards the store
+          const int d = run_swizzle((int)pos, mask);
+          kout[d] = key;
+          vout[d] = val;
+        }
+      }
+    }
+    group_sync<NT>();
+    uint32_t* tmp;
+    tmp = kin; kin = kout; kout = tmp;
+    tmp = vin; vin = vout; vout = tmp;
+  }
+  return kin == kA ? 0 : 1;
+}
+
 // Candidate records (OnchipLaunch::rec): written once by the gather, read
 // back in radial order by the fill and the removals.  Plain (coherent)
 // accesses: in a cluster another CTA may have written the record, which the

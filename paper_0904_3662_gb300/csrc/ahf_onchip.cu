@@ -90,6 +90,7 @@ struct Smem {
   long long scan_base[NW][3];
   long long tot[3];
   uint32_t or_bits, and_bits, max_m, max_mr, max_mv;
+  uint32_t max_key;             // largest member key (single-CTA sort)
   int n_member;
   long long acc[4];             // block accumulators (m v or removed m, m v)
   int acc_n, acc_band;
@@ -156,9 +157,12 @@ __device__ __forceinline__ void cluster_scan_totals(Smem<NT>& S, Xchg& X, int ra
 
 // Stable LSD radix sort of the halo's keys, 8-bit digits, skipping the digits
 // in which all keys agree.  Each CTA of the cluster holds `nloc` elements of a
-// chunk of `chunk` positions, in order; the result keeps that partition, the
-// last pass writing element p of a CTA at sw(p, mask).  Returns 0 if the
-// result is in (kA, vA), 1 if in (kB, vB) (the same in every CTA).
+// chunk of `chunk` positions, in order; the result keeps that partition, with
+// element p of a CTA at sw(p, mask).  Every pass scatters (key, value) pairs
+// as one 8-byte store into the owner CTA's shared memory (the two arrays of a
+// buffer, kA|vA or kB|vB, hold CAP interleaved pairs between passes); a local
+// pass splits the final pairs into the other buffer.  Returns 0 if the result
+// is in (kA, vA), 1 if in (kB, vB) (the same in every CTA).
 template <int NT, int IPT, int CS>
 __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, uint16_t* hist, Smem<NT>& S,
                                   Xchg& X, int nloc, int chunk, uint32_t diff, int mask, int rank) {
@@ -175,12 +179,13 @@ __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint
     __syncthreads();
     return 1;
   }
-  uint32_t *kin = kA, *vin = vA, *kout = kB, *vout = vB;
+  uint2* pA = reinterpret_cast<uint2*>(kA);     // kA|vA as interleaved pairs
+  uint2* pB = reinterpret_cast<uint2*>(kB);     // kB|vB
+  uint2 *pin = pA, *pout = pB;
   const int wchunk = ((nloc + NW * 32 - 1) / (NW * 32)) * 32;   // per-warp run
   const int nb = wchunk / 32;                                   // <= IPT
   for (int ip = 0; ip < np; ++ip) {
     const int shift = 8 * passes[ip];
-    const bool last = (ip == np - 1);
     for (int i = threadIdx.x; i < NW * 256; i += NT) hist[i] = 0;
     __syncthreads();
     uint32_t key[IPT], val[IPT];
@@ -190,8 +195,18 @@ __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint
       if (b < nb) {
         const int e = warp * wchunk + b * 32 + lane;
         const bool valid = e < nloc;
-        key[b] = valid ? kin[e] : 0u;
-        val[b] = valid ? vin[e] : 0u;
+        key[b] = 0u;
+        val[b] = 0u;
+        if (valid) {
+          if (ip == 0) {                        // the gather's separate arrays
+            key[b] = kA[e];
+            val[b] = vA[e];
+          } else {
+            const uint2 x = pin[e];
+            key[b] = x.x;
+            val[b] = x.y;
+          }
+        }
         const unsigned vmask = __ballot_sync(FULL_MASK, valid);
         rank_in[b] = 0;
         if (valid) {
@@ -247,20 +262,26 @@ __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint
         if (e < nloc) {
           const uint32_t dg = (key[b] >> shift) & 0xffu;
           const int g = (int)S.dtot[dg] + (int)hist[warp * 256 + dg] + (int)rank_in[b];
-          const int q = CS > 1 ? g / chunk : 0;
-          int li = g - q * chunk;
-          if (last) li = sw(li, mask);
-          Cl<CS>::at(kout, q)[li] = key[b];
-          Cl<CS>::at(vout, q)[li] = val[b];
+          const int q = g / chunk;
+          Cl<CS>::at(pout, q)[g - q * chunk] = make_uint2(key[b], val[b]);
         }
       }
     }
     Cl<CS>::sync();
-    uint32_t* t;
-    t = kin; kin = kout; kout = t;
-    t = vin; vin = vout; vout = t;
+    uint2* t = pin;
+    pin = pout;
+    pout = t;
   }
-  return (kin == kA) ? 0 : 1;
+  // split this CTA's sorted pairs into the other buffer, swizzled
+  uint32_t* ko = reinterpret_cast<uint32_t*>(pout);
+  uint32_t* vo = ko + IPT * NT;
+  for (int p = threadIdx.x; p < nloc; p += NT) {
+    const uint2 x = pin[p];
+    ko[sw(p, mask)] = x.x;
+    vo[sw(p, mask)] = x.y;
+  }
+  __syncthreads();
+  return pout == pA ? 0 : 1;
 }
 
 template <int NT, int CS>
@@ -301,10 +322,14 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     }
     const int lo = rank * chunk;
     const int nloc = max(0, min(n_cand - lo, chunk));
+    int ipt = 1;
+    while (ipt * NT < chunk) ipt <<= 1;
+    const int mask = ipt - 1;
     prefetch_candidates<CT>(L.p, L.out.member_idx, H.offset + lo, H.offset + lo + nloc, tid);
     if (tid == 0) {
       S.or_bits = 0u; S.and_bits = 0xffffffffu;
       S.max_m = 0u; S.max_mr = 0u; S.max_mv = 0u;
+      S.max_key = 0u;
       S.n_member = 0;
       S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
       S.acc_n = 0; S.acc_band = 0;
@@ -313,7 +338,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
 
     // ---- gather: key = radius bits of members, candidate position as value ----
     {
-      uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u;
+      uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u, kmx = 0u;
       int nmem = 0;
       for (int i = tid; i < nloc; i += NT) {
         const int j = lo + i;
@@ -347,10 +372,17 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         }
         // members start bound (removal overwrites with its iteration)
         if (L.out.removed_iter) L.out.removed_iter[slot] = key == KEY_NONMEMBER ? -1 : 0;
-        kA[i] = key;
-        vA[i] = (uint32_t)j;
-        orb |= key;
-        andb &= key;
+        // one CTA sorts runs of ipt consecutive positions (swizzled), a
+        // cluster contiguous chunks; the single-CTA sort's key range is
+        // the members' (non-members get a key just above it)
+        const int wpos = CS == 1 ? sw(i, mask) : i;
+        kA[wpos] = key;
+        vA[wpos] = (uint32_t)j;
+        if (CS > 1 || key != KEY_NONMEMBER) {
+          orb |= key;
+          andb &= key;
+          kmx = max(kmx, key);
+        }
       }
       orb = __reduce_or_sync(FULL_MASK, orb);
       andb = __reduce_and_sync(FULL_MASK, andb);
@@ -358,7 +390,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       mxr = __reduce_max_sync(FULL_MASK, mxr);
       mxv = __reduce_max_sync(FULL_MASK, mxv);
       nmem = __reduce_add_sync(FULL_MASK, nmem);
+      if constexpr (CS == 1) kmx = __reduce_max_sync(FULL_MASK, kmx);
       if (lane == 0) {
+        if constexpr (CS == 1) atomicMax(&S.max_key, kmx);
         atomicOr(&S.or_bits, orb);
         atomicAnd(&S.and_bits, andb);
         atomicMax(&S.max_m, mxm);
@@ -389,9 +423,6 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     }
     const int n_mem = S.n_member;                        // members of the halo
     const int nmem_loc = max(0, min(n_mem - lo, nloc));  // held by this CTA after the sort
-    int ipt = 1;
-    while (ipt * NT < chunk) ipt <<= 1;
-    const int mask = ipt - 1;
     const int s_m = fix_scale(float_exponent_of_bits(S.max_m), n_mem);
     const int s_r = fix_scale(float_exponent_of_bits(S.max_mr), n_mem);
     const int s_v = fix_scale(float_exponent_of_bits(S.max_mv), n_mem);
@@ -400,8 +431,22 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
 
     if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
-    const int which = cluster_radix_sort<NT, IPT, CS>(kA, vA, kB, vB, hist, S, X, nloc, chunk,
-                                                      S.or_bits ^ S.and_bits, mask, rank);
+    int which;
+    if constexpr (CS == 1) {
+      uint32_t diff = 0u, sub = 0u;
+      if (n_mem > 0) {
+        diff = S.or_bits ^ S.and_bits;
+        if (n_mem < n_cand) {
+          sub = S.max_key + 1u;
+          diff = (S.or_bits | sub) ^ (S.and_bits & sub);
+        }
+      }
+      which = count_sort<NT, IPT>(kA, vA, kB, vB, reinterpret_cast<uint32_t*>(hist),
+                                  reinterpret_cast<uint32_t*>(&S.red[0][0]), nloc, mask, diff, sub, tid);
+    } else {
+      which = cluster_radix_sort<NT, IPT, CS>(kA, vA, kB, vB, hist, S, X, nloc, chunk, S.or_bits ^ S.and_bits,
+                                              mask, rank);
+    }
     if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 2);
     float* rr = (float*)(which ? kB : kA);         // radius, sorted, swizzled
     uint32_t* jj = which ? vB : vA;                // candidate position
@@ -812,9 +857,11 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
   }
 }
 
-template <int NT, int CAP>
+// Dynamic shared memory: six 4-byte arrays of CAP slots, then the sort's
+// counters (per-warp digit counts in a cluster, count_sort's words in one CTA).
+template <int NT, int CAP, int CS>
 constexpr size_t dyn_bytes() {
-  return (size_t)CAP * 24 + (size_t)(NT / 32) * 256 * 2;
+  return (size_t)CAP * 24 + (CS == 1 ? (size_t)count_sort_words(NT) * 4 : (size_t)(NT / 32) * 256 * 2);
 }
 
 template <int CS>
@@ -830,7 +877,7 @@ void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
 template <int NT, int CAP, int CT, int CS>
 cudaError_t launch_variant(const OnchipLaunch& L, int grid, cudaStream_t s) {
   auto k = unbind_kernel<NT, CAP, CT, CS>;
-  constexpr size_t smem = dyn_bytes<NT, CAP>();
+  constexpr size_t smem = dyn_bytes<NT, CAP, CS>();
   static std::atomic<unsigned long long> attrs_set{0};
   if (first_use_on_device(attrs_set)) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -860,7 +907,7 @@ cudaError_t launch_variant(const OnchipLaunch& L, int grid, cudaStream_t s) {
 template <int NT, int CAP, int CS>
 int max_grid_variant(int device) {
   auto k = unbind_kernel<NT, CAP, AHF_COORD_F32_REL, CS>;
-  constexpr size_t smem = dyn_bytes<NT, CAP>();
+  constexpr size_t smem = dyn_bytes<NT, CAP, CS>();
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
