@@ -156,6 +156,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def count(self):
+        return len(self.lines)
+
+    def wait_samples(self, n, timeout=3.0):
+        """Block until the sampler has produced n lines (or the timeout)."""
+        t0 = time.perf_counter()
+        while self.proc and len(self.lines) < n and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -383,6 +392,8 @@ def run_ahf(args):
         step()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        clk.wait_samples(1)                       # the sampler is up before the timed steps
+        n0 = clk.count()
         t_wall = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()                         # L2 flush, outside the timed events
@@ -391,12 +402,24 @@ def run_ahf(args):
             ends[i].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        # a timed region shorter than the sampling period gets no sample of
+        # its own: the same steps keep the GPU under the same load (untimed)
+        # until two samples fall after the start of the timed steps
+        t_hold = time.perf_counter()
+        while clk.count() < n0 + 2 and time.perf_counter() - t_hold < 3.0:
+            for _ in range(20):
+                flush.zero_()
+                step()
+            torch.cuda.synchronize()
+        clk.lines = clk.lines[n0:]
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     # the same steps again with per-phase events (one host wait per step) for
-    # the per-kernel durations the roofline uses
+    # the per-kernel durations the roofline uses: the classes one after
+    # another, each kernel timed alone as in the ncu launch list
     ctx.set_option(ahf.OPT_GRAPHS, 0)
     ctx.set_option(ahf.OPT_TIMING, 1)
+    ctx.set_option(ahf.OPT_SERIAL, 1)
     for i in range(args.steps):
         flush.zero_()
         step()
@@ -406,6 +429,7 @@ def run_ahf(args):
             if st["phase_ms"][k] >= 0:
                 phase_ms[k] += st["phase_ms"][k]
                 phase_n[k] += 1
+    ctx.set_option(ahf.OPT_SERIAL, 0)
     ms = float(np.mean(step_ms))
     ms_max = reduce_max(world, ms)
     total_units = reduce_sum(world, units)
@@ -420,6 +444,7 @@ def run_ahf(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": ahf.PHASE_NAMES[dom], "algorithmic_bytes": float(pbytes[dom]),
                 "ms_per_launch": float(avg[dom]), "peak_source": peak_kind,
+                "durations": "each size class timed alone (AHF_OPT_SERIAL), L2 flushed before the step",
                 "phases_ms": {ahf.PHASE_NAMES[k]: round(float(avg[k]), 4) for k in range(ahf.N_PHASES)
                               if phase_n[k] > 0}}
 
@@ -433,6 +458,8 @@ def run_ahf(args):
             "gpu_launches": launches, "roofline": roofline,
             "timed_wall_s": t_wall}
     clocks = clk.summary()
+    if clocks:
+        clocks["window"] = "the timed steps and the same steps right after them (200 ms sampling)"
     line["clocks"] = clocks
     if rank == 0 and args.properties:
         line["properties"] = time_properties(ctx, parts, hal, prm, pop, stream, flush)

@@ -254,6 +254,11 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        launches.  Ignored while AHF_OPT_TIMING is on.
  *   AHF_OPT_TRACE        1 = the on-chip kernels of the following calls record
  *                        per-halo timestamps (read with ahf_get_trace), 0 = off
+ *   AHF_OPT_SERIAL       1 = the on-chip size classes run one after another on
+ *                        the caller's stream, so that each phase's events time
+ *                        its kernel alone (as a profiler's launch list does);
+ *                        0 (default) = concurrently on side streams.  Results
+ *                        are the same bits either way.
  *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
  *                        arrays that are page-locked (cudaHostAlloc,
  *                        cudaHostRegister) and write page-locked outputs in
@@ -269,6 +274,7 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
 #define AHF_OPT_HOST_DIRECT 4
 #define AHF_OPT_GRAPHS     5
 #define AHF_OPT_TRACE      6
+#define AHF_OPT_SERIAL     7
 
 /* Per-call statistics of the most recent unbinding or profile call.
  * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the

@@ -146,6 +146,7 @@ struct ahf_ctx {
   void* aux = nullptr;               // second-pass member lists (AHF_VAR_RETRUNCATE)
   size_t aux_bytes = 0;
   bool trace = false;                // per-halo timestamps from the on-chip kernels
+  bool serial = false;               // on-chip classes one after another on the caller's stream
   long long* trace_dev = nullptr;    // [n][AHF_TRACE_FIELDS] of the last traced call
   int64_t trace_cap = 0;             // haloes trace_dev holds
   int64_t trace_n = -1;              // haloes of the last traced call (-1: none)
@@ -645,6 +646,15 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     vl.push_back(x);
   }
   auto enqueue_onchip = [&](cudaStream_t o, bool join) -> int {
+    if (c->serial) {                     // one class after another on the caller's stream
+      for (const VLaunch& x : vl) {
+        int prc;
+        if ((prc = phase_begin(c, x.v, o, 0, 0))) return prc;
+        AHF_CUDA(launch_variant(x.L, x.v, x.grid, o));
+        if ((prc = phase_end(c, x.v, o))) return prc;
+      }
+      return AHF_OK;
+    }
     AHF_CUDA(cudaEventRecord(c->fork, o));
     for (const VLaunch& x : vl) {
       AHF_CUDA(cudaStreamWaitEvent(c->side[x.v], c->fork, 0));
@@ -702,7 +712,8 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     if (n_grid) {
       if ((rc = run_grid(c, G, prm, s))) return rc;
     }
-    for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
+    if (!c->serial)
+      for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
   }
   if ((rc = end_call(c, s))) return rc;
   if (prof) {
@@ -1439,6 +1450,10 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "trace is 0 or 1");
       c->trace = value == 1;
       return AHF_OK;
+    case AHF_OPT_SERIAL:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "serial is 0 or 1");
+      c->serial = value == 1;
+      return AHF_OK;
     default:
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
@@ -1453,6 +1468,7 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
     case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
     case AHF_OPT_TRACE: *value = c->trace ? 1 : 0; return AHF_OK;
+    case AHF_OPT_SERIAL: *value = c->serial ? 1 : 0; return AHF_OK;
     default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }

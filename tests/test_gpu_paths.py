@@ -63,7 +63,14 @@ def test_edge_cases_small():
     # 6: cold sphere moving with the bulk (nothing removed without Hubble flow in its frame)
     p, _ = synth.sample_uniform_sphere(rng, 700, 5.0, 0.0)
     pl.append(p); vl.append(np.tile([[300.0, -200.0, 50.0]], (700, 1))); cs.append([0, 0, 0]); rs.append(10.0)
-    # 7: ragged sizes just around the class boundaries
+    # 7, 8: every member at one radius (axis points: the float radius is exact),
+    # with non-members outside the sphere; the sort's key range is then only
+    # the step between members and non-members
+    for n_axis, n_out in ((60, 10), (700, 100)):
+        ax = np.repeat(np.vstack([np.eye(3), -np.eye(3)]) * 4.0, n_axis // 6 + 1, axis=0)[:n_axis]
+        p = np.vstack([ax, rng.uniform(40, 50, (n_out, 3))])
+        pl.append(p); vl.append(rng.normal(0, 5.0, p.shape)); cs.append([0, 0, 0]); rs.append(10.0)
+    # ragged sizes just around the class boundaries
     for n in (31, 32, 33, 511, 512, 513, 1023, 1024, 1025, 4095, 4097, 8191, 8192):
         p, v = synth.sample_nfw(rng, n, 10.0, 60.0)
         pl.append(p); vl.append(v); cs.append([0, 0, 0]); rs.append(120.0)
@@ -74,6 +81,7 @@ def test_edge_cases_small():
     assert res[2]["n_member"] == 0 and res[2]["status"] & O.EMPTY
     assert res[5]["status"] & O.EMPTY
     assert (out["removed_iter"][int(pop.offset[2]):int(pop.offset[2]) + 20] == -1).all()
+    assert res[7]["n_member"] == 60 and res[8]["n_member"] == 700
 
 
 def test_edge_cases_multi_cta():
@@ -384,3 +392,28 @@ def test_trace_fields_and_results_unchanged():
         assert tr[h, 7] & 255 == v and tr[h, 7] >> 8 == res["n_iter"][h]
     with pytest.raises(ahf.AHFError):
         ctx.trace(pop.n_halos + 1)
+
+
+def test_serial_classes_same_bits():
+    """AHF_OPT_SERIAL (classes one after another, each phase timed alone)
+    changes nothing in the results."""
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=75, n_halos=60, n_lo=100, n_hi=100_000)
+    ctx = ahf.Context(0)
+    base, _, _, _ = run_gpu(pop, ctx=ctx)
+    ctx.set_option(ahf.OPT_SERIAL, 1)
+    ctx.set_option(ahf.OPT_TIMING, 1)
+    assert ctx.get_option(ahf.OPT_SERIAL) == 1
+    ser, _, _, _ = run_gpu(pop, ctx=ctx)
+    st = ctx.stats()
+    assert ser["res"].tobytes() == base["res"].tobytes()
+    np.testing.assert_array_equal(ser["removed_iter"], base["removed_iter"])
+    for h in range(pop.n_halos):          # slots past n_bound are unspecified
+        lo, nb = int(pop.offset[h]), int(base["res"][h]["n_bound"])
+        np.testing.assert_array_equal(ser["bound_idx"][lo:lo + nb], base["bound_idx"][lo:lo + nb])
+        np.testing.assert_array_equal(ser["phi"][lo:lo + nb], base["phi"][lo:lo + nb])
+    used = [k for k in range(8) if st["phase_halos"][k] > 0]
+    assert used and all(st["phase_ms"][k] > 0 for k in used)
+    with pytest.raises(ahf.AHFError):
+        ctx.set_option(ahf.OPT_SERIAL, 2)
