@@ -94,6 +94,10 @@ struct Smem {
   int n_member;
   long long acc[4];             // block accumulators (m v or removed m, m v)
   int acc_n, acc_band;
+  // one CTA's removal sums, alternating between iterations: (removed m, m v),
+  // removed count, band count
+  long long racc[2][4];
+  int racc_n[2], racc_band[2];
   // cluster-wide values
   long long c_pre[3];           // exclusive prefix over lower ranks
   long long c_tot[3];
@@ -126,6 +130,27 @@ __device__ __forceinline__ void block_exclusive_scan3(long long& a, long long& b
   a = S.scan_base[warp][0] + ia - a;
   b = S.scan_base[warp][1] + ib - b;
   c = S.scan_base[warp][2] + ic - c;
+}
+
+// The same for two values (the iterations need no count): totals in
+// S.tot[0], S.tot[1].
+template <int NT>
+__device__ __forceinline__ void block_exclusive_scan2(long long& a, long long& b, Smem<NT>& S) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long ia = warp_inclusive_scan(a, lane);
+  long long ib = warp_inclusive_scan(b, lane);
+  if (lane == 31) { S.red[warp][0] = ia; S.red[warp][1] = ib; }
+  __syncthreads();
+  if (warp == 0) {
+    long long x = lane < NW ? S.red[lane][0] : 0, y = lane < NW ? S.red[lane][1] : 0;
+    long long sx = warp_inclusive_scan(x, lane), sy = warp_inclusive_scan(y, lane);
+    if (lane < NW) { S.scan_base[lane][0] = sx - x; S.scan_base[lane][1] = sy - y; }
+    if (lane == NW - 1) { S.tot[0] = sx; S.tot[1] = sy; }
+  }
+  __syncthreads();
+  a = S.scan_base[warp][0] + ia - a;
+  b = S.scan_base[warp][1] + ib - b;
 }
 
 // Publish this CTA's three scan totals and combine the cluster's: S.c_pre
@@ -520,30 +545,65 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     long long part_iter = 0, n_band = 0;
     int n_alive = n_mem;
     bool converged = false;
+    // one CTA: every thread keeps the exact sum m v and forms v_bulk itself
+    // (the same bits in every thread), and the removal sums alternate
+    // between two buffers, so an iteration takes three barriers
+    long long mvl[3] = {S.mv[0], S.mv[1], S.mv[2]};
+    float vbl[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (CS == 1) {
+      if (tid == 0)
+        for (int bsel = 0; bsel < 2; ++bsel) {
+          S.racc[bsel][0] = S.racc[bsel][1] = S.racc[bsel][2] = S.racc[bsel][3] = 0;
+          S.racc_n[bsel] = 0;
+          S.racc_band[bsel] = 0;
+        }
+    }
     while (n_alive > 0 && n_iter < P.max_iter) {
       ++n_iter;
       part_iter += n_alive;
-      long long tm = tm_own, tr = tr_own, tc = tc_own;
-      block_exclusive_scan3<NT>(tm, tr, tc, S);
-      cluster_scan_totals<NT, CS>(S, X, rank);
-      if (tid == 0) {
+      const int bsel = n_iter & 1;
+      long long tm = tm_own, tr = tr_own;
+      long long T_tot;
+      if constexpr (CS == 1) {
+        block_exclusive_scan2<NT>(tm, tr, S);
+        T_tot = S.tot[1];
         // v_bulk = sum m v / sum m of the current set, from the exact sums
         // (with AHF_VAR_VBULK_INITIAL the first iteration's value is kept)
         if (n_iter == 1 || !P.vbulk_initial) {
-          const float mt = float_from_fix(S.c_tot[0], s_m);
-          S.vb[0] = float_from_fix(S.mv[0], s_v) / mt;
-          S.vb[1] = float_from_fix(S.mv[1], s_v) / mt;
-          S.vb[2] = float_from_fix(S.mv[2], s_v) / mt;
+          const float mt = float_from_fix(S.tot[0], s_m);
+          vbl[0] = float_from_fix(mvl[0], s_v) / mt;
+          vbl[1] = float_from_fix(mvl[1], s_v) / mt;
+          vbl[2] = float_from_fix(mvl[2], s_v) / mt;
         }
-        S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
-        S.acc_n = 0;
-        S.acc_band = 0;
+        if (tid == 0) {                  // the next iteration's buffer: its readers are past the scan
+          S.racc[bsel ^ 1][0] = S.racc[bsel ^ 1][1] = S.racc[bsel ^ 1][2] = S.racc[bsel ^ 1][3] = 0;
+          S.racc_n[bsel ^ 1] = 0;
+          S.racc_band[bsel ^ 1] = 0;
+        }
+      } else {
+        long long tc = tc_own;
+        block_exclusive_scan3<NT>(tm, tr, tc, S);
+        cluster_scan_totals<NT, CS>(S, X, rank);
+        if (tid == 0) {
+          if (n_iter == 1 || !P.vbulk_initial) {
+            const float mt = float_from_fix(S.c_tot[0], s_m);
+            S.vb[0] = float_from_fix(S.mv[0], s_v) / mt;
+            S.vb[1] = float_from_fix(S.mv[1], s_v) / mt;
+            S.vb[2] = float_from_fix(S.mv[2], s_v) / mt;
+          }
+          S.acc[0] = S.acc[1] = S.acc[2] = S.acc[3] = 0;
+          S.acc_n = 0;
+          S.acc_band = 0;
+        }
+        __syncthreads();
+        tm += S.c_pre[0];
+        tr += S.c_pre[1];
+        T_tot = S.c_tot[1];
+        vbl[0] = S.vb[0];
+        vbl[1] = S.vb[1];
+        vbl[2] = S.vb[2];
       }
-      __syncthreads();
-      tm += S.c_pre[0];
-      tr += S.c_pre[1];
-      const long long T_tot = S.c_tot[1];
-      const float vb0 = S.vb[0], vb1 = S.vb[1], vb2 = S.vb[2];
+      const float vb0 = vbl[0], vb1 = vbl[1], vb2 = vbl[2];
       long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
       uint32_t rmask = 0;                 // this thread's removals (bit k: position p0 + k)
@@ -594,20 +654,33 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       tc_own -= nrem;
       nrem = __reduce_add_sync(FULL_MASK, nrem);
       nband = __reduce_add_sync(FULL_MASK, nband);
+      long long* acc = CS == 1 ? S.racc[bsel] : S.acc;
+      int* acc_n = CS == 1 ? &S.racc_n[bsel] : &S.acc_n;
+      int* acc_band = CS == 1 ? &S.racc_band[bsel] : &S.acc_band;
       if (nrem) {
         rm = warp_sum(rm); rv0 = warp_sum(rv0); rv1 = warp_sum(rv1); rv2 = warp_sum(rv2);
         if (lane == 0) {
-          atomicAdd((unsigned long long*)&S.acc[0], (unsigned long long)rm);
-          atomicAdd((unsigned long long*)&S.acc[1], (unsigned long long)rv0);
-          atomicAdd((unsigned long long*)&S.acc[2], (unsigned long long)rv1);
-          atomicAdd((unsigned long long*)&S.acc[3], (unsigned long long)rv2);
+          atomicAdd((unsigned long long*)&acc[0], (unsigned long long)rm);
+          atomicAdd((unsigned long long*)&acc[1], (unsigned long long)rv0);
+          atomicAdd((unsigned long long*)&acc[2], (unsigned long long)rv1);
+          atomicAdd((unsigned long long*)&acc[3], (unsigned long long)rv2);
         }
       }
       if (lane == 0 && (nrem | nband)) {
-        atomicAdd(&S.acc_n, nrem);
-        atomicAdd(&S.acc_band, nband);
+        atomicAdd(acc_n, nrem);
+        atomicAdd(acc_band, nband);
       }
       __syncthreads();
+      if constexpr (CS == 1) {
+        const int removed = *acc_n;
+        n_band += *acc_band;
+        mvl[0] -= acc[1];
+        mvl[1] -= acc[2];
+        mvl[2] -= acc[3];
+        n_alive -= removed;
+        if (removed == 0) { converged = true; break; }
+        continue;
+      }
       if constexpr (CS > 1) {
         if (tid == 0) {
           X.rem[0] = S.acc[0]; X.rem[1] = S.acc[1]; X.rem[2] = S.acc[2]; X.rem[3] = S.acc[3];
@@ -641,6 +714,13 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     }
     if (n_alive == 0) status |= AHF_HALO_EMPTY;
     else if (!converged) status |= AHF_HALO_NOT_CONVERGED;
+    if constexpr (CS == 1) {
+      if (tid == 0) {                    // for the record (the emit's scan barriers order it)
+        S.mv[0] = mvl[0];
+        S.mv[1] = mvl[1];
+        S.mv[2] = mvl[2];
+      }
+    }
 
     if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 4);
     // ---- emit: bound list, phi, compacted (r, inclusive M) for the virial search ----
