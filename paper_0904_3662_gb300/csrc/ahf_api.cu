@@ -382,6 +382,7 @@ ParamsDev to_dev(const ahf_params* prm) {
   d.Gf = (float)prm->G; d.Hf = (float)prm->H; d.r_soft_f = (float)prm->r_soft; d.band_f = (float)prm->band;
   d.crit = prm->delta_rho * (4.0 * M_PI / 3.0);
   d.crit_f = (float)d.crit;
+  d.inv_crit = 1.0 / d.crit;
   d.max_iter = prm->max_iter;
   d.precision = prm->precision;
   d.vbulk_initial = (prm->variant & AHF_VAR_VBULK_INITIAL) ? 1 : 0;
@@ -507,13 +508,15 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
 
   // workspace layout (must match the Bump sequence below)
   double* dfac = nullptr;
+  float* dfacf = nullptr;
   float4* drec = nullptr;
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>((size_t)n_halos);
     int* queues = B.take<int>(16);
     double* fac = B.take<double>(prof ? 3 * (size_t)n_bins : 0);
+    float* facf = B.take<float>(prof ? 3 * (size_t)n_bins : 0);
     float4* rec = B.take<float4>(2 * (size_t)P.onchip_flat);
-    if (G) { dfac = fac; drec = P.onchip_flat ? rec : nullptr; }
+    if (G) { dfac = fac; dfacf = facf; drec = P.onchip_flat ? rec : nullptr; }
     if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (unsigned long long*)(queues + 10); }
     if (n_grid) {
       const size_t es = fp64 ? 8 : 4;
@@ -546,7 +549,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
-  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 24 * (size_t)n_bins + 256 : 0) +
+  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 36 * (size_t)n_bins + 512 : 0) +
                           (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
@@ -570,6 +573,8 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     std::vector<double> tab(3 * (size_t)n_bins);
     profile_bin_tables(n_bins, r_min_frac, tab.data());
     AHF_CUDA(stage(dfac, tab.data(), sizeof(double) * tab.size()));
+    std::vector<float> tabf(tab.begin(), tab.end());
+    AHF_CUDA(stage(dfacf, tabf.data(), sizeof(float) * tabf.size()));
   }
 
   OutputsDev O;
@@ -637,6 +642,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     L.halos = hd + first_of[v]; L.n_halos = n; L.queue = queues + v;
     L.rows.prof = (prof && v <= FUSED_MAX) ? prof : nullptr;
     L.rows.factor = dfac;
+    L.rows.factor_f = dfacf;
     L.rows.n_bins = n_bins;
     L.trace = c->trace ? c->trace_dev : nullptr;
     L.variant = v;
@@ -774,14 +780,20 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   std::vector<double> factor(3 * (size_t)n_bins);
   profile_bin_tables(n_bins, r_min_frac, factor.data());
   double* dfac = nullptr;
+  float* dfacf = nullptr;
   auto layout = [&](Bump& B, ProfileLaunch* L, int** h0) {
     HaloDev* d = B.take<HaloDev>((size_t)n_halos);
     int* ch = B.take<int>((size_t)n_chunks + 1);
     long long* cs = B.take<long long>((size_t)n_chunks + 1);
     int* hc0 = B.take<int>((size_t)n_halos + 1);
     double* fac = B.take<double>(3 * (size_t)n_bins);
+    float* facf = B.take<float>(3 * (size_t)n_bins);
     long long* acc = B.take<long long>((size_t)n_chunks * (2 + 2 * (size_t)n_bins) + 1);
-    if (L) { L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0; dfac = fac; }
+    if (L) {
+      L->halos = d; L->chunk_halo = ch; L->chunk_start = cs; L->chunk_acc = acc; *h0 = hc0;
+      dfac = fac;
+      dfacf = facf;
+    }
   };
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr, nullptr);
@@ -807,8 +819,11 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
   AHF_CUDA(stage(L.chunk_start, chunk_start.data(), sizeof(long long) * (size_t)n_chunks));
   AHF_CUDA(stage(hc0, halo_chunk0.data(), sizeof(int) * ((size_t)n_halos + 1)));
   AHF_CUDA(stage(dfac, factor.data(), sizeof(double) * factor.size()));
+  const std::vector<float> factor_f(factor.begin(), factor.end());
+  AHF_CUDA(stage(dfacf, factor_f.data(), sizeof(float) * factor_f.size()));
   if ((rc = pin_release(c, s))) return rc;
   L.edge_factor = dfac;
+  L.edge_factor_f = dfacf;
   L.n_multi = n_multi;
   L.p = to_dev(p);
   L.frame = P.frame;

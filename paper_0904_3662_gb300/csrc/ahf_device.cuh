@@ -104,10 +104,95 @@ __device__ __forceinline__ float float_from_fix(long long v, int s) {
   return scale_pow2f(fmaf(hi, 4294967296.0f, lo), -s);
 }
 
+// v 2^-s as the nearest double (ties to even), assembled from the bits on the
+// integer pipes: the FP64 pipe of this part is narrow and its latency long, and
+// the per-halo record and profile rows would otherwise wait on it.  Results
+// outside the normal range take the FP64 route (the same value).
 __device__ __forceinline__ double double_from_fix(long long v, int s) {
-  const double hi = (double)(int)(v >> 32);
-  const double lo = (double)(unsigned)(v & 0xffffffffll);
-  return scale_pow2d(fma(hi, 4294967296.0, lo), -s);
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int e = 63 - __clzll((long long)a);                   // leading bit
+  unsigned long long m;
+  if (e <= 52) {
+    m = a << (52 - e);
+  } else {
+    const int sh = e - 52;
+    m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 53)) {
+        m >>= 1;
+        ++e;
+      }
+    }
+  }
+  const int ex = e - s + 1023;
+  if (ex <= 0 || ex >= 2047) {
+    const double hi = (double)(int)(v >> 32);
+    const double lo = (double)(unsigned)(v & 0xffffffffll);
+    return scale_pow2d(fma(hi, 4294967296.0, lo), -s);
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (m & ((1ull << 52) - 1ull))));
+}
+
+// A float as a double (exact), from the bits.
+__device__ __forceinline__ double float_to_double(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;           // zero, subnormal, inf, nan
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// A double rounded to the nearest float (ties to even), from the bits.
+__device__ __forceinline__ float double_to_float(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ffull) - 1023 + 127;
+  if (e <= 0 || e >= 254) return (float)x;               // outside float's normal range
+  uint32_t m = (uint32_t)((u >> 29) & 0x7fffffull);
+  const unsigned long long rem = u & ((1ull << 29) - 1ull), half = 1ull << 28;
+  uint32_t b = ((uint32_t)e << 23) | m;
+  if (rem > half || (rem == half && (m & 1u))) ++b;       // a carry into the exponent is right
+  return __uint_as_float(b | (uint32_t)((u >> 63) << 31));
+}
+
+// ---- the record's FP64 values from float estimates ---------------------------------
+
+// a / b: q = a r with r the float reciprocal of b, corrected once by the
+// residual a - q b in FP64 (the error squares: ~1e-14).
+__device__ __forceinline__ double quotient(double a, double b) {
+  const float bf = double_to_float(b);
+  if (!(fabsf(bf) > 1e-30f && fabsf(bf) < 1e30f)) return a / b;
+  const double r = float_to_double(__frcp_rn(bf));
+  const double q = a * r;
+  return fma(fma(-q, b, a), r, q);
+}
+
+// R_vir = (M / crit)^(1/3) with crit = Delta rho_ref 4 pi / 3 (Eq. 1): x = M / crit
+// as M inv_crit, a float estimate z of x^(-1/3) and two Newton steps in FP64,
+// z <- z + z (1 - x z^3) / 3 (each squares the error: 1e-7 -> 1e-14 -> below
+// the FP64 rounding), then x z^2.
+__device__ __forceinline__ double virial_radius(double m, double inv_crit) {
+  const double x = m * inv_crit;
+  const float xf = double_to_float(x);
+  if (!(xf > 1e-30f && xf < 1e30f)) return cbrt(x);
+  double z = float_to_double(__frcp_rn(cbrtf(xf)));
+  z = fma(z * fma(-x, z * z * z, 1.0), 1.0 / 3.0, z);
+  z = fma(z * fma(-x, z * z * z, 1.0), 1.0 / 3.0, z);
+  return x * (z * z);
+}
+
+// m < crit r^3 (the mean density inside r above the threshold fails), in float
+// (mf: m rounded) except within 1e-5 of equality, where it is decided in FP64.
+__device__ __forceinline__ bool below_threshold(double m, float mf, float r, float crit_f, double crit) {
+  const float rhs = crit_f * r * r * r;
+  if (mf < rhs * (1.0f - 1e-5f)) return true;
+  if (mf > rhs * (1.0f + 1e-5f)) return false;
+  const double rd = float_to_double(r);
+  return m < crit * rd * rd * rd;
 }
 
 // ---- recentring (Sect. 2.1: the sphere around the candidate centre) -----------
@@ -568,16 +653,32 @@ __device__ __forceinline__ bool le_edge(float r, float ef, double e) {
   return (double)r <= e;
 }
 
-// Profile columns from the per-bin tables (see profile_bin_tables): the shell
-// density M_bin / V_bin with V_bin = r_out^3 (4 pi / 3)(f_{b+1}^3 - f_b^3), and
-// v_circ = sqrt(G M(<= e_{b+1}) / e_{b+1}) with e_{b+1} = r_out f_{b+1}; the
-// divisions by r_out are one reciprocal per halo.
-__device__ __forceinline__ double shell_density(double m_bin, double inv_r3, const double* tab, int n, int b) {
-  return (m_bin * inv_r3) * tab[n + b];
+// Profile columns from the per-bin tables (see profile_bin_tables; tf is
+// their float copy): the shell density M_bin / V_bin with V_bin = r_out^3
+// (4 pi / 3)(f_{b+1}^3 - f_b^3), and v_circ = sqrt(G M(<= e_{b+1}) / e_{b+1}) with
+// e_{b+1} = r_out f_{b+1}.  Both are formed in float (relative precision
+// ~1e-7; counts and masses stay exact), in FP64 only if float overflows.
+__device__ __forceinline__ double shell_density(double m_bin, double r_out, float inv_r, const double* tab,
+                                                const float* tf, int n, int b) {
+  const float d = ((double_to_float(m_bin) * (inv_r * inv_r * inv_r)) * tf[n + b]);
+  if (isfinite(d) && (d > 0.0f || m_bin == 0.0)) return float_to_double(d);
+  const double ir = 1.0 / r_out;
+  return (m_bin * (ir * ir * ir)) * tab[n + b];
 }
-__device__ __forceinline__ double circular_velocity(double G, double m_in, double inv_r, const double* tab, int n,
-                                                    int b) {
-  return sqrt(((G * m_in) * inv_r) * tab[2 * n + b]);
+__device__ __forceinline__ double circular_velocity(double G, float Gf, double m_in, double r_out, float inv_r,
+                                                    const double* tab, const float* tf, int n, int b) {
+  const float v2 = ((Gf * double_to_float(m_in)) * inv_r) * tf[2 * n + b];
+  if (isfinite(v2) && (v2 > 0.0f || m_in == 0.0)) return float_to_double(sqrtf(v2));
+  return sqrt(((G * m_in) / r_out) * tab[2 * n + b]);
+}
+
+// r <= e for a float radius r and the FP64 edge e = r_out fac, decided against
+// ef = r_out_f fac_f (float values within three roundings of e) outside an
+// 8-ulp band, in FP64 inside it.
+__device__ __forceinline__ bool le_edge_band(float r, float ef, double r_out, double fac) {
+  if (r < ef * (1.0f - 4.8e-7f)) return true;
+  if (r > ef * (1.0f + 4.8e-7f)) return false;
+  return float_to_double(r) <= r_out * fac;
 }
 
 // Log-radial profile rows of one halo from its compacted bound set held on
@@ -587,46 +688,45 @@ __device__ __forceinline__ double circular_velocity(double G, double m_in, doubl
 // output).  The calling threads take rows t0, t0 + stride, ...
 template <typename Idx>
 __device__ void profile_rows(const ProfileRows& Q, int h, const float* rc, const long long* mc, Idx idx, long long nb,
-                             double r_vir, int s_m, double G, const double* m0, int t0, int stride) {
+                             double r_vir, int s_m, double G, float Gf, const double* m0, int t0, int stride) {
   const int n = Q.n_bins;
   double* out = Q.prof + (size_t)h * n * 4;
   if (nb == 0) {
     for (int i = t0; i < 4 * n; i += stride) out[i] = 0.0;
     return;
   }
-  const double r_out = r_vir > 0.0 ? r_vir : (double)rc[idx(nb - 1)];
-  const double inv_r = 1.0 / r_out;
-  const double inv_r3 = inv_r * inv_r * inv_r;
-  auto count_le = [&](double e) {
-    const float ef = (float)e;
-    long long lo = 0, hi = nb;            // first k with rc[k] > e
+  const double r_out = r_vir > 0.0 ? r_vir : float_to_double(rc[idx(nb - 1)]);
+  const float r_out_f = double_to_float(r_out);
+  const float inv_r = 1.0f / r_out_f;
+  auto count_le = [&](int b) {               // first k with rc[k] > e_b (b = n: r_out)
+    const float ef = b == n ? r_out_f : r_out_f * Q.factor_f[b];
+    const double fac = b == n ? 1.0 : Q.factor[b];
+    long long lo = 0, hi = nb;
     while (lo < hi) {
       const long long mid = (lo + hi) >> 1;
-      if (le_edge(rc[idx(mid)], ef, e)) lo = mid + 1;
+      if (le_edge_band(rc[idx(mid)], ef, r_out, fac)) lo = mid + 1;
       else hi = mid;
     }
     return lo;
   };
   for (int b = t0; b < n; b += stride) {
-    const double e0 = r_out * Q.factor[b];
-    const double e1 = b + 1 == n ? r_out : r_out * Q.factor[b + 1];
-    const long long c0 = count_le(e0), c1 = count_le(e1);
+    const long long c0 = count_le(b), c1 = count_le(b + 1);
     // masses: count * m0 for a uniform particle mass (m0 != NULL), else the
     // exact fixed-point sums
     double M1, Mshell;
     if (m0) {
-      M1 = (double)c1 * *m0;
-      Mshell = (double)(c1 - c0) * *m0;
+      M1 = double_from_fix(c1, 0) * *m0;
+      Mshell = double_from_fix(c1 - c0, 0) * *m0;
     } else {
       const long long f0 = c0 > 0 ? mc[idx(c0 - 1)] : 0;
       const long long f1 = c1 > 0 ? mc[idx(c1 - 1)] : 0;
       M1 = double_from_fix(f1, s_m);
       Mshell = double_from_fix(f1 - f0, s_m);
     }
-    out[4 * b + 0] = (double)(c1 - c0);
+    out[4 * b + 0] = double_from_fix(c1 - c0, 0);
     out[4 * b + 1] = M1;
-    out[4 * b + 2] = shell_density(Mshell, inv_r3, Q.factor, n, b);
-    out[4 * b + 3] = circular_velocity(G, M1, inv_r, Q.factor, n, b);
+    out[4 * b + 2] = shell_density(Mshell, r_out, inv_r, Q.factor, Q.factor_f, n, b);
+    out[4 * b + 3] = circular_velocity(G, Gf, M1, r_out, inv_r, Q.factor, Q.factor_f, n, b);
   }
 }
 

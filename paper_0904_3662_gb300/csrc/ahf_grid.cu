@@ -800,18 +800,28 @@ __global__ void g_result(GridLaunch L) {
   if (nb > 0) {
     const long long kk = S.k_first;
     // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
-    const double mk = L.p.m == nullptr ? (double)(kk + 1) * L.p.m0 : double_from_fix(L.mc[H.gbase + kk], S.s_m);
-    const double rk = (double)rc[H.gbase + kk];
+    const bool unim = L.p.m == nullptr;
+    const long long mkx = unim ? 0 : L.mc[H.gbase + kk];
+    const double mk = unim ? double_from_fix(kk + 1, 0) * L.p.m0 : double_from_fix(mkx, S.s_m);
     if (kk == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
-    if (mk < L.prm.crit * rk * rk * rk) {
+    bool none;
+    if (sizeof(Real) == 4) {
+      // the decision and the values as in the on-chip classes (the same bits)
+      const float mkf = unim ? (float)(kk + 1) * L.p.m0f : float_from_fix(mkx, S.s_m);
+      none = below_threshold(mk, mkf, (float)rc[H.gbase + kk], L.prm.crit_f, L.prm.crit);
+    } else {
+      const double rk = (double)rc[H.gbase + kk];
+      none = mk < L.prm.crit * rk * rk * rk;
+    }
+    if (none) {
       status |= AHF_HALO_RVIR_NONE;
     } else {
       Rs.k_vir = kk;
       Rs.m_vir = mk;
-      Rs.r_vir = cbrt(mk / L.prm.crit);
+      Rs.r_vir = virial_radius(mk, L.prm.inv_crit);
     }
     const double mt = double_from_fix(S.m_tot, S.s_m);
-    for (int a = 0; a < 3; ++a) Rs.vbulk[a] = double_from_fix(S.mv[a], S.s_mv) / mt;
+    for (int a = 0; a < 3; ++a) Rs.vbulk[a] = quotient(double_from_fix(S.mv[a], S.s_mv), mt);
   } else {
     Rs.vbulk[0] = Rs.vbulk[1] = Rs.vbulk[2] = 0.0;
   }

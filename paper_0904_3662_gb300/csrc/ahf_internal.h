@@ -50,6 +50,7 @@ struct ParamsDev {
   float Gf, Hf, r_soft_f, band_f;
   float crit_f;        // delta_rho * 4 pi / 3 as float
   double crit;         // delta_rho * 4 pi / 3
+  double inv_crit;     // 1 / crit
   int max_iter;
   int precision;
   int vbulk_initial;   // AHF_VAR_VBULK_INITIAL: v_bulk of the initial set throughout
@@ -112,6 +113,7 @@ void profile_bin_tables(int n_bins, double r_min_frac, double *t);
 struct ProfileRows {
   double *prof;              // [n_halos][n_bins][4] (caller order), NULL = none
   const double *factor;      // the bin tables (3 n_bins doubles)
+  const float *factor_f;     // the same rounded to float
   int n_bins;
 };
 
@@ -206,6 +208,7 @@ struct ProfileLaunch {
   int *chunk_halo;         // chunk -> halo
   long long *chunk_start;  // chunk -> first position in the halo's bound list
   const double *edge_factor;  // the bin tables (3 n_bins doubles)
+  const float *edge_factor_f; // the same rounded to float
   int n_chunks;
   int n_multi;             // haloes held by more than one chunk
 };

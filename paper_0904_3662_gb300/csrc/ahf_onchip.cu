@@ -824,15 +824,16 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           if (nb > 0) {
             const int kl = (int)(k - C_pre);
             // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
-            const double mk = unim ? (double)(k + 1) * L.p.m0 : double_from_fix(mc[sw(kl, mask)], s_m);
-            const double rk = (double)rc[sw(kl, mask)];
+            const long long mkx = unim ? 0 : mc[sw(kl, mask)];
+            const double mk = unim ? double_from_fix(k + 1, 0) * L.p.m0 : double_from_fix(mkx, s_m);
+            const float mkf = unim ? (float)(k + 1) * L.p.m0f : float_from_fix(mkx, s_m);
             if (k == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
-            if (mk < P.crit * rk * rk * rk) {
+            if (below_threshold(mk, mkf, rc[sw(kl, mask)], P.crit_f, P.crit)) {
               status |= AHF_HALO_RVIR_NONE;
             } else {
               kv = k;
               mv = mk;
-              rv = cbrt(mk / P.crit);
+              rv = virial_radius(mk, P.inv_crit);
             }
           }
           R->n_bound = nb;
@@ -851,7 +852,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           }
         } else if (tid == 32 || tid == 64 || tid == 96) {
           const int c = tid / 32 - 1;
-          R->vbulk[c] = nb > 0 ? double_from_fix(S.mv[c], s_v) / double_from_fix(S.c_tot[0], s_m) : 0.0;
+          R->vbulk[c] = nb > 0 ? quotient(double_from_fix(S.mv[c], s_v), double_from_fix(S.c_tot[0], s_m)) : 0.0;
         }
       }
       if constexpr (CS > 1) {
@@ -871,15 +872,16 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
             if (Y->has_rvir) r_vir = Y->rvir;
             if (Y->nb_loc > 0) r_last = Y->last_r;
           }
-          const double r_out = r_vir > 0.0 ? r_vir : (double)r_last;
+          const double r_out = r_vir > 0.0 ? r_vir : float_to_double(r_last);
+          const float r_out_f = double_to_float(r_out);
           const int n = L.rows.n_bins;
           for (int b = tid; b <= n; b += NT) {
-            const double e = b == n ? r_out : r_out * L.rows.factor[b];
-            const float ef = (float)e;
-            int lo = 0, hi = (int)C_loc;            // first local k with rc[k] > e
+            const float ef = b == n ? r_out_f : r_out_f * L.rows.factor_f[b];
+            const double fac = b == n ? 1.0 : L.rows.factor[b];
+            int lo = 0, hi = (int)C_loc;            // first local k with rc[k] > e_b
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (le_edge(rc[sw(mid, mask)], ef, e)) lo = mid + 1;
+              if (le_edge_band(rc[sw(mid, mask)], ef, r_out, fac)) lo = mid + 1;
               else hi = mid;
             }
             X.pc[b] = lo;
@@ -888,8 +890,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           Cl<CS>::sync();
           if (rank == 0) {
             double* out = L.rows.prof + (size_t)H.index * n * 4;
-            const double inv_r = 1.0 / r_out;
-            const double inv_r3 = inv_r * inv_r * inv_r;
+            const float inv_r = 1.0f / r_out_f;
             for (int b = tid; b < n; b += NT) {
               long long c0 = 0, c1 = 0, f0 = 0, f1 = 0;
               for (int r2 = 0; r2 < CS; ++r2) {
@@ -905,16 +906,16 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
               }
               double M1, Ms;
               if (unim) {
-                M1 = (double)c1 * L.p.m0;
-                Ms = (double)(c1 - c0) * L.p.m0;
+                M1 = double_from_fix(c1, 0) * L.p.m0;
+                Ms = double_from_fix(c1 - c0, 0) * L.p.m0;
               } else {
                 M1 = double_from_fix(f1, s_m);
                 Ms = double_from_fix(f1 - f0, s_m);
               }
-              out[4 * b + 0] = (double)(c1 - c0);
+              out[4 * b + 0] = double_from_fix(c1 - c0, 0);
               out[4 * b + 1] = M1;
-              out[4 * b + 2] = shell_density(Ms, inv_r3, L.rows.factor, n, b);
-              out[4 * b + 3] = circular_velocity(P.G, M1, inv_r, L.rows.factor, n, b);
+              out[4 * b + 2] = shell_density(Ms, r_out, inv_r, L.rows.factor, L.rows.factor_f, n, b);
+              out[4 * b + 3] = circular_velocity(P.G, P.Gf, M1, r_out, inv_r, L.rows.factor, L.rows.factor_f, n, b);
             }
           }
         }
@@ -923,7 +924,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         if (L.rows.prof) {
           __syncthreads();                        // S.rvir
           profile_rows(L.rows, H.index, rc, mc, [&](long long kk) { return sw((int)kk, mask); }, nb, S.rvir, s_m,
-                       P.G, unim ? &L.p.m0 : nullptr, tid, NT);
+                       P.G, P.Gf, unim ? &L.p.m0 : nullptr, tid, NT);
         }
       }
     }

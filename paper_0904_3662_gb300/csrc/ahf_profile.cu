@@ -55,8 +55,8 @@ __device__ void write_rows(const ProfileLaunch& L, int h, const double* e, const
   __shared__ double carry;
   const int n = L.n_bins;
   double* out = L.prof + (size_t)h * n * 4;
-  const double inv_r = 1.0 / e[n];
-  const double inv_r3 = inv_r * inv_r * inv_r;
+  const double r_out = e[n];
+  const float inv_r = 1.0f / double_to_float(r_out);
   if (threadIdx.x == 0) carry = inner;
   __syncthreads();
   for (int b0 = 0; b0 < n; b0 += PT) {
@@ -67,8 +67,8 @@ __device__ void write_rows(const ProfileLaunch& L, int h, const double* e, const
     if (b < n) {
       out[4 * b + 0] = (double)cnt[b];
       out[4 * b + 1] = run;
-      out[4 * b + 2] = shell_density(mb, inv_r3, L.edge_factor, n, b);
-      out[4 * b + 3] = circular_velocity(L.prm.G, run, inv_r, L.edge_factor, n, b);
+      out[4 * b + 2] = shell_density(mb, r_out, inv_r, L.edge_factor, L.edge_factor_f, n, b);
+      out[4 * b + 3] = circular_velocity(L.prm.G, L.prm.Gf, run, r_out, inv_r, L.edge_factor, L.edge_factor_f, n, b);
     }
     __syncthreads();
     if (threadIdx.x == PT - 1) carry = run;

@@ -162,12 +162,13 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   L.prm.band_f = (float)prm->band;
   L.prm.crit = prm->delta_rho * (4.0 * M_PI / 3.0);
   L.prm.crit_f = (float)L.prm.crit;
+  L.prm.inv_crit = 1.0 / L.prm.crit;
   L.prm.max_iter = prm->max_iter;
   L.prm.precision = prm->precision;
   L.prm.vbulk_initial = (prm->variant & AHF_VAR_VBULK_INITIAL) ? 1 : 0;
   L.out.res = out; L.out.bound_idx = (long long*)bound_idx; L.out.phi = phi; L.out.removed_iter = removed_iter;
   L.out.member_idx = (const long long*)member_idx; L.out.n_slots = n_slots; L.out.err = counters + 8;
-  L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.n_bins = 0;
+  L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.factor_f = nullptr; L.rows.n_bins = 0;
   L.trace = nullptr;
   L.variant = 0;
   L.rec = nullptr;                  // no scratch for records: the fill re-reads the particle store

@@ -307,15 +307,16 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       double mvir = 0.0;
       if (nb > 0) {
         // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
-        const double mk = unim ? (double)(kf + 1) * L.p.m0 : double_from_fix(mc[sw(kf, mask)], s_m);
-        const double rk = (double)rc[sw(kf, mask)];
+        const long long mkx = unim ? 0 : mc[sw(kf, mask)];
+        const double mk = unim ? double_from_fix(kf + 1, 0) * L.p.m0 : double_from_fix(mkx, s_m);
+        const float mkf = unim ? (float)(kf + 1) * L.p.m0f : float_from_fix(mkx, s_m);
         if (kf == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
-        if (mk < P.crit * rk * rk * rk) {
+        if (below_threshold(mk, mkf, rc[sw(kf, mask)], P.crit_f, P.crit)) {
           status |= AHF_HALO_RVIR_NONE;
         } else {
           kv = kf;
           mvir = mk;
-          r_vir_l = cbrt(mk / P.crit);
+          r_vir_l = virial_radius(mk, P.inv_crit);
         }
       }
       ahf_result* R = L.out.res + H.index;
@@ -330,11 +331,11 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       R->r_vir = r_vir_l;
     } else if (lane < 4) {
       const long long m = lane == 1 ? mv[0] : (lane == 2 ? mv[1] : mv[2]);
-      L.out.res[H.index].vbulk[lane - 1] = nb > 0 ? double_from_fix(m, s_v) / double_from_fix(M_tot, s_m) : 0.0;
+      L.out.res[H.index].vbulk[lane - 1] = nb > 0 ? quotient(double_from_fix(m, s_v), double_from_fix(M_tot, s_m)) : 0.0;
     }
     if (L.rows.prof) {
       const double r_vir = __shfl_sync(FULL_MASK, r_vir_l, 0);
-      profile_rows(L.rows, H.index, rc, mc, [&](long long k) { return sw((int)k, mask); }, nb, r_vir, s_m, P.G,
+      profile_rows(L.rows, H.index, rc, mc, [&](long long k) { return sw((int)k, mask); }, nb, r_vir, s_m, P.G, P.Gf,
                    unim ? &L.p.m0 : nullptr, lane, 32);
     }
     if (lane == 0 && L.trace) {

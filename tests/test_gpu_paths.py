@@ -314,7 +314,9 @@ def test_fused_profile_matches_standalone_and_oracle(with_masses):
         a = fused["prof"].cpu().numpy()
         b = sep.cpu().numpy()
         np.testing.assert_array_equal(a[:, :, 0], b[:, :, 0])
-        np.testing.assert_allclose(a[:, :, 1:], b[:, :, 1:], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(a[:, :, 1], b[:, :, 1], rtol=1e-12, atol=0)
+        # density and v_circ are formed in float from the (exact) masses
+        np.testing.assert_allclose(a[:, :, 2:], b[:, :, 2:], rtol=1e-6, atol=0)
         res = ahf.results_to_numpy(fused["res"])
         compare(pop, prm, res, fused["bound_idx"].cpu().numpy(), fused["phi"].cpu().numpy(),
                 fused["removed_iter"].cpu().numpy())
