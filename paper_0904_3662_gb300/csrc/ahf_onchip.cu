@@ -213,29 +213,19 @@ __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint
     const int shift = 8 * passes[ip];
     for (int i = threadIdx.x; i < NW * 256; i += NT) hist[i] = 0;
     __syncthreads();
-    uint32_t key[IPT], val[IPT];
+    // keys are read again for the scatter (the input buffer does not change
+    // during a pass): only the ranks stay in registers
     uint16_t rank_in[IPT];
 #pragma unroll
     for (int b = 0; b < IPT; ++b) {
       if (b < nb) {
         const int e = warp * wchunk + b * 32 + lane;
         const bool valid = e < nloc;
-        key[b] = 0u;
-        val[b] = 0u;
-        if (valid) {
-          if (ip == 0) {                        // the gather's separate arrays
-            key[b] = kA[e];
-            val[b] = vA[e];
-          } else {
-            const uint2 x = pin[e];
-            key[b] = x.x;
-            val[b] = x.y;
-          }
-        }
+        const uint32_t key = valid ? (ip == 0 ? kA[e] : pin[e].x) : 0u;   // pass 0: the gather's arrays
         const unsigned vmask = __ballot_sync(FULL_MASK, valid);
         rank_in[b] = 0;
         if (valid) {
-          const uint32_t dg = (key[b] >> shift) & 0xffu;
+          const uint32_t dg = (key >> shift) & 0xffu;
           const unsigned peers = __match_any_sync(vmask, dg);
           const unsigned below = peers & lanemask_lt();
           const uint16_t base = hist[warp * 256 + dg];
@@ -285,10 +275,11 @@ __device__ int cluster_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint
       if (b < nb) {
         const int e = warp * wchunk + b * 32 + lane;
         if (e < nloc) {
-          const uint32_t dg = (key[b] >> shift) & 0xffu;
+          const uint2 kv = ip == 0 ? make_uint2(kA[e], vA[e]) : pin[e];
+          const uint32_t dg = (kv.x >> shift) & 0xffu;
           const int g = (int)S.dtot[dg] + (int)hist[warp * 256 + dg] + (int)rank_in[b];
           const int q = g / chunk;
-          Cl<CS>::at(pout, q)[g - q * chunk] = make_uint2(key[b], val[b]);
+          Cl<CS>::at(pout, q)[g - q * chunk] = kv;
         }
       }
     }
