@@ -18,7 +18,7 @@ namespace {
 constexpr int WARP_CAP = 512;                 // candidate slots per warp
 constexpr int IPL = WARP_CAP / 32;            // items per lane
 constexpr int WPB = 8;                        // warps per CTA
-constexpr size_t WARP_BYTES = (size_t)WARP_CAP * 24 + (size_t)count_sort_words(32) * 4;
+constexpr size_t WARP_BYTES = (size_t)WARP_CAP * 24 + 256 * 2;
 
 __device__ __forceinline__ int sw(int p, int mask) { return p ^ ((p >> 5) & mask); }
 
@@ -26,6 +26,88 @@ __device__ __forceinline__ long long warp_excl(long long x, int lane, long long&
   const long long inc = warp_inclusive_scan(x, lane);
   total = __shfl_sync(FULL_MASK, inc, 31);
   return inc - x;
+}
+
+// Stable LSD radix sort of n <= WARP_CAP (key, val) pairs by one warp, 8-bit
+// digits ranked by lane matching; the last pass writes element p at
+// sw(p, mask).  For one warp this is faster than the CTA classes' counting
+// sort (4 passes at most instead of 6); keys are read again for the scatter,
+// so only the ranks stay in registers.  Returns 0 if the result is in
+// (kA, vA), 1 if in (kB, vB).
+__device__ int warp_radix_sort(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, uint16_t* hist, int n,
+                               uint32_t diff, int mask, int lane) {
+  int passes[4], np = 0;
+  for (int d = 0; d < 4; ++d)
+    if ((diff >> (8 * d)) & 0xffu) passes[np++] = d;
+  if (np == 0) {
+    for (int p = lane; p < n; p += 32) {
+      kB[sw(p, mask)] = kA[p];
+      vB[sw(p, mask)] = vA[p];
+    }
+    __syncwarp();
+    return 1;
+  }
+  uint32_t *kin = kA, *vin = vA, *kout = kB, *vout = vB;
+  const int nb = (n + 31) / 32;
+  for (int ip = 0; ip < np; ++ip) {
+    const int shift = 8 * passes[ip];
+    const bool last = (ip == np - 1);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
+    __syncwarp();
+    uint16_t rk[IPL];
+#pragma unroll
+    for (int b = 0; b < IPL; ++b) {
+      if (b < nb) {
+        const int e = b * 32 + lane;
+        const bool valid = e < n;
+        const uint32_t key = valid ? kin[e] : 0u;
+        const unsigned vmask = __ballot_sync(FULL_MASK, valid);
+        rk[b] = 0;
+        if (valid) {
+          const uint32_t dg = (key >> shift) & 0xffu;
+          const unsigned peers = __match_any_sync(vmask, dg);
+          const unsigned below = peers & lanemask_lt();
+          const uint16_t base = hist[dg];
+          rk[b] = (uint16_t)(base + __popc(below));
+          __syncwarp(vmask);
+          if (below == 0) hist[dg] = (uint16_t)(base + __popc(peers));
+        }
+        __syncwarp();
+      }
+    }
+    // exclusive offsets of the 256 digits (8 consecutive digits per lane)
+    {
+      uint32_t loc[8], s = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { loc[i] = hist[lane * 8 + i]; s += loc[i]; }
+      const uint32_t inc = warp_inclusive_scan(s, lane);
+      uint32_t run = inc - s;
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { hist[lane * 8 + i] = (uint16_t)run; run += loc[i]; }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int b = 0; b < IPL; ++b) {
+      if (b < nb) {
+        const int e = b * 32 + lane;
+        if (e < n) {
+          const uint32_t key = kin[e], val = vin[e];
+          const uint32_t dg = (key >> shift) & 0xffu;
+          int dst = (int)hist[dg] + (int)rk[b];
+          if (last) dst = sw(dst, mask);
+          kout[dst] = key;
+          vout[dst] = val;
+        }
+      }
+    }
+    __syncwarp();
+    uint32_t* t;
+    t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  return (kin == kA) ? 0 : 1;
 }
 
 template <int CT>
@@ -39,7 +121,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
   uint32_t* vB = kB + WARP_CAP;
   float* ex1 = (float*)(vB + WARP_CAP);
   float* ex2 = ex1 + WARP_CAP;
-  uint32_t* sort_aux = (uint32_t*)(ex2 + WARP_CAP);
+  uint16_t* hist = (uint16_t*)(ex2 + WARP_CAP);
   const ParamsDev& P = L.prm;
 
   for (;;) {
@@ -59,8 +141,8 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     while (ipt * 32 < n_cand) ipt <<= 1;
     const int mask = ipt - 1;
 
-    // ---- gather: keys in runs of ipt per lane (swizzled) for the sort ----
-    uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u, kmx = 0u;
+    // ---- gather ----
+    uint32_t orb = 0u, andb = 0xffffffffu, mxm = 0u, mxr = 0u, mxv = 0u;
     int nmem = 0;
     for (int i = lane; i < n_cand; i += 32) {
       const long long slot = H.offset + i;
@@ -90,20 +172,16 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
         }
       }
       if (key == KEY_NONMEMBER && L.out.removed_iter) L.out.removed_iter[slot] = -1;
-      kA[sw(i, mask)] = key;
-      vA[sw(i, mask)] = (uint32_t)i;
-      if (key != KEY_NONMEMBER) {      // the key range is the members'
-        orb |= key;
-        andb &= key;
-        kmx = max(kmx, key);
-      }
+      kA[i] = key;
+      vA[i] = (uint32_t)i;
+      orb |= key;
+      andb &= key;
     }
     orb = __reduce_or_sync(FULL_MASK, orb);
     andb = __reduce_and_sync(FULL_MASK, andb);
     mxm = __reduce_max_sync(FULL_MASK, mxm);
     mxr = __reduce_max_sync(FULL_MASK, mxr);
     mxv = __reduce_max_sync(FULL_MASK, mxv);
-    kmx = __reduce_max_sync(FULL_MASK, kmx);
     const int n_mem = (int)__reduce_add_sync(FULL_MASK, (unsigned)nmem);
     __syncwarp();
     const int s_m = fix_scale(float_exponent_of_bits(mxm), n_mem);
@@ -114,15 +192,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
 
     if (lane == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
-    uint32_t diff = 0u, sub = 0u;          // non-members sort last, keyed just above the members
-    if (n_mem > 0) {
-      diff = orb ^ andb;
-      if (n_mem < n_cand) {
-        sub = kmx + 1u;
-        diff = (orb | sub) ^ (andb & sub);
-      }
-    }
-    const int which = count_sort<32, IPL>(kA, vA, kB, vB, sort_aux, nullptr, n_cand, mask, diff, sub, lane);
+    const int which = warp_radix_sort(kA, vA, kB, vB, hist, n_cand, orb ^ andb, mask, lane);
     float* rr = (float*)(which ? kB : kA);
     uint32_t* jj = which ? vB : vA;
     float* mm = (float*)(which ? kA : kB);
