@@ -3,13 +3,16 @@
 //
 // Per halo (Sect. 2.1 and Appendix A):
 //   gather   candidates -> (radius key, candidate position), FP64-accurate
-//            recentring and sphere test, exponent maxima for the exact sums
+//            recentring and sphere test, exponent maxima for the exact sums;
+//            each member's offset, mass and velocity to its 32-byte record
 //   sort     stable LSD radix sort of the keys, once: the centre is fixed and
 //            particles only leave, so the survivors of every later iteration
-//            stay in radial order.  In a cluster each CTA holds a contiguous
-//            chunk of the order and the scatter writes into the owner CTA's
-//            shared memory.
-//   fill     sorted SoA: radius, mass, w = v + H d; exact sum m v
+//            stay in radial order.  One CTA ranks 5-bit digits by counting
+//            (count_sort); a cluster ranks 8-bit digits by lane matching, each
+//            CTA holding a contiguous chunk of the order, the scatter writing
+//            into the owner CTA's shared memory.
+//   fill     sorted SoA from the records: radius, mass, w = v + H d; exact
+//            sum m v
 //   iterate  scan of the exact M(<r) and sum m/r prefixes ->
 //            phi_i = -G [M(<r_i)/r_i + sum_{j>=i} m_j/r_j], escape test
 //            |w - v_bulk|^2 > 2|phi|, removal of every unbound particle, until
