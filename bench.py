@@ -193,16 +193,19 @@ class ClockSampler:
 
 # ---- algorithmic bytes per phase (see the design notes) --------------------------------
 
-def class_of(counts):
-    """Size class of each halo as the library's scheduler assigns it:
-    0 warp, 1-3 single-CTA shared-memory variants, 4-7 clusters of 2/4/8/16
-    CTAs, 8 the multi-CTA class."""
+def traced_classes(ctx, step, pop):
+    """The size class each halo ran in (the library may promote the haloes
+    of a small batch): the class recorded by a traced step for on-chip
+    haloes, the multi-CTA class for the others."""
+    import torch
     from paper_0904_3662_gb300 import ahf
-    caps = ahf.VARIANT_CAPS
-    cls = np.full(counts.shape[0], len(caps))
-    for v in range(len(caps) - 1, -1, -1):
-        cls = np.where(counts <= caps[v], v, cls)
-    return cls
+    ctx.set_option(ahf.OPT_TRACE, 1)
+    step()
+    torch.cuda.synchronize()
+    ctx.sync()
+    ctx.set_option(ahf.OPT_TRACE, 0)
+    t = ctx.trace(pop.n_halos)
+    return np.where(t[:, 0] > 0, t[:, 7] & 255, len(ahf.VARIANT_CAPS))
 
 
 def phase_bytes(pop, res, cls):
@@ -371,7 +374,7 @@ def run_ahf(args):
     ctx.sync()
     res = ahf.results_to_numpy(out["res"])
     units = float(res["part_iter"].sum())
-    cls = class_of(pop.count)
+    cls = traced_classes(ctx, step, pop)
     pbytes = phase_bytes(pop, res, cls)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

@@ -259,6 +259,12 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        its kernel alone (as a profiler's launch list does);
  *                        0 (default) = concurrently on side streams.  Results
  *                        are the same bits either way.
+ *   AHF_OPT_PROMOTE      1 (default) = a batch that would leave SMs idle runs its
+ *                        haloes in larger size classes (up to two classes up,
+ *                        more threads per halo, lower latency) as long as the
+ *                        whole batch still runs at once; 0 = every halo in the
+ *                        smallest class that holds it.  Results are the same
+ *                        bits either way.
  *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
  *                        arrays that are page-locked (cudaHostAlloc,
  *                        cudaHostRegister) and write page-locked outputs in
@@ -275,6 +281,7 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
 #define AHF_OPT_GRAPHS     5
 #define AHF_OPT_TRACE      6
 #define AHF_OPT_SERIAL     7
+#define AHF_OPT_PROMOTE    8
 
 /* Per-call statistics of the most recent unbinding or profile call.
  * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the

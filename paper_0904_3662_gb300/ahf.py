@@ -25,6 +25,7 @@ COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
 VAR_VBULK_INITIAL, VAR_RETRUNCATE = 1, 2
 OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE, OPT_SERIAL = 1, 2, 3, 4, 5, 6, 7
+OPT_PROMOTE = 8
 TRACE_FIELDS = 8
 N_PHASES = 12
 PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster2_16k", "cluster4_32k", "cluster8_64k",

@@ -147,6 +147,7 @@ struct ahf_ctx {
   size_t aux_bytes = 0;
   bool trace = false;                // per-halo timestamps from the on-chip kernels
   bool serial = false;               // on-chip classes one after another on the caller's stream
+  bool promote = true;               // small batches take larger classes (lower latency)
   long long* trace_dev = nullptr;    // [n][AHF_TRACE_FIELDS] of the last traced call
   int64_t trace_cap = 0;             // haloes trace_dev holds
   int64_t trace_n = -1;              // haloes of the last traced call (-1: none)
@@ -346,8 +347,37 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
       for (int v = 0; v < NV; ++v)
         if (n <= caps[v]) { k = v; break; }
     cls[h] = k;
-    P.n_class[k]++;
   }
+  // latency: a batch that leaves SMs idle moves its haloes to larger classes
+  // (more threads per halo; every class gives the same bits), at most two
+  // classes up and to the 8-CTA cluster (the 16-CTA one for haloes that
+  // start in a 4-CTA cluster or larger), while the whole batch still runs at
+  // once
+  if (c->promote) {
+    double inflight[NV];
+    for (int v = 0; v < NV; ++v)
+      inflight[v] = v == 0 ? (double)c->variant_grid[0] * warp_halos_per_cta()
+                           : (double)c->variant_grid[v] / onchip_cluster_size(v - 1);
+    const std::vector<int> base = cls;
+    for (int round = 0; round < 2; ++round) {
+      std::vector<int> next = cls;
+      double load = 0.0;
+      bool moved = false;
+      for (int64_t h = 0; h < n_halos; ++h) {
+        const int k = cls[(size_t)h];
+        if (k >= NV) continue;
+        const int top = base[(size_t)h] >= 5 ? NV - 1 : 6;
+        if (k + 1 <= top && caps[k + 1] > 0 && inflight[k + 1] >= 1.0) {
+          next[(size_t)h] = k + 1;
+          moved = true;
+        }
+        load += 1.0 / inflight[next[(size_t)h]];
+      }
+      if (!moved || load > 1.0) break;
+      cls.swap(next);
+    }
+  }
+  for (int64_t h = 0; h < n_halos; ++h) P.n_class[cls[(size_t)h]]++;
   // order: by class, largest first within a class (ties by input position),
   // as one sort of packed keys (class | ~count | position)
   std::vector<uint64_t> key((size_t)n_halos);
@@ -1469,6 +1499,10 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "serial is 0 or 1");
       c->serial = value == 1;
       return AHF_OK;
+    case AHF_OPT_PROMOTE:
+      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "promote is 0 or 1");
+      c->promote = value == 1;
+      return AHF_OK;
     default:
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
@@ -1484,6 +1518,7 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
     case AHF_OPT_TRACE: *value = c->trace ? 1 : 0; return AHF_OK;
     case AHF_OPT_SERIAL: *value = c->serial ? 1 : 0; return AHF_OK;
+    case AHF_OPT_PROMOTE: *value = c->promote ? 1 : 0; return AHF_OK;
     default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }

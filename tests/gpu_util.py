@@ -20,7 +20,11 @@ def require_gpu():
 def run_gpu(pop, params=None, halos=None, member_idx=None, plain=False, ctx=None, **kw):
     torch = require_gpu()
     from paper_0904_3662_gb300 import ahf
-    ctx = ctx or ahf.Context(0)
+    if ctx is None:
+        ctx = ahf.Context(0)
+        # the smallest class per halo, so that each test exercises the classes
+        # its sizes select (promotion of small batches has its own tests)
+        ctx.set_option(ahf.OPT_PROMOTE, 0)
     parts = ahf.particles_from_population(pop)
     prm = params or ahf.params_for(pop)
     hal = ahf.halos_from_population(pop) if halos is None else halos

@@ -369,6 +369,7 @@ def test_trace_fields_and_results_unchanged():
     from paper_0904_3662_gb300 import ahf
     pop = synth.halo_batch(seed=73, n_halos=60, n_lo=100, n_hi=200_000)
     ctx = ahf.Context(0)
+    ctx.set_option(ahf.OPT_PROMOTE, 0)               # each halo in the smallest class
     parts = ahf.particles_from_population(pop)
     hal = ahf.halos_from_population(pop)
     prm = ahf.params_for(pop)
@@ -419,3 +420,33 @@ def test_serial_classes_same_bits():
     assert used and all(st["phase_ms"][k] > 0 for k in used)
     with pytest.raises(ahf.AHFError):
         ctx.set_option(ahf.OPT_SERIAL, 2)
+
+
+@pytest.mark.parametrize("case", ["single", "small_warp", "cta", "clusters"])
+def test_promotion_same_bits(case):
+    """AHF_OPT_PROMOTE (the default): a batch that leaves SMs idle runs in
+    larger classes, with the same results as in the smallest ones."""
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = {"single": lambda: synth.single_halo(seed=synth.SEED_BASE + 1),
+           "small_warp": lambda: synth.halo_batch(seed=81, n_halos=3, n_lo=150, n_hi=400),
+           "cta": lambda: synth.halo_batch(seed=82, n_halos=8, n_lo=1500, n_hi=6000),
+           "clusters": lambda: synth.halo_batch(seed=83, n_halos=4, n_lo=9000, n_hi=40000)}[case]()
+    base, _, c0, _ = run_gpu(pop)                              # the smallest classes
+    st0 = c0.stats()["phase_halos"][:8]
+    ctx = ahf.Context(0)
+    assert ctx.get_option(ahf.OPT_PROMOTE) == 1
+    prom, _, _, _ = run_gpu(pop, ctx=ctx)
+    st1 = ctx.stats()["phase_halos"][:8]
+    # every halo moved up (the batches are far below the machine's capacity)
+    mean0 = sum(k * n for k, n in enumerate(st0)) / max(1, sum(st0))
+    mean1 = sum(k * n for k, n in enumerate(st1)) / max(1, sum(st1))
+    assert sum(st1) == sum(st0) == pop.n_halos and mean1 > mean0, (st0, st1)
+    assert prom["res"].tobytes() == base["res"].tobytes()
+    np.testing.assert_array_equal(prom["removed_iter"], base["removed_iter"])
+    for h in range(pop.n_halos):
+        lo, nb = int(pop.offset[h]), int(base["res"][h]["n_bound"])
+        np.testing.assert_array_equal(prom["bound_idx"][lo:lo + nb], base["bound_idx"][lo:lo + nb])
+        np.testing.assert_array_equal(prom["phi"][lo:lo + nb], base["phi"][lo:lo + nb])
+    with pytest.raises(ahf.AHFError):
+        ctx.set_option(ahf.OPT_PROMOTE, 3)
