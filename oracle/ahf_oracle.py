@@ -63,6 +63,7 @@ NOT_CONVERGED = 1
 EMPTY = 2
 RVIR_BEYOND_EDGE = 4
 RVIR_NONE = 8
+RISE_EDGE = 16          # the extent is the rise of the density profile (variant)
 
 
 @dataclasses.dataclass
@@ -76,6 +77,7 @@ class Params:
     band: float = 1e-5
     vbulk_initial: bool = False   # variant: v_bulk of the initial set in every iteration
     retruncate: bool = False      # variant: unbind again within r_vir (second pass)
+    rise_edge: bool = False       # variant: extent at the rise of the density profile
 
 
 def _f64(a):
@@ -167,6 +169,37 @@ def virial(r, m, delta_rho):
     return r_vir, m_vir, k, status
 
 
+RISE_SHELLS = 16        # equal-count shells of the bound set
+RISE_MIN_N = 64         # fewer members: no density-profile edge
+
+
+def rise_edge(r, m):
+    """Edge of a halo whose mean overdensity never drops below the threshold:
+    the rise of the density profile (Sect. 2.1, the truncation of subhaloes).
+
+    The bound set, sorted by radius, is cut into RISE_SHELLS shells of equal
+    particle count (shell s ends with particle b_s = (s+1) n / RISE_SHELLS - 1);
+    the density of shell s is its mass over the volume between the radii of
+    particles b_{s-1} and b_s.  Among the shells of the outer half (s >=
+    RISE_SHELLS / 2) the first one of least density is the edge if a shell
+    beyond it is denser; the halo then ends with its last particle.
+    Returns that particle's index, or None (no rise, or too few members)."""
+    n = r.shape[0]
+    if n < RISE_MIN_N:
+        return None
+    b = [(s + 1) * n // RISE_SHELLS - 1 for s in range(RISE_SHELLS)]
+    mk = np.cumsum(m)
+    rho = {}
+    for s in range(RISE_SHELLS // 2, RISE_SHELLS):
+        lo, hi = b[s - 1], b[s]
+        vol = 4.0 * math.pi / 3.0 * (float(r[hi]) ** 3 - float(r[lo]) ** 3)
+        rho[s] = (mk[hi] - mk[lo]) / vol if vol > 0.0 else math.inf
+    smin = min(rho, key=lambda s: (rho[s], s))
+    if any(rho[s] > rho[smin] for s in rho if s > smin):
+        return b[smin]
+    return None
+
+
 def unbind_halo(d, v, m, inside, params: Params, forced=None, u_th=None):
     """Iterative unbinding of one halo (Appendix A; Sect. 2.1).
 
@@ -233,6 +266,12 @@ def unbind_halo(d, v, m, inside, params: Params, forced=None, u_th=None):
         vbulk = (mo[:, None] * v[order]).sum(axis=0) / mo.sum()
         r_vir, m_vir, k_vir, vst = virial(r[order], mo, params.delta_rho)
         status |= vst
+        if params.rise_edge and (vst & RVIR_BEYOND_EDGE) and not (vst & RVIR_NONE):
+            k = rise_edge(r[order], mo)
+            if k is not None:
+                # the subhalo ends at the least dense shell before the rise
+                k_vir, r_vir, m_vir = k, float(r[order][k]), float(np.cumsum(mo)[k])
+                status |= RISE_EDGE
     else:
         vbulk = np.zeros(3)
         r_vir, m_vir, k_vir = 0.0, 0.0, -1

@@ -303,6 +303,48 @@ def precision_sweep(seed=SEED_BASE + 4, n_halos=100_000, n_lo=100, n_hi=100_000)
                       name=f"sweep_{n_halos}_nfw_{n_lo}-{n_hi}_cont10_f64")
 
 
+def shell_profile_batch(seed=SEED_BASE + 8, n_shells=(25, 100, 1250), rise=True, sigma_v=1.0, rho_shells=None):
+    """Haloes whose density profile is designed shell by shell: 16 shells of
+    n particles each (one halo per entry of n_shells), shell densities
+    falling by 2 per shell to shell 11 and, with rise=True, growing by 1.5
+    per shell beyond it (a subhalo seen against its host's rising
+    background); positions uniform in volume within each shell, cold
+    velocities, uniform mass.  rho_shells (16 relative densities) replaces
+    that design.  The mean density stays far above 200 rho_crit throughout,
+    so the virial crossing is never reached inside the set."""
+    rng = np.random.default_rng(seed)
+    n_h = len(n_shells)
+    counts = np.array([16 * n for n in n_shells], dtype=np.int64)
+    offset = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    tot = int(counts.sum())
+    pos = np.zeros((tot, 3)); vel = np.zeros((tot, 3))
+    radius = np.zeros(n_h)
+    m0 = PARTICLE_MASS
+    for h, n in enumerate(n_shells):
+        if rho_shells is not None:
+            rho = [1e12 * 0.5 ** 11 * float(x) for x in rho_shells]
+        else:
+            rho = [1e12 * 0.5 ** s if s <= 11 else 1e12 * 0.5 ** 11 * (1.5 ** (s - 11) if rise else 0.5 ** (s - 11))
+                   for s in range(16)]
+        r_in = 0.0
+        parts = []
+        for s in range(16):
+            r_out = (r_in ** 3 + 3.0 * n * m0 / (4.0 * math.pi * rho[s])) ** (1.0 / 3.0)
+            rr = (r_in ** 3 + (r_out ** 3 - r_in ** 3) * rng.uniform(0.0, 1.0, n)) ** (1.0 / 3.0)
+            parts.append(_iso_dirs(rng, n) * rr[:, None])
+            r_in = r_out
+        lo = int(offset[h])
+        pos[lo:lo + 16 * n] = np.concatenate(parts)
+        vel[lo:lo + 16 * n] = rng.standard_normal((16 * n, 3)) * sigma_v
+        radius[h] = 1.01 * r_in
+    f = np.float32
+    return Population(name=f"shell_profile_{'rise' if rise else 'fall'}", coord_type=COORD_F32_REL,
+                      x=pos[:, 0].astype(f), y=pos[:, 1].astype(f), z=pos[:, 2].astype(f),
+                      vx=vel[:, 0].astype(f), vy=vel[:, 1].astype(f), vz=vel[:, 2].astype(f),
+                      m=None, m0=m0, box=0.0, centre=np.zeros((n_h, 3)), radius=radius, offset=offset,
+                      count=counts, r200=np.zeros(n_h), conc=np.zeros(n_h))
+
+
 def with_gas(pop, frac=0.3, u_max=5e4, seed=SEED_BASE + 7):
     """A copy of pop in which a random fraction of the particles are gas with
     a specific thermal energy uniform on [0, u_max) (km/s)^2 (the others 0),

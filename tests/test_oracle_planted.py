@@ -109,3 +109,32 @@ def test_properties_mutant_is_caught(name, func, old, new, monkeypatch):
         except Exception:
             failed.append(pin.__name__)
     assert failed, f"mutant {name} passed every pin"
+
+
+from tests import test_oracle_variants as variant_pins
+
+RISE_MUTANTS = [
+    ("rise_edge_next_shell", "rise_edge", "return b[smin]", "return b[smin] + 1"),
+    ("rise_edge_inner_radius", "rise_edge", "float(r[hi]) ** 3 - float(r[lo]) ** 3",
+     "float(r[hi]) ** 3 - float(r[lo - 1]) ** 3 * 0.0"),
+    ("rise_edge_no_rise_test", "rise_edge", "if any(rho[s] > rho[smin] for s in rho if s > smin):", "if True:"),
+    ("rise_edge_max_not_min", "rise_edge", "smin = min(rho, key=lambda s: (rho[s], s))",
+     "smin = max(rho, key=lambda s: (rho[s], s))"),
+    ("rise_edge_shell_mass", "rise_edge", "(mk[hi] - mk[lo]) / vol", "mk[hi] / vol"),
+]
+
+RISE_PINS = [variant_pins.test_rise_edge_truncates_at_the_density_minimum,
+             variant_pins.test_rise_edge_leaves_other_haloes_alone, variant_pins.test_rise_edge_uses_shell_masses]
+
+
+@pytest.mark.parametrize("name,func,old,new", RISE_MUTANTS, ids=[m[0] for m in RISE_MUTANTS])
+def test_rise_edge_mutant_is_caught(name, func, old, new, monkeypatch):
+    mod = _mutant_module(func, old, new, monkeypatch)
+    monkeypatch.setattr(variant_pins, "O", mod)
+    failed = []
+    for pin in RISE_PINS:
+        try:
+            pin()
+        except Exception:
+            failed.append(pin.__name__)
+    assert failed, f"mutant {name} passed every pin"

@@ -1,9 +1,11 @@
 """Pins of the oracle's method variants: the bulk velocity fixed from the
-initial set, and the second unbinding pass within r_vir (Appendix A's
-truncation at r_vir)."""
+initial set, the second unbinding pass within r_vir (Appendix A's
+truncation at r_vir), the subhalo edge at the rise of the density profile,
+gas thermal energy and the host/subhalo hierarchy."""
 import dataclasses
 
 import numpy as np
+import pytest
 
 from oracle import ahf_oracle as O
 from paper_0904_3662_gb300 import synth
@@ -230,3 +232,61 @@ def test_hierarchy_excludes_what_subhaloes_bound():
     none = O.unbind_hierarchy(pop, prm, np.full(5, -1), member_idx=mi)
     for h in range(5):
         np.testing.assert_array_equal(none[h]["bound_idx"], flat[h]["bound_idx"])
+
+
+def test_rise_edge_truncates_at_the_density_minimum():
+    # Sect. 2.1: a subhalo whose overdensity never drops below the threshold
+    # ends where its density profile rises.  The designed haloes (16 shells
+    # of n particles, density halving per shell to shell 11, then growing)
+    # end with the last particle of shell 11; the mean density at the edge
+    # is still far above delta_rho (no virial crossing inside the set).
+    pop = synth.shell_profile_batch(rise=True)
+    base = O.unbind_population(pop, O.Params())
+    rise = O.unbind_population(pop, O.Params(rise_edge=True))
+    for h in range(pop.n_halos):
+        n = int(pop.count[h]) // 16
+        a, b = base[h], rise[h]
+        assert a["status"] == O.RVIR_BEYOND_EDGE and b["status"] == O.RVIR_BEYOND_EDGE | O.RISE_EDGE
+        assert a["order"].shape[0] == pop.count[h]                   # all bound, as designed
+        k = 12 * n - 1
+        assert b["k_vir"] == k
+        assert b["r_vir"] == b["r"][k] and b["m_vir"] == pytest.approx(pop.m0 * (k + 1), rel=1e-12)
+        # the minimum found independently: shell densities from the designed
+        # counts and the particles' radii, by histogram over the shell edges
+        r = np.sort(b["r"])
+        edges = np.concatenate([[0.0], r[n - 1::n]])
+        cnt, _ = np.histogram(r, bins=edges)
+        rho = cnt * pop.m0 / (4.0 / 3.0 * np.pi * np.diff(edges ** 3))
+        assert int(np.argmin(rho[8:])) + 8 == 11 and rho[12] > rho[11] < rho[10]
+        # the rest of the result is the method's
+        for f in ("removed_iter", "order", "phi"):
+            np.testing.assert_array_equal(a[f], b[f])
+
+
+def test_rise_edge_leaves_other_haloes_alone():
+    # a falling profile has no rise; a halo with a virial crossing keeps it;
+    # fewer than 64 members never take the variant
+    fall = synth.shell_profile_batch(rise=False)
+    a = O.unbind_population(fall, O.Params())
+    b = O.unbind_population(fall, O.Params(rise_edge=True))
+    for h in range(fall.n_halos):
+        assert a[h]["status"] == b[h]["status"] == O.RVIR_BEYOND_EDGE
+        assert (a[h]["k_vir"], a[h]["r_vir"], a[h]["m_vir"]) == (b[h]["k_vir"], b[h]["r_vir"], b[h]["m_vir"])
+    pop = synth.halo_batch(seed=95, n_halos=10, n_lo=300, n_hi=20_000)
+    a = O.unbind_population(pop, O.Params())
+    b = O.unbind_population(pop, O.Params(rise_edge=True))
+    for h in range(pop.n_halos):
+        if not a[h]["status"] & O.RVIR_BEYOND_EDGE:
+            assert (a[h]["k_vir"], a[h]["r_vir"], a[h]["status"]) == (b[h]["k_vir"], b[h]["r_vir"], b[h]["status"])
+    r = np.linspace(1.0, 2.0, 63)
+    assert O.rise_edge(r, np.ones(63)) is None
+
+
+def test_rise_edge_uses_shell_masses():
+    # a shallow minimum: relative shell densities ... 1.08, 1.00, 1.05 ... at
+    # shells 9, 10, 11; the edge is the end of shell 10 (the enclosed mass
+    # over a shell's volume would put it at shell 9)
+    rel = [2.0 ** (9 - s) * 1.08 for s in range(9)] + [1.08, 1.0, 1.05, 1.2, 1.4, 1.6, 1.8]
+    pop = synth.shell_profile_batch(seed=77, n_shells=(400,), rho_shells=rel, sigma_v=0.0)
+    o = O.unbind_population(pop, O.Params(rise_edge=True))[0]
+    assert o["status"] & O.RISE_EDGE and o["k_vir"] == 11 * 400 - 1
