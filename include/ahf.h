@@ -61,6 +61,8 @@ extern "C" {
 #define AHF_HALO_EMPTY            2  /* no member left                        */
 #define AHF_HALO_RVIR_BEYOND_EDGE 4  /* mean density above delta_rho at the outermost member */
 #define AHF_HALO_RVIR_NONE        8  /* mean density never reaches delta_rho  */
+#define AHF_HALO_RISE_EDGE       16  /* extent at the rise of the density
+                                        profile (AHF_VAR_RISE_EDGE)           */
 
 /* ---- coordinate encodings (ahf_particles.coord_type) -------------------- */
 #define AHF_COORD_F64     0  /* double x,y,z,vx,vy,vz,m; any frame           */
@@ -102,9 +104,20 @@ typedef struct ahf_params {
  *   only as missing from the bound list).  The call then reads the first
  *   pass's records back to the host (it synchronises `stream` once).
  *   ahf_unbind_batch, ahf_unbind_profile_batch and ahf_unbind_batch_host
- *   only. */
+ *   only.
+ * AHF_VAR_RISE_EDGE: a halo whose mean overdensity never drops below
+ *   delta_rho inside its bound set (AHF_HALO_RVIR_BEYOND_EDGE) ends at the rise
+ *   of its density profile (Sect. 2.1, the truncation of subhaloes): the bound
+ *   set, sorted by radius, is cut into 16 shells of equal particle count; among
+ *   the outer 8 shells the first of least density (shell mass over the volume
+ *   between the radii of the last particles of the shell and of the one
+ *   before) is the edge when a denser shell lies beyond it.  k_vir is then the
+ *   shell's last particle, r_vir its radius, m_vir the mass up to it, and the
+ *   status gains AHF_HALO_RISE_EDGE.  Bound sets of fewer than 64 particles
+ *   are left as they are.  The profile rows use that r_vir. */
 #define AHF_VAR_VBULK_INITIAL 1
 #define AHF_VAR_RETRUNCATE    2
+#define AHF_VAR_RISE_EDGE     4
 
 typedef struct ahf_particles {
   /* Structure-of-arrays particle store, n entries each.  Element type is

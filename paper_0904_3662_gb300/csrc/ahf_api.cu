@@ -292,7 +292,7 @@ int validate(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, con
   if (prm->max_iter < 1) return fail(AHF_ERR_INVALID, "max_iter must be >= 1");
   if (prm->precision != AHF_PREC_MIXED && prm->precision != AHF_PREC_FP64)
     return fail(AHF_ERR_INVALID, "unknown precision mode %d", prm->precision);
-  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE))
+  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE | AHF_VAR_RISE_EDGE))
     return fail(AHF_ERR_INVALID, "unknown variant bits %d", prm->variant);
   if (prm->reserved != 0) return fail(AHF_ERR_INVALID, "params.reserved must be 0");
   if (!(prm->G > 0.0) || !std::isfinite(prm->G)) return fail(AHF_ERR_INVALID, "G must be > 0");
@@ -416,6 +416,7 @@ ParamsDev to_dev(const ahf_params* prm) {
   d.max_iter = prm->max_iter;
   d.precision = prm->precision;
   d.vbulk_initial = (prm->variant & AHF_VAR_VBULK_INITIAL) ? 1 : 0;
+  d.rise_edge = (prm->variant & AHF_VAR_RISE_EDGE) ? 1 : 0;
   return d;
 }
 

@@ -185,6 +185,43 @@ __device__ __forceinline__ double virial_radius(double m, double inv_crit) {
   return x * (z * z);
 }
 
+// Edge of a halo whose mean overdensity never drops below the threshold: the
+// rise of its density profile (Sect. 2.1, the truncation of subhaloes).  The
+// n bound particles, in radial order, form 16 shells of equal count (shell s
+// ends with particle (s+1) n / 16 - 1); among the outer 8 shells the first of
+// least density (shell mass over the volume between the radii of the last
+// particles of the shell and of the one before, in FP64) is the edge when a
+// denser shell lies beyond it.  at(k, r, m) gives particle k's radius and the
+// mass up to and including it.  Returns the edge particle's index, or -1.
+constexpr int RISE_SHELLS = 16;
+constexpr int RISE_MIN_N = 64;
+template <typename At>
+__device__ long long rise_edge_index(long long n, At at) {
+  if (n < RISE_MIN_N) return -1;
+  double r_lo, m_lo;
+  at((RISE_SHELLS / 2) * n / RISE_SHELLS - 1, r_lo, m_lo);
+  double rho_min = 0.0;
+  long long k_min = -1;
+  bool rise = false;
+  for (int s = RISE_SHELLS / 2; s < RISE_SHELLS; ++s) {
+    const long long hi = (long long)(s + 1) * n / RISE_SHELLS - 1;
+    double r_hi, m_hi;
+    at(hi, r_hi, m_hi);
+    const double vol = (4.0 * M_PI / 3.0) * (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo);
+    const double rho = vol > 0.0 ? (m_hi - m_lo) / vol : INFINITY;
+    if (k_min < 0 || rho < rho_min) {
+      rho_min = rho;
+      k_min = hi;
+      rise = false;
+    } else if (rho > rho_min) {
+      rise = true;
+    }
+    r_lo = r_hi;
+    m_lo = m_hi;
+  }
+  return rise ? k_min : -1;
+}
+
 // m < crit r^3 (the mean density inside r above the threshold fails), in float
 // (mf: m rounded) except within 1e-5 of equality, where it is decided in FP64.
 __device__ __forceinline__ bool below_threshold(double m, float mf, float r, float crit_f, double crit) {

@@ -819,6 +819,18 @@ __global__ void g_result(GridLaunch L) {
       Rs.k_vir = kk;
       Rs.m_vir = mk;
       Rs.r_vir = virial_radius(mk, L.prm.inv_crit);
+      if (L.prm.rise_edge && kk == nb - 1) {
+        auto at = [&](long long k, double& r, double& m) {
+          r = sizeof(Real) == 4 ? float_to_double((float)rc[H.gbase + k]) : (double)rc[H.gbase + k];
+          m = unim ? double_from_fix(k + 1, 0) * L.p.m0 : double_from_fix(L.mc[H.gbase + k], S.s_m);
+        };
+        const long long ke = rise_edge_index(nb, at);
+        if (ke >= 0) {
+          at(ke, Rs.r_vir, Rs.m_vir);
+          Rs.k_vir = ke;
+          status |= AHF_HALO_RISE_EDGE;
+        }
+      }
     }
     const double mt = double_from_fix(S.m_tot, S.s_m);
     for (int a = 0; a < 3; ++a) Rs.vbulk[a] = quotient(double_from_fix(S.mv[a], S.s_mv), mt);

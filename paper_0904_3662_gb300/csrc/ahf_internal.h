@@ -54,6 +54,7 @@ struct ParamsDev {
   int max_iter;
   int precision;
   int vbulk_initial;   // AHF_VAR_VBULK_INITIAL: v_bulk of the initial set throughout
+  int rise_edge;       // AHF_VAR_RISE_EDGE: extent at the rise of the density profile
 };
 
 struct OutputsDev {

@@ -828,6 +828,29 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
               kv = k;
               mv = mk;
               rv = virial_radius(mk, P.inv_crit);
+              if (P.rise_edge && k == nb - 1) {
+                // bound position p of the cluster: rank q holds [pre_q, pre_q + nb_loc_q)
+                auto at = [&](long long p, double& r, double& m) {
+                  int q = 0;
+                  long long pre = 0;
+                  if constexpr (CS > 1) {
+                    for (; q < CS - 1; ++q) {
+                      const long long nl = Cl<CS>::at(&X, q)->nb_loc;
+                      if (p < pre + nl) break;
+                      pre += nl;
+                    }
+                  }
+                  const int l = sw((int)(p - pre), mask);
+                  r = float_to_double(Cl<CS>::at(rc, q)[l]);
+                  m = unim ? double_from_fix(p + 1, 0) * L.p.m0 : double_from_fix(Cl<CS>::at(mc, q)[l], s_m);
+                };
+                const long long ke = rise_edge_index(nb, at);
+                if (ke >= 0) {
+                  at(ke, rv, mv);
+                  kv = ke;
+                  status |= AHF_HALO_RISE_EDGE;
+                }
+              }
             }
           }
           R->n_bound = nb;

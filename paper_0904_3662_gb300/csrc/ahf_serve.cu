@@ -284,7 +284,7 @@ int check_params(const ahf_params* prm) {
   if (prm->max_iter < 1) return set_last_error_fmt(AHF_ERR_INVALID, "max_iter < 1");
   if (prm->precision != AHF_PREC_MIXED && prm->precision != AHF_PREC_FP64)
     return set_last_error_fmt(AHF_ERR_INVALID, "unknown precision %d", prm->precision);
-  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE))
+  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RETRUNCATE | AHF_VAR_RISE_EDGE))
     return set_last_error_fmt(AHF_ERR_INVALID, "unknown variant bits %d", prm->variant);
   if (prm->reserved != 0) return set_last_error_fmt(AHF_ERR_INVALID, "params.reserved must be 0");
   return AHF_OK;

@@ -75,8 +75,8 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   if (prm->max_iter < 1) return fail_static(AHF_ERR_INVALID, "max_iter must be >= 1");
   if (prm->precision != AHF_PREC_MIXED) return fail_static(AHF_ERR_INVALID, "only AHF_PREC_MIXED");
   if (p->u_th) return fail_static(AHF_ERR_INVALID, "no gas thermal energies (u_th) here");
-  if (prm->variant & ~AHF_VAR_VBULK_INITIAL)
-    return fail_static(AHF_ERR_INVALID, "only the AHF_VAR_VBULK_INITIAL variant");
+  if (prm->variant & ~(AHF_VAR_VBULK_INITIAL | AHF_VAR_RISE_EDGE))
+    return fail_static(AHF_ERR_INVALID, "only the AHF_VAR_VBULK_INITIAL and AHF_VAR_RISE_EDGE variants");
   if (prm->reserved != 0) return fail_static(AHF_ERR_INVALID, "params.reserved must be 0");
   if (!(prm->G > 0.0) || !std::isfinite(prm->G) || !std::isfinite(prm->H) || !(prm->delta_rho > 0.0) ||
       !std::isfinite(prm->delta_rho) || !(prm->r_soft >= 0.0) || !std::isfinite(prm->r_soft) ||
@@ -166,6 +166,7 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
   L.prm.max_iter = prm->max_iter;
   L.prm.precision = prm->precision;
   L.prm.vbulk_initial = (prm->variant & AHF_VAR_VBULK_INITIAL) ? 1 : 0;
+  L.prm.rise_edge = (prm->variant & AHF_VAR_RISE_EDGE) ? 1 : 0;
   L.out.res = out; L.out.bound_idx = (long long*)bound_idx; L.out.phi = phi; L.out.removed_iter = removed_iter;
   L.out.member_idx = (const long long*)member_idx; L.out.n_slots = n_slots; L.out.err = counters + 8;
   L.rows.prof = nullptr; L.rows.factor = nullptr; L.rows.factor_f = nullptr; L.rows.n_bins = 0;

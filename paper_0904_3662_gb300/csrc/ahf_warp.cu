@@ -387,6 +387,18 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
           kv = kf;
           mvir = mk;
           r_vir_l = virial_radius(mk, P.inv_crit);
+          if (P.rise_edge && kf == nb - 1) {
+            auto at = [&](long long k, double& r, double& m) {
+              r = float_to_double(rc[sw((int)k, mask)]);
+              m = unim ? double_from_fix(k + 1, 0) * L.p.m0 : double_from_fix(mc[sw((int)k, mask)], s_m);
+            };
+            const long long ke = rise_edge_index(nb, at);
+            if (ke >= 0) {
+              at(ke, r_vir_l, mvir);
+              kv = ke;
+              status |= AHF_HALO_RISE_EDGE;
+            }
+          }
         }
       }
       ahf_result* R = L.out.res + H.index;

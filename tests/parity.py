@@ -34,7 +34,7 @@ def _positions(ref_idx, idx):
 def oracle_params(p):
     return O.Params(G=p.G, H=p.H, delta_rho=p.delta_rho, r_soft=p.r_soft, box=p.box,
                     max_iter=p.max_iter, band=p.band, vbulk_initial=bool(p.variant & 1),
-                    retruncate=bool(p.variant & 2))
+                    retruncate=bool(p.variant & 2), rise_edge=bool(p.variant & 4))
 
 
 def compare(pop, params, res, bound_idx, phi, removed_iter, halos=None, member_idx=None,

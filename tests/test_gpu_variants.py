@@ -1,5 +1,6 @@
 """Method variants on the GPU against the oracle: the bulk velocity fixed
-from the initial set (every class) and the second pass within r_vir."""
+from the initial set (every class), the second pass within r_vir, the
+subhalo edge at the rise of the density profile, gas thermal energy."""
 import numpy as np
 import pytest
 
@@ -75,7 +76,7 @@ def test_variant_arguments_checked():
         run_gpu(pop, params=_prm(pop, ahf.VAR_RETRUNCATE), plain=True)
     assert e.value.code == ahf.ERR_INVALID
     with pytest.raises(ahf.AHFError):
-        run_gpu(pop, params=_prm(pop, 4))                       # unknown bit
+        run_gpu(pop, params=_prm(pop, 8))                       # unknown bit
 
 
 @pytest.mark.parametrize("coord_type,precision", [(synth.COORD_F32_REL, 0), (synth.COORD_F64, 1)])
@@ -101,3 +102,36 @@ def test_gas_thermal_energy(coord_type, precision):
     hp = ahf.Particles(pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz, None, pop.m0, pop.coord_type, pop.u_th)
     h = ctx.unbind_batch_host(hp, ahf.halos_from_population(pop), prm)
     assert h["res"].tobytes() == out["res"].tobytes()
+
+
+@pytest.mark.parametrize("onchip_max", [None, 0])
+def test_rise_edge_every_class(onchip_max):
+    # designed profiles of 400, 1,600 and 20,000 particles (warp, one CTA,
+    # 2-CTA cluster; or all in the multi-CTA class) end at the last particle
+    # of shell 11; a falling profile keeps its edge; records, bound lists and
+    # profile rows against the oracle
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    for rise in (True, False):
+        pop = synth.shell_profile_batch(rise=rise)
+        ctx = ahf.Context(0)
+        ctx.set_option(ahf.OPT_PROMOTE, 0)
+        if onchip_max is not None:
+            ctx.set_option(ahf.OPT_ONCHIP_MAX, onchip_max)
+        prm = _prm(pop, ahf.VAR_RISE_EDGE)
+        out, prm, _, _ = run_gpu(pop, params=prm, ctx=ctx)
+        compare(pop, prm, out["res"], out["bound_idx"], out["phi"], out["removed_iter"])
+        res = out["res"]
+        for h in range(pop.n_halos):
+            n = int(pop.count[h]) // 16
+            if rise:
+                assert res[h]["status"] == ahf.HALO_RVIR_BEYOND_EDGE | ahf.HALO_RISE_EDGE
+                assert res[h]["k_vir"] == 12 * n - 1
+            else:
+                assert res[h]["status"] == ahf.HALO_RVIR_BEYOND_EDGE
+        parts = ahf.particles_from_population(pop)
+        p2 = ctx.unbind_profile_batch(parts, ahf.halos_from_population(pop), prm, n_bins=16, r_min_frac=0.05)
+        torch.cuda.synchronize()
+        r2 = ahf.results_to_numpy(p2["res"])
+        assert r2.tobytes() == res.tobytes()
+        check_profiles(pop, prm, r2, p2["prof"].cpu().numpy(), 16, 0.05)
