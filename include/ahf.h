@@ -349,7 +349,7 @@ int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
  * Limits: n_halos <= AHF_STATIC_MAX_HALOS and every halo's count <=
  * AHF_STATIC_MAX_COUNT; larger requests return AHF_ERR_INVALID before any
  * work is enqueued.  Only AHF_PREC_MIXED, no gas (u_th), and of the
- * variants only AHF_VAR_VBULK_INITIAL.
+ * variants only AHF_VAR_VBULK_INITIAL and AHF_VAR_RISE_EDGE.
  *
  * Scratch: the halo descriptors and work counters live in one fixed array
  * in device memory (about 3.8 MiB) that every GPU loading the library holds
