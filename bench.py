@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ahf", "reference"], default="ahf")
-    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep", "serve"], default="batch")
+    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep", "serve", "latency"], default="batch")
     ap.add_argument("--requests", type=int, default=50_000, help="serve workload: requests per rate")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000",
                     help="serve workload: Poisson arrival rates (requests/s)")
@@ -680,12 +680,59 @@ def run_serve(args):
     return 0
 
 
+def run_latency(args):
+    """Latency of one call for small batches, each size class as small as
+    possible (AHF_OPT_PROMOTE off) and with latency promotion (on): median
+    CUDA-event time of back-to-back calls with graph replay."""
+    import torch
+    from paper_0904_3662_gb300 import ahf, synth
+    cases = [("one NFW halo, 11,000 candidates (float64)", synth.single_halo(seed=synth.SEED_BASE + 1))]
+    for n_lo, n_hi, nh in ((200, 400, 1), (4000, 6000, 1), (1500, 2500, 8), (20000, 30000, 2), (100, 100_000, 20),
+                           (100, 100_000, 100), (100, 100_000, 400)):
+        cases.append((f"{nh} haloes, N_p on [{n_lo}, {n_hi}]", synth.halo_batch(seed=11 + nh + n_lo, n_halos=nh,
+                                                                           n_lo=n_lo, n_hi=n_hi)))
+    rows = []
+    for desc, pop in cases:
+        r = {"batch": desc, "haloes": pop.n_halos, "candidates": int(pop.count.sum())}
+        for promote in (0, 1):
+            ctx = ahf.Context(0)
+            ctx.set_option(ahf.OPT_PROMOTE, promote)
+            ctx.set_option(ahf.OPT_GRAPHS, 1)
+            parts = ahf.particles_from_population(pop)
+            hal = ahf.halos_from_population(pop)
+            prm = ahf.params_for(pop)
+            out = ctx.alloc_outputs(len(hal), pop.n_particles)
+            prof = torch.empty((len(hal), N_BINS, 4), dtype=torch.float64, device="cuda")
+            for _ in range(max(3, args.warmup)):
+                ctx.unbind_profile_batch(parts, hal, prm, n_bins=N_BINS, r_min_frac=R_MIN_FRAC, out=out, prof=prof)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.unbind_profile_batch(parts, hal, prm, n_bins=N_BINS, r_min_frac=R_MIN_FRAC, out=out, prof=prof)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3)
+            st = ctx.stats()["phase_halos"][:len(ahf.VARIANT_CAPS)]
+            key = "promoted" if promote else "smallest_class"
+            r[key + "_us"] = float(np.median(ts))
+            r[key + "_classes"] = {ahf.PHASE_NAMES[k]: int(n) for k, n in enumerate(st) if n}
+        rows.append(r)
+        log(f"{desc}: {r['smallest_class_us']:.1f} us -> {r['promoted_us']:.1f} us")
+    print(json.dumps({"metric": "call latency", "unit": "us", "higher_is_better": False, "data": "synthetic",
+                      "steps": args.steps, "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "latency":
+        return run_latency(args)
     return run_ahf(args)
 
 
