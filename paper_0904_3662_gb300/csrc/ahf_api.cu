@@ -580,7 +580,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
-  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 256 + (prof ? 36 * (size_t)n_bins + 512 : 0) +
+  const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 1024 + (prof ? 36 * (size_t)n_bins + 512 : 0) +
                           (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
@@ -598,14 +598,28 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     po += bytes;
     return e;
   };
-  AHF_CUDA(stage(hd, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos));
-  AHF_CUDA(cudaMemsetAsync(queues, 0, 16 * sizeof(int), s));
-  if (prof) {
-    std::vector<double> tab(3 * (size_t)n_bins);
-    profile_bin_tables(n_bins, r_min_frac, tab.data());
-    AHF_CUDA(stage(dfac, tab.data(), sizeof(double) * tab.size()));
-    std::vector<float> tabf(tab.begin(), tab.end());
-    AHF_CUDA(stage(dfacf, tabf.data(), sizeof(float) * tabf.size()));
+  {
+    // descriptors, zeroed queue counters and the bin tables sit back to back
+    // in the workspace: one copy of the same image from pinned memory
+    char* d0 = reinterpret_cast<char*>(hd);
+    const size_t qo = (size_t)(reinterpret_cast<char*>(queues) - d0);
+    size_t span = qo + 16 * sizeof(int);
+    std::memcpy(pin, P.hd.data(), sizeof(HaloDev) * (size_t)n_halos);
+    std::memset(pin + sizeof(HaloDev) * (size_t)n_halos, 0, span - sizeof(HaloDev) * (size_t)n_halos);
+    if (prof) {
+      std::vector<double> tab(3 * (size_t)n_bins);
+      profile_bin_tables(n_bins, r_min_frac, tab.data());
+      const size_t fo = (size_t)(reinterpret_cast<char*>(dfac) - d0);
+      const size_t ffo = (size_t)(reinterpret_cast<char*>(dfacf) - d0);
+      std::memset(pin + span, 0, fo - span);
+      std::memcpy(pin + fo, tab.data(), sizeof(double) * tab.size());
+      std::memset(pin + fo + sizeof(double) * tab.size(), 0, ffo - fo - sizeof(double) * tab.size());
+      float* tf = reinterpret_cast<float*>(pin + ffo);
+      for (size_t k = 0; k < tab.size(); ++k) tf[k] = (float)tab[k];
+      span = ffo + sizeof(float) * tab.size();
+    }
+    AHF_CUDA(cudaMemcpyAsync(d0, pin, span, cudaMemcpyHostToDevice, s));
+    po = span;
   }
 
   OutputsDev O;
