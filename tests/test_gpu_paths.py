@@ -450,3 +450,34 @@ def test_promotion_same_bits(case):
         np.testing.assert_array_equal(prom["phi"][lo:lo + nb], base["phi"][lo:lo + nb])
     with pytest.raises(ahf.AHFError):
         ctx.set_option(ahf.OPT_PROMOTE, 3)
+
+
+@pytest.mark.parametrize("n_bins", [1, 7, 129, 300])
+def test_profile_bin_counts(n_bins):
+    # one bin, an odd count, and counts above the clusters' fused limit (128:
+    # their rows then come from the standalone profile kernel); the bin
+    # tables travel in the same staged copy as the halo descriptors
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=43, n_halos=40, n_lo=100, n_hi=60_000)
+    ctx = ahf.Context(0)
+    parts = ahf.particles_from_population(pop)
+    hal = ahf.halos_from_population(pop)
+    prm = ahf.params_for(pop)
+    fused = ctx.unbind_profile_batch(parts, hal, prm, n_bins=n_bins, r_min_frac=0.02)
+    sep = ctx.profile_batch(parts, hal, prm, fused["res"], fused["bound_idx"], n_bins=n_bins, r_min_frac=0.02)
+    torch.cuda.synchronize()
+    a = fused["prof"].cpu().numpy()
+    b = sep.cpu().numpy()
+    assert a.shape == (pop.n_halos, n_bins, 4)
+    np.testing.assert_array_equal(a[:, :, 0], b[:, :, 0])
+    np.testing.assert_allclose(a[:, :, 1], b[:, :, 1], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(a[:, :, 2:], b[:, :, 2:], rtol=1e-6, atol=0)
+    res = ahf.results_to_numpy(fused["res"])
+    compare(pop, prm, res, fused["bound_idx"].cpu().numpy(), fused["phi"].cpu().numpy(),
+            fused["removed_iter"].cpu().numpy())
+    _check_profiles(pop, prm, res, a, n_bins, 0.02)
+    # the host-buffer entry stages the same tables
+    hparts = ahf.Particles(pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz, pop.m, pop.m0, pop.coord_type)
+    host = ctx.unbind_batch_host(hparts, hal, prm, n_bins=n_bins, r_min_frac=0.02)
+    np.testing.assert_array_equal(host["prof"], a)
