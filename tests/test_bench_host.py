@@ -1,0 +1,95 @@
+"""CPU: the benchmark's host logic (clock samples, the committed DRAM traffic
+keyed by kernel source, the peak file, algorithmic bytes per phase)."""
+import json
+import os
+import shutil
+import types
+
+import numpy as np
+
+import bench
+
+
+def test_clock_summary_median_and_reasons():
+    s = bench.ClockSampler(0)
+    s.lines = [
+        "0, 2070, 2070, 812.4, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1375.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2040, 2070, 1201.9, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    out = s.summary()
+    assert out["sm_mhz"] == 2040.0
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["samples"] == 3
+    s.lines = ["0, 1500, 2070, 900, 0x8, Active, Not Active, Active, Not Active"]
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.lines = []
+    assert s.summary() is None
+
+
+def _tree(tmp_path):
+    """A copy of the kernel sources the traffic entries are keyed on."""
+    for files in bench.PHASE_SOURCES.values():
+        for f in files:
+            dst = tmp_path / f
+            dst.parent.mkdir(parents=True, exist_ok=True)
+            shutil.copyfile(os.path.join(bench.ROOT, f), dst)
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+
+
+def test_measured_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    _tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic(7, "batch") is None            # no summary at all
+    entry = {"kernel": "cluster16_128k", "dram_bytes_per_launch": 1234.0, "launches": 3,
+             "source_hash": bench.source_hash(bench.PHASE_SOURCES[7])}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"batch:7": entry}))
+    assert bench.measured_traffic(7, "batch") == 1234.0
+    assert bench.measured_traffic(0, "batch") is None            # no entry for that phase
+    assert bench.measured_traffic(7, "sweep") is None            # nor for that workload
+    # an edit of a kernel source the entry was measured on voids it
+    with open(tmp_path / bench.PHASE_SOURCES[7][0], "a") as f:
+        f.write("\n// edited\n")
+    assert bench.measured_traffic(7, "batch") is None
+
+
+def test_source_hash_depends_on_every_file(tmp_path, monkeypatch):
+    _tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    files = bench.PHASE_SOURCES[0]
+    h0 = bench.source_hash(files)
+    assert h0 == bench.source_hash(list(files))
+    with open(tmp_path / files[-1], "a") as f:
+        f.write(" ")
+    assert bench.source_hash(files) != h0
+
+
+def test_peaks_measured_else_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7012.5}))
+    assert bench.peaks() == (7012.5, "measured")
+
+
+def test_phase_bytes_of_a_small_batch():
+    # two on-chip haloes (warp class, 8k class) and one multi-CTA halo;
+    # float32 coordinates with per-particle masses: 7 x 4 B per candidate
+    pop = types.SimpleNamespace(coord_type=1, m=np.ones(1), count=np.array([300, 6000, 200_000]))
+    res = {"n_bound": np.array([250, 5000, 150_000]), "n_member": np.array([280, 5600, 180_000]),
+           "part_iter": np.array([560, 16_800, 720_000])}
+    cls = np.array([0, 3, 8])
+    out = bench.phase_bytes(pop, res, cls)
+    assert out.shape == (12,)
+    assert out[0] == 28 * 300 + 12 * 250 + 88
+    assert out[3] == 28 * 6000 + 12 * 5000 + 88
+    assert out[1] == out[2] == out[4] == out[5] == out[6] == out[7] == 0
+    assert out[8] == 28 * 200_000 + 24 * 180_000
+    assert out[9] == 20 * 720_000
+    assert out[10] == 20 * 180_000 + 12 * 150_000 + 88
+    assert out[11] == (16 + 8) * (250 + 5000 + 150_000) + 32 * bench.N_BINS * 3
+    # float64 coordinates, uniform mass: 6 x 8 B per candidate
+    pop64 = types.SimpleNamespace(coord_type=0, m=None, count=pop.count)
+    assert bench.phase_bytes(pop64, res, cls)[0] == 48 * 300 + 12 * 250 + 88
