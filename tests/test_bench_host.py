@@ -1,5 +1,6 @@
 """CPU: the benchmark's host logic (clock samples, the committed DRAM traffic
-keyed by kernel source, the peak file, algorithmic bytes per phase)."""
+keyed by kernel source, the peak file, algorithmic bytes per phase) and the
+summary of a per-halo trace."""
 import json
 import os
 import shutil
@@ -93,3 +94,28 @@ def test_phase_bytes_of_a_small_batch():
     # float64 coordinates, uniform mass: 6 x 8 B per candidate
     pop64 = types.SimpleNamespace(coord_type=0, m=None, count=pop.count)
     assert bench.phase_bytes(pop64, res, cls)[0] == 48 * 300 + 12 * 250 + 88
+
+
+def test_trace_summary_of_a_synthetic_trace():
+    from paper_0904_3662_gb300 import ahf, trace_report
+    # rows: start, gathered, sorted, filled, iterated, done (ns), SM, variant + 256 * iterations
+    t = np.array([
+        [1000, 2000, 4000, 5000, 9000, 11000, 3, 0 + 256 * 2],     # warp class, 2 iterations
+        [3000, 3500, 6500, 7000, 12000, 15000, 4, 0 + 256 * 4],    # warp class, 4 iterations
+        [500, 1500, 3500, 4500, 8500, 10500, 7, 7 + 256 * 6],      # 16-CTA cluster
+        [0, 0, 0, 0, 0, 0, 0, 0],                                  # not an on-chip halo: left out
+    ], dtype=np.int64)
+    s = trace_report.summarize(t)
+    assert s["haloes"] == 3
+    assert s["span_us"] == (15000 - 500) / 1e3
+    w = s["variants"][ahf.PHASE_NAMES[0]]
+    assert w["haloes"] == 2 and w["iterations_mean"] == 3.0
+    assert w["first_start_us"] == 0.5 and w["last_end_us"] == 14.5
+    assert w["gather_us_mean"] == 0.75 and w["sort_us_mean"] == 2.5 and w["fill_us_mean"] == 0.75
+    assert w["iterate_us_mean"] == 4.5 and w["emit_us_mean"] == 2.5
+    assert w["halo_us_mean"] == 11.0 and w["halo_us_max"] == 12.0
+    c = s["variants"][ahf.PHASE_NAMES[7]]
+    assert c["haloes"] == 1 and c["iterations_mean"] == 6.0 and c["first_start_us"] == 0.0
+    tab = trace_report.table(s).splitlines()
+    assert len(tab) == 2 + 2 and tab[2].startswith(f"| {ahf.PHASE_NAMES[0]} | 2 | 3.0 |")
+    assert trace_report.summarize(np.zeros((4, 8), dtype=np.int64)) == {"haloes": 0}
