@@ -240,13 +240,16 @@ def halo_batch(seed=SEED_BASE + 2, n_halos=2000, n_lo=100, n_hi=100_000,
 
 
 def large_tail(seed=SEED_BASE + 3, n_halos=64, n_lo=1_000_000, n_hi=10_000_000,
-               n_sub=20, sub_frac=0.005, box=5e5, host_sigma_v=300.0):
+               n_sub=20, sub_frac=0.005, box=5e5, host_sigma_v=300.0, counts=None):
     """Massive hosts in a periodic box: N_p ~ N_p^-1.9 on [n_lo, n_hi], each with
     n_sub NFW subhaloes of sub_frac of the host's particles placed at radii drawn
     from the host profile inside R_200 with N(0, 300 km/s) bulk offsets.
-    Float32 box coordinates (wrapped into [0, box))."""
+    Float32 box coordinates (wrapped into [0, box)).  `counts` (one particle
+    count per host) replaces the power-law draw when given."""
     rng = np.random.default_rng(seed)
-    counts = powerlaw_counts(rng, n_halos, n_lo, n_hi)
+    drawn = powerlaw_counts(rng, n_halos, n_lo, n_hi)
+    counts = drawn if counts is None else np.asarray(counts, dtype=np.int64)
+    n_halos = int(counts.shape[0])
     conc = np.exp(rng.normal(math.log(10.0), 0.25, n_halos))
     offset = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
     n = int(counts.sum())

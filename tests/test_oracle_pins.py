@@ -384,3 +384,27 @@ def test_radius_order_matters():
     b = O.potential_sorted(r, np.array([1.0, 10.0]), 1.0)
     np.testing.assert_allclose(a, [-(10.0 + 0.5), -(10.0 / 2 + 0.5)])
     np.testing.assert_allclose(b, [-(1.0 + 5.0), -(1.0 / 2 + 5.0)])
+
+
+def test_profile_two_bins_hand_worked():
+    # Six particles at r = 1, 2, 3, 4, 5, 8 with masses 1..6, G = 1,
+    # r_out = 8, two bins from f = 1/4: edges e_0 = 8 (1/4)^1 = 2,
+    # e_1 = 8 (1/4)^(1/2) = 4, e_2 = 8.  Bin 0 = (2, 4] holds r = 3, 4
+    # (r = 2 sits on e_0 and stays out): count 2, shell mass 3 + 4 = 7,
+    # M(<= 4) = 1 + 2 + 3 + 4 = 10, density 7 / (4 pi / 3 (4^3 - 2^3))
+    # = 21 / (224 pi), v_c = sqrt(10 / 4).  Bin 1 = (4, 8] holds r = 5, 8:
+    # count 2, shell mass 11, M(<= 8) = 21, density 11 / (4 pi / 3 (8^3 - 4^3))
+    # = 33 / (1792 pi), v_c = sqrt(21 / 8).
+    r = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 8.0])
+    m = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0])
+    want = np.array([[2.0, 10.0, 0.029841551829730376, 1.5811388300841898],
+                     [2.0, 21.0, 0.005861733395125609, 1.620185174601965]])
+    np.testing.assert_allclose(O.profile(r, m, 8.0, 2, 0.25, 1.0), want, rtol=1e-14)
+    # r_vir = 0: the outermost particle (8) is r_out, the same rows
+    np.testing.assert_allclose(O.profile(r, m, 0.0, 2, 0.25, 1.0), want, rtol=1e-14)
+    # r_vir = 4: edges 1, 2, 4; bin 0 = (1, 2] holds r = 2 (mass 2), M(<= 2) = 3,
+    # density 2 / (4 pi / 3 (2^3 - 1)) = 3 / (14 pi), v_c = sqrt(3 / 2);
+    # bin 1 = (2, 4] as above with G M / r = 10 / 4
+    want4 = np.array([[1.0, 3.0, 0.06820926132509800, 1.2247448713915890],
+                      [2.0, 10.0, 0.029841551829730376, 1.5811388300841898]])
+    np.testing.assert_allclose(O.profile(r, m, 4.0, 2, 0.25, 1.0), want4, rtol=1e-14)

@@ -138,3 +138,27 @@ def test_rise_edge_mutant_is_caught(name, func, old, new, monkeypatch):
         except Exception:
             failed.append(pin.__name__)
     assert failed, f"mutant {name} passed every pin"
+
+
+PROFILE_MUTANTS = [
+    ("profile_volume_inner_edge_twice", "profile", "(hi ** 3 - lo ** 3)", "(lo ** 3 - lo ** 3 / 8.0)"),
+    ("profile_volume_outer_only", "profile", "(hi ** 3 - lo ** 3)", "(hi ** 3)"),
+    ("profile_closed_lower_edge", "profile", "(r_sorted > lo) & (r_sorted <= hi)", "(r_sorted >= lo) & (r_sorted <= hi)"),
+    ("profile_vc_inner_edge", "profile", "math.sqrt(G * mass_in / hi)", "math.sqrt(G * mass_in / lo)"),
+    ("profile_exclusive_mass", "profile", "m_sorted[r_sorted <= hi].sum()", "m_sorted[r_sorted < hi].sum()"),
+]
+
+PROFILE_PINS = [pins.test_profile_two_bins_hand_worked, pins.test_profile_counts_and_mass]
+
+
+@pytest.mark.parametrize("name,func,old,new", PROFILE_MUTANTS, ids=[m[0] for m in PROFILE_MUTANTS])
+def test_profile_mutant_is_caught(name, func, old, new, monkeypatch):
+    mod = _mutant_module(func, old, new, monkeypatch)
+    monkeypatch.setattr(pins, "O", mod)
+    failed = []
+    for pin in PROFILE_PINS:
+        try:
+            pin()
+        except Exception:
+            failed.append(pin.__name__)
+    assert failed, f"mutant {name} passed every pin"
