@@ -208,6 +208,12 @@ def traced_classes(ctx, step, pop):
     return np.where(t[:, 0] > 0, t[:, 7] & 255, len(ahf.VARIANT_CAPS))
 
 
+def es_grid(pop):
+    """Bytes of a real in the multi-CTA class's streams (float in the mixed mode
+    the bench runs)."""
+    return 4
+
+
 def phase_bytes(pop, res, cls):
     """Algorithmic HBM bytes of each phase for one step."""
     es = 8 if pop.coord_type == 0 else 4
@@ -224,9 +230,14 @@ def phase_bytes(pop, res, cls):
         # read the candidates once, write bound list + phi + the record
         out[v] = in_b * cand[s].sum() + 12.0 * nb[s].sum() + 88.0 * s.sum()
     g = cls == nv
-    out[nv] = in_b * cand[g].sum() + 24.0 * nm[g].sum()            # inputs in, sorted SoA out
-    out[nv + 1] = 20.0 * pit[g].sum()                               # (w, m) + r per particle-iteration
-    out[nv + 2] = 20.0 * nm[g].sum() + 12.0 * nb[g].sum() + 88.0 * g.sum()
+    # multi-CTA class: the radial-order stream holds (w, r) per member, w the
+    # velocity plus the Hubble flow (4 reals), and the mass when masses differ
+    stream = 4 * es_grid(pop) + (es_grid(pop) if pop.m is not None else 0)
+    out[nv] = in_b * cand[g].sum() + stream * nm[g].sum()          # inputs in once, radial stream out once
+    out[nv + 1] = stream * pit[g].sum()                             # the stream read once per particle-iteration
+    # the stream read once more; bound list, phi, record, profile rows out
+    out[nv + 2] = (stream * nm[g].sum() + (8.0 + es_grid(pop)) * nb[g].sum() + 88.0 * g.sum()
+                   + 32.0 * N_BINS * g.sum())
     pos_b = 3 * es + (es if pop.m is not None else 0)
     out[nv + 3] = (pos_b + 8.0) * nb.sum() + 32.0 * N_BINS * len(nb)  # gather bound particles, write rows
     return out

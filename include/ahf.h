@@ -50,7 +50,7 @@ extern "C" {
 #define AHF_PENDING       1
 #define AHF_ERR_INVALID   (-1)   /* bad argument, size or layout           */
 #define AHF_ERR_NOMEM     (-2)   /* device allocation failed / above a cap */
-#define AHF_ERR_TIMEOUT   (-3)   /* a bounded device wait gave up          */
+/* (-3 is not used: no kernel of the library waits for another CTA)         */
 #define AHF_ERR_CUDA      (-4)   /* a CUDA runtime call failed             */
 #define AHF_ERR_FULL      (-5)   /* serving queue full                     */
 #define AHF_ERR_NOT_FOUND (-6)   /* unknown request id                     */
@@ -189,8 +189,8 @@ int ahf_destroy(ahf_ctx *ctx);
  * Slots of a halo beyond offset + n_bound are left unspecified in bound_idx
  * and phi.  Errors: AHF_ERR_INVALID (NULL pointers, negative sizes, n_halos
  * of 2^27 or more, slots out of range or shared, bad coord_type/precision/
- * max_iter), AHF_ERR_NOMEM,
- * AHF_ERR_CUDA, AHF_ERR_TIMEOUT.  Outputs are undefined after an error. */
+ * max_iter), AHF_ERR_NOMEM, AHF_ERR_CUDA.  Outputs are undefined after an
+ * error. */
 int ahf_unbind_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
                      int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
                      ahf_result *out, int64_t *bound_idx, void *phi,
@@ -235,8 +235,10 @@ int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halo
 
 /* Wait for the context's enqueued work and report problems the device
  * found while running it: AHF_ERR_INVALID for an out-of-range member index
- * or a halo routed to a class it did not fit, AHF_ERR_TIMEOUT when a bounded
- * device wait gave up.  The device error word is cleared by the call. */
+ * or a halo routed to a class it did not fit.  The device error word is
+ * cleared by the call.  No kernel waits for another CTA (the multi-CTA
+ * class's look-back reads only sums an earlier kernel finished), so there is
+ * no device-side timeout. */
 int ahf_sync(ahf_ctx *ctx);
 
 /* ahf_unbind_batch and ahf_profile_batch in one call: the same arguments
@@ -256,8 +258,6 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *   AHF_OPT_ONCHIP_MAX   largest candidate count handled in shared memory (by one
  *                        CTA or one thread-block cluster); larger haloes take the
  *                        multi-CTA class (default and maximum 131072)
- *   AHF_OPT_WAIT_LIMIT   spin iterations a bounded device wait may take before
- *                        it reports AHF_ERR_TIMEOUT (0 = give up at once)
  *   AHF_OPT_TIMING       1 = record CUDA events around every phase of the
  *                        following calls (read with ahf_get_stats), 0 = off
  *   AHF_OPT_GRAPHS       1 = a batch whose haloes all take the on-chip classes
@@ -288,7 +288,7 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        radial order.  Pageable buffers are always staged.
  * Errors: AHF_ERR_INVALID (unknown option or value). */
 #define AHF_OPT_ONCHIP_MAX 1
-#define AHF_OPT_WAIT_LIMIT 2
+/* (option 2 is not used) */
 #define AHF_OPT_TIMING     3
 #define AHF_OPT_HOST_DIRECT 4
 #define AHF_OPT_GRAPHS     5

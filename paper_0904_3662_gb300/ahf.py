@@ -19,13 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libahfgpu.so")
 
 # status / codes (values from include/ahf.h)
 OK, PENDING = 0, 1
-ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2, -3, -4, -5, -6
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2, -4, -5, -6
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 HALO_RISE_EDGE = 16
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
 VAR_VBULK_INITIAL, VAR_RETRUNCATE, VAR_RISE_EDGE = 1, 2, 4
-OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE, OPT_SERIAL = 1, 2, 3, 4, 5, 6, 7
+OPT_ONCHIP_MAX, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE, OPT_SERIAL = 1, 3, 4, 5, 6, 7
 OPT_PROMOTE = 8
 TRACE_FIELDS = 8
 N_PHASES = 12

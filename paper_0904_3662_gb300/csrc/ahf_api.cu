@@ -122,7 +122,6 @@ struct ahf_ctx {
   cudaEvent_t last = nullptr;    // end of the previous call's device work
   bool last_valid = false;
   int64_t onchip_max = 16 * 8192;    // largest candidate count of the shared-memory classes
-  int64_t wait_limit = 1 << 22;
   std::mutex mu;
   // pinned staging for host descriptors: a ring of slots, each released by
   // an event after the copies that read it, so a call never waits for the
@@ -161,6 +160,7 @@ struct ahf_ctx {
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[NV] = {};
   int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
+  int iter_grid[2] = {-1, -1};       // CTAs of the multi-CTA pass (mixed, FP64; -1: not queried)
 };
 
 namespace {
@@ -441,28 +441,103 @@ int end_call(ahf_ctx* c, cudaStream_t s) {
   return AHF_OK;
 }
 
-// Sort, fill, iterate (convergence read back on the host) and finish the
-// multi-CTA class; phases 3 (to the end of fill), 4 and 5.
-int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
+// Sizes of the multi-CTA class's workspace for one call.
+struct GridSizes {
+  size_t nf = 0;       // flat candidate slots
+  int n_tiles = 0;
+  int max_halo_tiles = 0;
+  int n_grid = 0;      // haloes
+  int n_big = 0;       // haloes of more than 256 tiles
+  bool fp64 = false;
+  bool masses = false; // per-particle masses
+  bool gas = false;
+};
+
+// The class's arrays, in one fixed order (sizing pass with G == NULL).
+void grid_take(Bump& B, GridLaunch* G, const GridSizes& z) {
+  const size_t es = z.fp64 ? 8 : 4;          // real
+  const size_t v4 = 4 * es;                  // (w, r) or (v, m)
+  const size_t as = z.fp64 ? 16 : 8;         // exact sum
+  GridHaloState* st = B.take<GridHaloState>((size_t)z.n_grid);
+  GridCtl* ctl = B.take<GridCtl>(1);
+  char* rec = B.take<char>(z.nf * 2 * v4);
+  char* ka = B.take<char>(z.nf * es);
+  char* kb = B.take<char>(z.nf * es);
+  uint32_t* va = B.take<uint32_t>(z.nf);
+  uint32_t* vb = B.take<uint32_t>(z.nf);
+  char* wr = B.take<char>(z.nf * v4);
+  char* ms = B.take<char>(z.masses ? z.nf * es : 0);
+  char* uth = B.take<char>(z.gas ? z.nf * es : 0);
+  uint32_t* vx = B.take<uint32_t>(z.nf);
+  char* mc = B.take<char>(z.nf * as);
+  char* rcp = B.take<char>(z.nf * es);
+  int2* trg = B.take<int2>((size_t)z.n_tiles);
+  int* th = B.take<int>((size_t)z.n_tiles);
+  int* ht0 = B.take<int>((size_t)z.n_grid + 1);
+  int* big = B.take<int>((size_t)std::max(1, z.n_big));
+  uint32_t* hist = B.take<uint32_t>((size_t)z.n_tiles * 256);
+  uint32_t* dbase = B.take<uint32_t>((size_t)z.n_grid * 256);
+  const size_t n_sub = (size_t)z.n_tiles * (GRID_TILE / GRID_SUB);
+  char* agm = B.take<char>(2 * n_sub * as);
+  char* agr = B.take<char>(2 * n_sub * as);
+  int* agc = B.take<int>(2 * n_sub);
+  char* prm_ = B.take<char>((size_t)z.n_tiles * as);
+  char* prr = B.take<char>((size_t)z.n_tiles * as);
+  long long* prc = B.take<long long>((size_t)z.n_tiles);
+  int4* work = B.take<int4>(2 * n_sub);
+  AccSlot* tmv = B.take<AccSlot>(3 * (size_t)z.n_tiles);
+  if (!G) return;
+  G->state = st; G->ctl = ctl; G->rec = rec; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb;
+  G->wr = wr; G->ms = z.masses ? ms : nullptr; G->uth = z.gas ? uth : nullptr; G->val_x = vx; G->mc = mc;
+  G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0; G->big_halos = big;
+  G->n_big = z.n_big; G->tile_hist = hist; G->digit_base = dbase;
+  G->agg_m = agm; G->agg_r = agr; G->agg_c = agc; G->pre_m = prm_; G->pre_r = prr; G->pre_c = prc;
+  G->work = work;
+  G->tile_mv = tmv; G->max_halo_tiles = z.max_halo_tiles; G->n_halos = z.n_grid; G->n_flat = (long long)z.nf; G->n_tiles = z.n_tiles;
+  G->fp64 = z.fp64 ? 1 : 0;
+}
+
+// Per-call device resets of the class's control words and halo states
+// (before grid_prepare).
+int grid_reset(const GridLaunch& G, cudaStream_t s) {
+  AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState) * (size_t)G.n_halos, s));
+  AHF_CUDA(cudaMemsetAsync(G.ctl, 0, sizeof(GridCtl), s));
+  AHF_CUDA(cudaMemsetAsync(&G.ctl->key_and, 0xff, sizeof(unsigned long long), s));
+  return AHF_OK;
+}
+
+// Resident CTAs of the persistent pass on the context's device.
+int grid_pass_ctas(ahf_ctx* c, bool fp64) {
+  int& g = c->iter_grid[fp64 ? 1 : 0];
+  if (g < 0) g = std::max(1, grid_iter_grid(c->device, fp64 ? 1 : 0));
+  return g;
+}
+
+// Sort, iterate and finish the multi-CTA class (phases 8 to the end of the
+// sort, 9 and 10).  The passes go out `chunk` at a time; the host reads the
+// count of still-active haloes once per chunk (a pass with nothing left to
+// do returns at once).
+int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s, int chunk) {
   int rc;
-  AHF_CUDA(cudaMemcpyAsync(c->flag_host, G.key_or_and, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  AHF_CUDA(cudaMemcpyAsync(c->flag_host, &G.ctl->key_or, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   AHF_CUDA(cudaStreamSynchronize(s));
   c->stats.host_syncs += 1;
   unsigned long long orb, andb;
   std::memcpy(&orb, c->flag_host, 8);
   std::memcpy(&andb, c->flag_host + 2, 8);
   AHF_CUDA(grid_sort(G, s, orb, andb));
-  c->stats.launches += 4 * G.sort_passes;
-  AHF_CUDA(grid_fill(G, s));
-  c->stats.launches += 1;
+  c->stats.launches += (4 + (G.n_big ? 1 : 0)) * G.sort_passes + (G.sort_passes ? 0 : 1) + 2;
   if ((rc = phase_end(c, PH_GRID_SORT, s))) return rc;
   if ((rc = phase_begin(c, PH_GRID_ITER, s, G.n_halos, G.n_flat))) return rc;
-  for (int it = 1; it <= prm->max_iter; ++it) {
-    AHF_CUDA(cudaMemsetAsync(G.any_active, 0, sizeof(int), s));
-    AHF_CUDA(grid_iterate(G, it, s));
-    c->stats.launches += 4;
-    c->stats.grid_iterations += 1;
-    AHF_CUDA(cudaMemcpyAsync(c->flag_host + 4, G.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+  for (int pass = 1; pass <= prm->max_iter;) {
+    const int n = std::min(chunk, prm->max_iter - pass + 1);
+    for (int i = 0; i < n; ++i) {
+      AHF_CUDA(grid_iterate(G, pass++, s));
+      c->stats.launches += 2;
+      c->stats.grid_iterations += 1;
+    }
+    if (pass > prm->max_iter) break;
+    AHF_CUDA(cudaMemcpyAsync(c->flag_host + 4, &G.ctl->work_n[pass & 1], sizeof(int), cudaMemcpyDeviceToHost, s));
     AHF_CUDA(cudaStreamSynchronize(s));
     c->stats.host_syncs += 1;
     if (c->flag_host[4] == 0) break;
@@ -470,7 +545,7 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s) {
   if ((rc = phase_end(c, PH_GRID_ITER, s))) return rc;
   if ((rc = phase_begin(c, PH_GRID_FINISH, s, G.n_halos, G.n_flat))) return rc;
   AHF_CUDA(grid_finish(G, s));
-  c->stats.launches += 5;
+  c->stats.launches += 3 + (G.rows.prof ? 1 : 0);
   return phase_end(c, PH_GRID_FINISH, s);
 }
 
@@ -478,11 +553,13 @@ struct GridTables {
   std::vector<int2> tile_range;
   std::vector<int> tile_halo;
   std::vector<int> halo_tile0;
+  std::vector<int> big;        // haloes of more than 256 tiles
 };
 
 void build_tiles(const Plan& P, int first, int n, GridTables& T) {
   T.tile_range.clear();
   T.tile_halo.clear();
+  T.big.clear();
   T.halo_tile0.assign((size_t)n + 1, 0);
   for (int k = 0; k < n; ++k) {
     const HaloDev& d = P.hd[(size_t)first + k];
@@ -492,6 +569,7 @@ void build_tiles(const Plan& P, int first, int n, GridTables& T) {
       T.tile_range.push_back(make_int2((int)(d.gbase + o), (int)len));
       T.tile_halo.push_back(k);
     }
+    if ((int)T.tile_range.size() - T.halo_tile0[k] > 256) T.big.push_back(k);
   }
   T.halo_tile0[n] = (int)T.tile_range.size();
 }
@@ -536,6 +614,11 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   const int n_tiles = (int)T.tile_range.size();
   const size_t nf = (size_t)P.grid_flat;
   const bool fp64 = prm->precision == AHF_PREC_FP64;
+  GridSizes gz;
+  gz.nf = nf; gz.n_tiles = n_tiles; gz.n_grid = n_grid; gz.n_big = (int)T.big.size(); gz.fp64 = fp64;
+  for (int k = 0; k < n_grid; ++k)
+    gz.max_halo_tiles = std::max(gz.max_halo_tiles, T.halo_tile0[(size_t)k + 1] - T.halo_tile0[(size_t)k]);
+  gz.masses = p->m != nullptr; gz.gas = p->u_th != nullptr;
 
   // workspace layout (must match the Bump sequence below)
   double* dfac = nullptr;
@@ -548,40 +631,16 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     float* facf = B.take<float>(prof ? 3 * (size_t)n_bins : 0);
     float4* rec = B.take<float4>(2 * (size_t)P.onchip_flat);
     if (G) { dfac = fac; dfacf = facf; drec = P.onchip_flat ? rec : nullptr; }
-    if (G) { G->halos = hd + n_onchip; G->any_active = queues + 8; G->key_or_and = (unsigned long long*)(queues + 10); }
-    if (n_grid) {
-      const size_t es = fp64 ? 8 : 4;
-      GridHaloState* st = B.take<GridHaloState>((size_t)n_grid);
-      char* ka = B.take<char>(nf * es);
-      char* kb = B.take<char>(nf * es);
-      uint32_t* va = B.take<uint32_t>(nf);
-      uint32_t* vb = B.take<uint32_t>(nf);
-      char* wm = B.take<char>(nf * 4 * es);
-      char* r = B.take<char>(nf * es);
-      char* uth = B.take<char>(p->u_th ? nf * es : 0);
-      long long* mc = B.take<long long>(nf);
-      char* rcp = B.take<char>(nf * es);
-      int2* trg = B.take<int2>((size_t)n_tiles);
-      int* th = B.take<int>((size_t)n_tiles);
-      int* ht0 = B.take<int>((size_t)n_grid + 1);
-      uint32_t* hist = B.take<uint32_t>((size_t)n_tiles * 256);
-      uint32_t* dbase = B.take<uint32_t>((size_t)n_grid * 256);
-      long long* agg = B.take<long long>((size_t)n_tiles * 3);
-      long long* pre = B.take<long long>((size_t)n_tiles * 3);
-      if (G) {
-        G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
-        G->uth = p->u_th ? uth : nullptr;
-        G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
-        G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
-      }
-    }
+    if (G) G->halos = hd + n_onchip;
+    if (n_grid) grid_take(B, G, gz);
     return hd;
   };
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
   const size_t pin_need = sizeof(HaloDev) * (size_t)n_halos + 1024 + (prof ? 36 * (size_t)n_bins + 512 : 0) +
-                          (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256;
+                          (sizeof(int2) + sizeof(int)) * (size_t)n_tiles + 256 + sizeof(int) * ((size_t)n_grid + 1) + 256 +
+                          sizeof(int) * T.big.size() + 256;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
   GridLaunch G{};
@@ -638,12 +697,15 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     AHF_CUDA(stage(G.tile_range, T.tile_range.data(), sizeof(int2) * (size_t)n_tiles));
     AHF_CUDA(stage(G.tile_halo, T.tile_halo.data(), sizeof(int) * (size_t)n_tiles));
     AHF_CUDA(stage(G.halo_tile0, T.halo_tile0.data(), sizeof(int) * ((size_t)n_grid + 1)));
-    AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState) * (size_t)n_grid, s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(unsigned long long), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(unsigned long long), s));
-    G.fp64 = fp64 ? 1 : 0;
+    AHF_CUDA(stage(G.big_halos, T.big.data(), sizeof(int) * T.big.size()));
+    if ((rc = grid_reset(G, s))) return rc;
     G.p = pd; G.frame = P.frame; G.prm = prd; G.out = O;
-    G.n_halos = n_grid; G.n_flat = (long long)nf; G.n_tiles = n_tiles;
+    G.iter_grid = grid_pass_ctas(c, fp64);
+    // profile rows of this class from its final pass
+    G.rows.prof = prof;
+    G.rows.factor = dfac;
+    G.rows.factor_f = dfacf;
+    G.rows.n_bins = n_bins;
     if ((rc = phase_begin(c, PH_GRID_SORT, s, n_grid, (long long)nf))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
@@ -766,7 +828,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   } else {
     if ((rc = enqueue_onchip(s, false))) return rc;
     if (n_grid) {
-      if ((rc = run_grid(c, G, prm, s))) return rc;
+      if ((rc = run_grid(c, G, prm, s, 8))) return rc;
     }
     if (!c->serial)
       for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
@@ -779,7 +841,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     int64_t first = 0;
     for (int v = 0; v <= NV; ++v) {
       for (int k = 0; k < P.n_class[v]; ++k)
-        if (v > FUSED_MAX) { rest[(size_t)P.hd[(size_t)(first + k)].index] = 1; any = true; }
+        if (v > FUSED_MAX && v < NV) { rest[(size_t)P.hd[(size_t)(first + k)].index] = 1; any = true; }
       first += P.n_class[v];
     }
     if (any) return profile_impl(c, p, halos, n_halos, member_idx, prm, out, bound_idx, n_bins, r_min_frac, prof, s,
@@ -919,48 +981,29 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
   for (const HaloDev& d : P.hd) maxc = std::max(maxc, d.count);
   const size_t nf = (size_t)maxc;
   const int max_tiles = (int)((maxc + GRID_TILE - 1) / GRID_TILE);
+  GridSizes gz;
+  gz.nf = nf; gz.n_tiles = max_tiles; gz.n_grid = 1; gz.n_big = max_tiles > 256 ? 1 : 0;
+  gz.max_halo_tiles = max_tiles;
+  gz.fp64 = prm->precision == AHF_PREC_FP64; gz.masses = p->m != nullptr; gz.gas = p->u_th != nullptr;
   auto layout = [&](Bump& B, GridLaunch* G) {
     HaloDev* hd = B.take<HaloDev>(1);
-    int* words = B.take<int>(16);
-    const size_t es = prm->precision == AHF_PREC_FP64 ? 8 : 4;
-    GridHaloState* st = B.take<GridHaloState>(1);
-    char* ka = B.take<char>(nf * es);
-    char* kb = B.take<char>(nf * es);
-    uint32_t* va = B.take<uint32_t>(nf);
-    uint32_t* vb = B.take<uint32_t>(nf);
-    char* wm = B.take<char>(nf * 4 * es);
-    char* r = B.take<char>(nf * es);
-    char* uth = B.take<char>(p->u_th ? nf * es : 0);
-    long long* mc = B.take<long long>(nf);
-    char* rcp = B.take<char>(nf * es);
-    int2* trg = B.take<int2>((size_t)max_tiles);
-    int* th = B.take<int>((size_t)max_tiles);
-    int* ht0 = B.take<int>(2);
-    uint32_t* hist = B.take<uint32_t>((size_t)max_tiles * 256);
-    uint32_t* dbase = B.take<uint32_t>(256);
-    long long* agg = B.take<long long>((size_t)max_tiles * 3);
-    long long* pre = B.take<long long>((size_t)max_tiles * 3);
-    if (G) {
-      G->halos = hd; G->any_active = words + 8; G->key_or_and = (unsigned long long*)(words + 10);
-      G->state = st; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb; G->wm = wm; G->r = r;
-      G->uth = p->u_th ? uth : nullptr;
-      G->mc = mc; G->rc = rcp; G->tile_range = trg; G->tile_halo = th; G->halo_tile0 = ht0;
-      G->tile_hist = hist; G->digit_base = dbase; G->tile_agg = agg; G->tile_pre = pre;
-    }
+    if (G) G->halos = hd;
+    grid_take(B, G, gz);
   };
   Bump sizing{nullptr, 0, 0};
   layout(sizing, nullptr);
   if ((rc = ensure_workspace(c, sizing.used + 4096))) return rc;
-  const size_t pin_need = sizeof(HaloDev) + (sizeof(int2) + sizeof(int)) * (size_t)max_tiles + 1024;
+  const size_t pin_need = sizeof(HaloDev) + (sizeof(int2) + sizeof(int)) * (size_t)max_tiles + 2048;
   if ((rc = begin_call(c, s))) return rc;
   Bump B{c->ws, 0, c->ws_bytes};
   GridLaunch G{};
   layout(B, &G);
   OutputsDev O;
+  std::memset(&O, 0, sizeof O);
   O.res = out; O.bound_idx = (long long*)bound_idx; O.phi = phi; O.removed_iter = removed_iter;
   O.member_idx = (const long long*)member_idx; O.n_slots = n_slots; O.err = c->err_dev;
-  G.p = to_dev(p); G.frame = P.frame; G.prm = to_dev(prm); G.out = O; G.n_halos = 1;
-  G.fp64 = prm->precision == AHF_PREC_FP64 ? 1 : 0;
+  G.p = to_dev(p); G.frame = P.frame; G.prm = to_dev(prm); G.out = O;
+  G.iter_grid = grid_pass_ctas(c, gz.fp64);
   reset_stats(c);
   for (const HaloDev& d0 : P.hd) {
     HaloDev d = d0;
@@ -973,8 +1016,10 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
       th.push_back(0);
     }
     const int ht0[2] = {0, (int)tr.size()};
+    const int big0 = 0;
     G.n_tiles = (int)tr.size();
     G.n_flat = d.count;
+    G.n_big = G.n_tiles > 256 ? 1 : 0;
     char* pin = nullptr;
     if ((rc = pin_acquire(c, pin_need, &pin))) return rc;
     size_t po = 0;
@@ -990,10 +1035,9 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     AHF_CUDA(stage(G.tile_range, tr.data(), sizeof(int2) * tr.size()));
     AHF_CUDA(stage(G.tile_halo, th.data(), sizeof(int) * th.size()));
     AHF_CUDA(stage(G.halo_tile0, ht0, sizeof(ht0)));
+    AHF_CUDA(stage(G.big_halos, &big0, sizeof(int)));
     if ((rc = pin_release(c, s))) return rc;
-    AHF_CUDA(cudaMemsetAsync(G.state, 0, sizeof(GridHaloState), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and, 0, sizeof(unsigned long long), s));
-    AHF_CUDA(cudaMemsetAsync(G.key_or_and + 1, 0xff, sizeof(unsigned long long), s));
+    if ((rc = grid_reset(G, s))) return rc;
     if (G.n_tiles == 0) {
       // no candidates: an empty record
       ahf_result R{};
@@ -1006,7 +1050,8 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
     if ((rc = phase_begin(c, PH_GRID_SORT, s, 1, d.count))) return rc;
     AHF_CUDA(grid_prepare(G, s));
     c->stats.launches += 2;
-    if ((rc = run_grid(c, G, prm, s))) return rc;
+    // the plain form reads the change flag after every pass
+    if ((rc = run_grid(c, G, prm, s, 1))) return rc;
   }
   return end_call(c, s);
 }
@@ -1495,10 +1540,6 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value < 0 || value > variant_capacity(NV - 1)) return fail(AHF_ERR_INVALID, "onchip max out of range");
       c->onchip_max = value;
       return AHF_OK;
-    case AHF_OPT_WAIT_LIMIT:
-      if (value < 0) return fail(AHF_ERR_INVALID, "wait limit < 0");
-      c->wait_limit = value;
-      return AHF_OK;
     case AHF_OPT_TIMING:
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "timing is 0 or 1");
       c->timing = value == 1;
@@ -1532,7 +1573,6 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
   if (!c || !value) return fail(AHF_ERR_INVALID, "NULL argument");
   switch (option) {
     case AHF_OPT_ONCHIP_MAX: *value = c->onchip_max; return AHF_OK;
-    case AHF_OPT_WAIT_LIMIT: *value = c->wait_limit; return AHF_OK;
     case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
     case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
@@ -1551,7 +1591,6 @@ int ahf_sync(ahf_ctx* c) {
   AHF_CUDA(cudaMemcpy(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
   const int e = *c->err_host;
   if (e) AHF_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
-  if (e & ERR_TIMEOUT) return fail(AHF_ERR_TIMEOUT, "a bounded device wait gave up");
   if (e & ERR_BAD_INDEX) return fail(AHF_ERR_INVALID, "a member index was out of range");
   if (e & ERR_CAPACITY) return fail(AHF_ERR_INVALID, "a halo exceeded its size class");
   if (e & ERR_ID_RANGE) return fail(AHF_ERR_INVALID, "a catalogue particle id was out of range");

@@ -1,19 +1,39 @@
-// Multi-CTA class: haloes too large for one CTA's shared memory.
+// Multi-CTA class: haloes too large for one CTA's (or one cluster's) shared
+// memory, and every halo in the all-FP64 mode.
 //
 // The haloes of this class share flat arrays (halo k owns [gbase_k,
 // gbase_k + count_k)) cut into tiles of GRID_TILE elements that never cross
-// a halo.  The steps are those of the on-chip class (Sect. 2.1, Appendix A),
-// each a grid-wide kernel:
-//   prepare   recentre, sphere test, radius key, exponent maxima
-//   sort      segmented stable LSD radix sort (per pass: tile histograms,
-//             per-(halo, digit) scans over tiles, per-halo digit bases,
-//             stable tile scatter)
-//   fill      sorted SoA (w.x, w.y, w.z, m) + radius, exact sum m v
-//   iterate   tile sums -> per-halo tile scan -> phi / escape test / removal
-//             -> per-halo bookkeeping, repeated while any halo changes
-//   finish    final scan, bound list and phi, virial crossing, records
-// Every cross-tile combination goes through a separate kernel, so no CTA
-// ever waits on another one.
+// a halo.  The steps are those of the on-chip classes (Sect. 2.1, Appendix
+// A), laid out for HBM streaming:
+//   prepare  one coalesced read of the candidates: recentring, sphere test,
+//            radius key, and a 32-byte record per candidate, (w, r) and
+//            (v, m) with w = v + H d (64 bytes in the all-FP64 mode)
+//   sort     segmented stable LSD radix sort of (key, position) with 8-bit
+//            digits (tile histograms, per-(halo, digit) scans over tiles,
+//            digit bases, a scatter ranked by warp ballots and staged in
+//            shared memory so that each digit's run is written contiguously);
+//            the last pass gathers each member's record once and writes the
+//            radial-order stream (w, r) (+ m), so no later step touches the
+//            particle store
+//   init     exact sums of the initial set per tile and per halo, v_bulk
+//   passes   ONE streaming kernel per iteration: each tile takes the exact
+//            prefix sums M(<r) and sum m/r of the tiles before it from the
+//            tile prefixes of the current set, evaluates phi (Appendix A),
+//            the escape test and the removals, and subtracts what it removed
+//            from its own sums; the last tile of a halo to finish turns the
+//            tiles' sums into the prefixes of the set left, the halo's
+//            totals, v_bulk and its convergence
+//   final    bound lists, phi, compacted radii and inclusive masses, the
+//            first virial crossing, the records, and the profile rows by
+//            binary search over the compacted radii
+//
+// No CTA ever waits for another one: a tile reads only prefixes that an
+// earlier kernel finished, and each halo's bookkeeping is done by whichever
+// of its tiles finishes last (an atomic count).
+
+// Exact sums: long long fixed point in the mixed mode (the same scales and
+// bits as the on-chip classes), __int128 in the all-FP64 mode, where a
+// 64-bit quantum would limit large haloes to ~1e-11 relative in sum m/r.
 #include <cstdint>
 
 #include "ahf_device.cuh"
@@ -28,7 +48,7 @@ constexpr int NWARP = T / 32;
 
 // Precision of the per-particle arithmetic.  float: the mixed mode (FP32
 // radius key, FP32 phi and escape test).  double: the all-FP64 mode (FP64
-// offsets, radius key, phi and escape test); sums stay exact fixed point.
+// offsets, radius key, phi and escape test).
 struct alignas(32) D4 {
   double x, y, z, w;
 };
@@ -38,33 +58,202 @@ template <>
 struct Prec<float> {
   using Key = uint32_t;
   using V4 = float4;
-  static constexpr int KEY_BYTES = 4;
+  using Acc = long long;
+  static constexpr int ACC_BITS = 61;   // partial sums stay below 2^62
 };
 template <>
 struct Prec<double> {
   using Key = unsigned long long;
   using V4 = D4;
-  static constexpr int KEY_BYTES = 8;
+  using Acc = __int128;
+  static constexpr int ACC_BITS = 125;  // partial sums stay below 2^126
 };
+
+// ---- exact sums ---------------------------------------------------------------------
+
+template <typename Acc>
+__device__ __forceinline__ Acc& A(AccSlot& s) {
+  return *reinterpret_cast<Acc*>(s.w);
+}
+template <typename Acc>
+__device__ __forceinline__ Acc Ald(const AccSlot& s) {
+  return *reinterpret_cast<const Acc*>(s.w);
+}
+// an AccSlot another CTA of the running kernel wrote (read through L2)
+template <typename Acc>
+__device__ __forceinline__ Acc Acg(const AccSlot& s);
+template <>
+__device__ __forceinline__ long long Acg<long long>(const AccSlot& s) {
+  return __ldcg(&s.w[0]);
+}
+template <>
+__device__ __forceinline__ __int128 Acg<__int128>(const AccSlot& s) {
+  const unsigned long long lo = (unsigned long long)__ldcg(&s.w[0]);
+  const unsigned long long hi = (unsigned long long)__ldcg(&s.w[1]);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+
+// Scale exponent s for sums of n terms of magnitude < 2^(emax+1) (the mixed
+// mode's is fix_scale's).
+template <typename R>
+__device__ __forceinline__ int acc_scale(int emax, long long n) {
+  int bits = 0;
+  while (bits < 40 && (1ll << bits) < n) ++bits;
+  return Prec<R>::ACC_BITS - bits - emax;
+}
+
+// round(x 2^s) for the all-FP64 mode (round half away from zero); the caller
+// guarantees |x| 2^s < 2^126.
+__device__ __forceinline__ __int128 fix128_from_double(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = e - 1075 + s;
+  __int128 v;
+  if (sh >= 0) v = (__int128)mant << (sh > 73 ? 73 : sh);
+  else if (sh > -54) v = (__int128)(((mant >> (-sh - 1)) + 1) >> 1);
+  else v = 0;
+  return (b >> 63) ? -v : v;
+}
+
+// v 2^-s as the nearest double (ties to even).
+__device__ __forceinline__ double double_from_fix128(__int128 v, int s) {
+  if (v == 0) return 0.0;
+  const bool negv = v < 0;
+  const unsigned __int128 a = negv ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long m;
+  if (msb <= 52) {
+    m = lo << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    m = (unsigned long long)(a >> sh);
+    const unsigned __int128 rem = a & (((unsigned __int128)1 << sh) - 1);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 53)) {
+        m >>= 1;
+        ++msb;
+      }
+    }
+  }
+  // 2^msb (1 + frac): exact, msb <= 127
+  const double d = __longlong_as_double((long long)(((unsigned long long)(msb + 1023) << 52) | (m & ((1ull << 52) - 1ull))));
+  return scale_pow2d(negv ? -d : d, -s);
+}
+
+__device__ __forceinline__ long long fixr(float x, int s) { return fix_from_float(x, s); }
+// round(x 2^s) for x >= 0 (the terms m and m/r): fix_from_float's value, with
+// the round half up done as one add before the shift
+__device__ __forceinline__ long long fixp(float x, int s) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)(b >> 23);
+  if (e == 0) return 0;
+  const int sh = e - 150 + s;
+  const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
+  if (sh >= 0) return (long long)((unsigned long long)mant << (sh > 39 ? 39 : sh));
+  const int rs = -sh;
+  return rs > 24 ? 0ll : (long long)((mant + (1u << (rs - 1))) >> rs);
+}
+__device__ __forceinline__ __int128 fixp(double x, int s) { return fix128_from_double(x, s); }
+__device__ __forceinline__ __int128 fixr(double x, int s) { return fix128_from_double(x, s); }
+__device__ __forceinline__ float from_fix(long long v, int s, float) { return float_from_fix(v, s); }
+__device__ __forceinline__ double from_fix(__int128 v, int s, double) { return double_from_fix128(v, s); }
+__device__ __forceinline__ double dfix(long long v, int s) { return double_from_fix(v, s); }
+__device__ __forceinline__ double dfix(__int128 v, int s) { return double_from_fix128(v, s); }
+
+__device__ __forceinline__ uint32_t shfl_up_x(uint32_t x, int o) { return __shfl_up_sync(FULL_MASK, x, o); }
+__device__ __forceinline__ int shfl_xor_x(int x, int o) { return __shfl_xor_sync(FULL_MASK, x, o); }
+__device__ __forceinline__ long long shfl_up_x(long long x, int o) { return __shfl_up_sync(FULL_MASK, x, o); }
+__device__ __forceinline__ __int128 shfl_up_x(__int128 x, int o) {
+  const unsigned long long lo = __shfl_up_sync(FULL_MASK, (unsigned long long)x, o);
+  const unsigned long long hi = __shfl_up_sync(FULL_MASK, (unsigned long long)((unsigned __int128)x >> 64), o);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+__device__ __forceinline__ long long shfl_xor_x(long long x, int o) { return __shfl_xor_sync(FULL_MASK, x, o); }
+__device__ __forceinline__ __int128 shfl_xor_x(__int128 x, int o) {
+  const unsigned long long lo = __shfl_xor_sync(FULL_MASK, (unsigned long long)x, o);
+  const unsigned long long hi = __shfl_xor_sync(FULL_MASK, (unsigned long long)((unsigned __int128)x >> 64), o);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+__device__ __forceinline__ long long shfl_idx_x(long long x, int l) { return __shfl_sync(FULL_MASK, x, l); }
+__device__ __forceinline__ __int128 shfl_idx_x(__int128 x, int l) {
+  const unsigned long long lo = __shfl_sync(FULL_MASK, (unsigned long long)x, l);
+  const unsigned long long hi = __shfl_sync(FULL_MASK, (unsigned long long)((unsigned __int128)x >> 64), l);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+template <typename X>
+__device__ __forceinline__ X wsum(X x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += shfl_xor_x(x, o);
+  return x;
+}
+template <typename X>
+__device__ __forceinline__ X wscan(X x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const X y = shfl_up_x(x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Sum over the CTA of one value per thread (every thread gets the total).
+template <typename X>
+__device__ __forceinline__ X block_sum(X x, X* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = wsum(x);
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  X s = 0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) s += red[w];
+  return s;
+}
+
+// block_sum for a CTA of NT threads.
+template <typename X, int NT>
+__device__ __forceinline__ X block_sum_n(X x, X* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = wsum(x);
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  X s = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
+
+// Exclusive prefix over the CTA's threads (thread order) of one value.
+template <typename X>
+__device__ __forceinline__ X block_excl(X x, X* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const X inc = wscan(x, lane);
+  __syncthreads();
+  if (lane == 31) red[warp] = inc;
+  __syncthreads();
+  X b = 0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w)
+    if (w < warp) b += red[w];
+  return b + inc - x;
+}
+
+// ---- per-particle arithmetic ---------------------------------------------------------
 
 __device__ __forceinline__ uint32_t key_of(float r) { return __float_as_uint(r); }
 __device__ __forceinline__ unsigned long long key_of(double r) { return (unsigned long long)__double_as_longlong(r); }
-__device__ __forceinline__ float real_of(uint32_t k, float) { return __uint_as_float(k); }
-__device__ __forceinline__ double real_of(unsigned long long k, double) { return __longlong_as_double((long long)k); }
-__device__ __forceinline__ long long fix_real(float x, int s) { return fix_from_float(x, s); }
-__device__ __forceinline__ long long fix_real(double x, int s) { return fix_from_double(x, s); }
 __device__ __forceinline__ int exp_of_bits(unsigned long long b, float) { return (int)((b >> 23) & 0xff) - 127; }
 __device__ __forceinline__ int exp_of_bits(unsigned long long b, double) { return (int)((b >> 52) & 0x7ff) - 1023; }
 __device__ __forceinline__ unsigned long long abs_bits(float x) { return __float_as_uint(fabsf(x)); }
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(fabs(x));
 }
-template <typename R>
-__device__ __forceinline__ R from_fix(long long v, int s);
-template <>
-__device__ __forceinline__ float from_fix<float>(long long v, int s) { return float_from_fix(v, s); }
-template <>
-__device__ __forceinline__ double from_fix<double>(long long v, int s) { return double_from_fix(v, s); }
 __device__ __forceinline__ float rinv_real(float r, const ParamsDev& P) { return rinv_of(r, P.r_soft_f); }
 __device__ __forceinline__ double rinv_real(double r, const ParamsDev& P) {
   const double rr = fmax(r, P.r_soft);
@@ -76,8 +265,10 @@ __device__ __forceinline__ double phi_real(double M, double ri, double S, const 
 }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ bool neg(float x) { return signbit(x); }
-__device__ __forceinline__ bool neg(double x) { return signbit(x); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float neg0(float) { return -0.0f; }
+__device__ __forceinline__ double neg0(double) { return -0.0; }
 
 // All-FP64 recentring, written as the FP64 definition reads: d = x - c, then
 // the minimum image, r^2 = (dx^2 + dy^2) + dz^2, r = sqrt(r^2) (both
@@ -107,10 +298,6 @@ __device__ __forceinline__ void offset_f64(const ParticlesDev& p, long long i, c
   }
 }
 
-__device__ __forceinline__ double r2_f64(const double d[3]) {
-  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-}
-
 template <int CT>
 __device__ __forceinline__ void load_velocity_f64(const ParticlesDev& p, long long i, double v[3]) {
   if (CT == AHF_COORD_F64) {
@@ -131,92 +318,58 @@ __device__ __forceinline__ double load_mass_f64(const ParticlesDev& p, long long
   return (double)__ldg((const float*)p.m + i);
 }
 
-// Member test, radius, mass and velocity of one candidate in precision R.
-template <int CT>
-__device__ __forceinline__ bool candidate(const ParticlesDev& p, long long pi, const HaloDev& H, const FrameDev& F,
-                                          float& r, float& m, float v[3]) {
-  long long f[3];
-  float df[3];
-  offset_of<CT>(p, pi, H, df, f);
-  if (!member_of<CT>(p, pi, H, df, f)) return false;
-  r = radius_of(df);
-  m = load_mass<CT>(p, pi);
-  load_velocity<CT>(p, pi, v);
-  return true;
-}
-template <int CT>
-__device__ __forceinline__ bool candidate(const ParticlesDev& p, long long pi, const HaloDev& H, const FrameDev& F,
-                                          double& r, double& m, double v[3]) {
-  double d[3];
-  offset_f64<CT>(p, pi, H, F.box, d);
-  const double r2 = r2_f64(d);
-  if (!(r2 <= H.R2)) return false;
-  r = sqrt(r2);
-  m = load_mass_f64<CT>(p, pi);
-  load_velocity_f64<CT>(p, pi, v);
-  return true;
-}
-
-// w = v + H d of a member (the offset recomputed exactly as for its key).
-template <int CT>
-__device__ __forceinline__ void w_of(const ParticlesDev& p, long long pi, const HaloDev& H, const FrameDev& F,
-                                     const ParamsDev& P, float w[3], float v[3], float& m) {
-  long long f[3];
-  float d[3];
-  offset_of<CT>(p, pi, H, d, f);
-  load_velocity<CT>(p, pi, v);
-  m = load_mass<CT>(p, pi);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) w[a] = fmaf(P.Hf, d[a], v[a]);
-}
-template <int CT>
-__device__ __forceinline__ void w_of(const ParticlesDev& p, long long pi, const HaloDev& H, const FrameDev& F,
-                                     const ParamsDev& P, double w[3], double v[3], double& m) {
-  double d[3];
-  offset_f64<CT>(p, pi, H, F.box, d);
-  load_velocity_f64<CT>(p, pi, v);
-  m = load_mass_f64<CT>(p, pi);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) w[a] = __fma_rn(P.H, d[a], v[a]);
-}
-template <int CT>
-__device__ __forceinline__ void velocity_real(const ParticlesDev& p, long long pi, float v[3]) {
-  load_velocity<CT>(p, pi, v);
-}
-template <int CT>
-__device__ __forceinline__ void velocity_real(const ParticlesDev& p, long long pi, double v[3]) {
-  load_velocity_f64<CT>(p, pi, v);
-}
-
 // ---- prepare ---------------------------------------------------------------------
 
-template <int CT, typename R>
-__global__ void __launch_bounds__(T) g_prepare(GridLaunch L) {
-  using Key = typename Prec<R>::Key;
+// Mixed precision: the on-chip classes' float offsets (exact recentring),
+// membership and radius; the record holds w = v + H d and r, then v and m.
+template <int CT>
+__global__ void __launch_bounds__(T) g_prepare_mixed(GridLaunch L) {
   const int t = blockIdx.x;
   const int2 tr = L.tile_range[t];
   const int k = L.tile_halo[t];
   const HaloDev H = L.halos[k];
   const ParamsDev& P = L.prm;
-  Key* key_a = (Key*)L.key_a;
-  const Key NONMEMBER = ~(Key)0;
-  Key orb = 0, andb = ~(Key)0;
+  uint32_t* key_a = (uint32_t*)L.key_a;
+  float4* rec = (float4*)L.rec;
+  Cand<CT> c[IPT];
+  bool ok[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int e = q * T + threadIdx.x;
+    ok[q] = e < tr.y;
+    if (ok[q]) {
+      const long long slot = H.offset + ((long long)tr.x + e - H.gbase);
+      long long pi = slot;
+      if (L.out.member_idx) {
+        pi = L.out.member_idx[slot];
+        if (pi < 0 || pi >= L.p.n) {
+          ok[q] = false;
+          atomicOr(L.out.err, ERR_BAD_INDEX);
+        }
+      }
+      if (ok[q]) load_cand<CT>(L.p, pi, c[q]);
+    }
+  }
+  uint32_t orb = 0, andb = 0xffffffffu;
   unsigned long long mxm = 0, mxr = 0, mxv = 0;
   int nmem = 0;
-  for (int e = threadIdx.x; e < tr.y; e += T) {
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int e = q * T + threadIdx.x;
+    if (e >= tr.y) continue;
     const long long g = (long long)tr.x + e;
-    const long long i = g - H.gbase;                 // candidate position
-    const long long slot = H.offset + i;
-    long long pi = slot;
-    bool ok = true;
-    if (L.out.member_idx) {
-      pi = L.out.member_idx[slot];
-      if (pi < 0 || pi >= L.p.n) { ok = false; atomicOr(L.out.err, ERR_BAD_INDEX); }
-    }
-    Key key = NONMEMBER;
-    if (ok) {
-      R r, m, v[3];
-      if (candidate<CT>(L.p, pi, H, L.frame, r, m, v)) {
+    uint32_t key = KEY_NONMEMBER;
+    if (ok[q]) {
+      float d[3];
+      long long f[3];
+      cand_offset<CT>(c[q], H, d, f);
+      if (cand_member<CT>(c[q], H, d, f)) {
+        const float r = radius_of(d);
+        const float m = cand_mass<CT>(L.p, c[q]);
+        float v[3];
+        cand_velocity<CT>(c[q], v);
+        rec[2 * g] = make_float4(fmaf(P.Hf, d[0], v[0]), fmaf(P.Hf, d[1], v[1]), fmaf(P.Hf, d[2], v[2]), r);
+        rec[2 * g + 1] = make_float4(v[0], v[1], v[2], m);
         key = key_of(r);
         mxm = max(mxm, abs_bits(m));
         mxr = max(mxr, abs_bits(m * rinv_real(r, P)));
@@ -225,9 +378,8 @@ __global__ void __launch_bounds__(T) g_prepare(GridLaunch L) {
         ++nmem;
       }
     }
-    if (key == NONMEMBER && L.out.removed_iter) L.out.removed_iter[slot] = -1;
+    if (key == KEY_NONMEMBER && L.out.removed_iter) L.out.removed_iter[H.offset + (g - H.gbase)] = -1;
     key_a[g] = key;
-    L.val_a[g] = (uint32_t)i;
     orb |= key;
     andb &= key;
   }
@@ -241,11 +393,88 @@ __global__ void __launch_bounds__(T) g_prepare(GridLaunch L) {
   nmem = __reduce_add_sync(FULL_MASK, nmem);
   if ((threadIdx.x & 31) == 0) {
     GridHaloState* st = L.state + k;
-    atomicOr(&L.key_or_and[0], (unsigned long long)orb);
-    atomicAnd(&L.key_or_and[1], (unsigned long long)andb | (Prec<R>::KEY_BYTES == 4 ? 0xffffffff00000000ull : 0ull));
-    atomicMax(&st->mass_max_bits, mxm);
-    atomicMax(&st->mr_max_bits, mxr);
-    atomicMax(&st->mv_max_bits, mxv);
+    atomicOr(&L.ctl->key_or, (unsigned long long)orb);
+    atomicAnd(&L.ctl->key_and, (unsigned long long)andb | 0xffffffff00000000ull);
+    if (mxm) atomicMax(&st->mass_max_bits, mxm);
+    if (mxr) atomicMax(&st->mr_max_bits, mxr);
+    if (mxv) atomicMax(&st->mv_max_bits, mxv);
+    if (nmem) atomicAdd((unsigned long long*)&st->n_member, (unsigned long long)nmem);
+  }
+}
+
+// All-FP64 mode: d = x - c in FP64 (minimum image), r^2 = (dx^2 + dy^2) + dz^2.
+template <int CT>
+__global__ void __launch_bounds__(T) g_prepare_f64(GridLaunch L) {
+  const int t = blockIdx.x;
+  const int2 tr = L.tile_range[t];
+  const int k = L.tile_halo[t];
+  const HaloDev H = L.halos[k];
+  const ParamsDev& P = L.prm;
+  unsigned long long* key_a = (unsigned long long*)L.key_a;
+  D4* rec = (D4*)L.rec;
+  unsigned long long orb = 0, andb = ~0ull, mxm = 0, mxr = 0, mxv = 0;
+  int nmem = 0;
+  for (int e = threadIdx.x; e < tr.y; e += T) {
+    const long long g = (long long)tr.x + e;
+    const long long slot = H.offset + (g - H.gbase);
+    long long pi = slot;
+    bool ok = true;
+    if (L.out.member_idx) {
+      pi = L.out.member_idx[slot];
+      if (pi < 0 || pi >= L.p.n) {
+        ok = false;
+        atomicOr(L.out.err, ERR_BAD_INDEX);
+      }
+    }
+    unsigned long long key = ~0ull;
+    if (ok) {
+      double d[3];
+      offset_f64<CT>(L.p, pi, H, L.frame.box, d);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+      if (r2 <= H.R2) {
+        const double r = sqrt(r2);
+        const double m = load_mass_f64<CT>(L.p, pi);
+        double v[3];
+        load_velocity_f64<CT>(L.p, pi, v);
+        D4 a, b;
+        a.x = __fma_rn(P.H, d[0], v[0]);
+        a.y = __fma_rn(P.H, d[1], v[1]);
+        a.z = __fma_rn(P.H, d[2], v[2]);
+        a.w = r;
+        b.x = v[0];
+        b.y = v[1];
+        b.z = v[2];
+        b.w = m;
+        rec[2 * g] = a;
+        rec[2 * g + 1] = b;
+        key = key_of(r);
+        mxm = max(mxm, abs_bits(m));
+        mxr = max(mxr, abs_bits(m * rinv_real(r, P)));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) mxv = max(mxv, abs_bits(mul_rn(m, v[q])));
+        ++nmem;
+      }
+    }
+    if (key == ~0ull && L.out.removed_iter) L.out.removed_iter[slot] = -1;
+    key_a[g] = key;
+    orb |= key;
+    andb &= key;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    orb |= __shfl_xor_sync(FULL_MASK, orb, o);
+    andb &= __shfl_xor_sync(FULL_MASK, andb, o);
+    mxm = max(mxm, __shfl_xor_sync(FULL_MASK, mxm, o));
+    mxr = max(mxr, __shfl_xor_sync(FULL_MASK, mxr, o));
+    mxv = max(mxv, __shfl_xor_sync(FULL_MASK, mxv, o));
+  }
+  nmem = __reduce_add_sync(FULL_MASK, nmem);
+  if ((threadIdx.x & 31) == 0) {
+    GridHaloState* st = L.state + k;
+    atomicOr(&L.ctl->key_or, orb);
+    atomicAnd(&L.ctl->key_and, andb);
+    if (mxm) atomicMax(&st->mass_max_bits, mxm);
+    if (mxr) atomicMax(&st->mr_max_bits, mxr);
+    if (mxv) atomicMax(&st->mv_max_bits, mxv);
     if (nmem) atomicAdd((unsigned long long*)&st->n_member, (unsigned long long)nmem);
   }
 }
@@ -256,17 +485,15 @@ __global__ void g_scales(GridLaunch L) {
   if (k >= L.n_halos) return;
   GridHaloState& s = L.state[k];
   const long long n = s.n_member;
-  s.s_m = fix_scale(exp_of_bits(s.mass_max_bits, R()), n);
-  s.s_mr = fix_scale(exp_of_bits(s.mr_max_bits, R()), n);
-  s.s_mv = fix_scale(exp_of_bits(s.mv_max_bits, R()), n);
+  s.s_m = acc_scale<R>(exp_of_bits(s.mass_max_bits, R()), n);
+  s.s_mr = acc_scale<R>(exp_of_bits(s.mr_max_bits, R()), n);
+  s.s_mv = acc_scale<R>(exp_of_bits(s.mv_max_bits, R()), n);
   s.n_alive = n;
-  s.active = n > 0 ? 1 : 0;
+  s.active = 0;                          // set by the init pass
   s.n_iter = 0;
   s.status = 0;
   s.part_iter = 0;
   s.band = 0;
-  s.removed = 0;
-  s.mv[0] = s.mv[1] = s.mv[2] = 0;
   s.k_first = 0x7fffffffffffffffll;
 }
 
@@ -291,13 +518,41 @@ __global__ void __launch_bounds__(T) g_hist(const Key* __restrict__ key, const i
   tile_hist[(size_t)t0 * 256 + (size_t)threadIdx.x * th + (t - t0)] = h[threadIdx.x];
 }
 
-// One CTA per (halo, digit): exclusive prefix of the digit's counts over the
-// halo's tiles (in place) and the digit's total.
-__global__ void __launch_bounds__(256) g_digit_scan(uint32_t* __restrict__ tile_hist, const int* __restrict__ halo_tile0,
-                                                    uint32_t* __restrict__ digit_base) {
+// Haloes of at most 256 tiles: one CTA per halo, thread d runs down digit
+// d's column (exclusive prefix in place) and leaves the digit's total.
+__global__ void __launch_bounds__(256) g_digit_scan_small(uint32_t* __restrict__ tile_hist,
+                                                          const int* __restrict__ halo_tile0,
+                                                          uint32_t* __restrict__ digit_base) {
+  const int k = blockIdx.x, d = threadIdx.x;
+  const int t0 = halo_tile0[k], th = halo_tile0[k + 1] - t0;
+  if (th > 256) return;                  // g_digit_scan_big
+  uint32_t* col = tile_hist + (size_t)t0 * 256 + (size_t)d * th;
+  uint32_t run = 0;
+  int i = 0;
+  for (; i + 4 <= th; i += 4) {
+    const uint32_t a = col[i], b = col[i + 1], c = col[i + 2], e = col[i + 3];
+    col[i] = run;
+    col[i + 1] = run + a;
+    col[i + 2] = run + a + b;
+    col[i + 3] = run + a + b + c;
+    run += a + b + c + e;
+  }
+  for (; i < th; ++i) {
+    const uint32_t a = col[i];
+    col[i] = run;
+    run += a;
+  }
+  digit_base[(size_t)k * 256 + d] = run;
+}
+
+// Haloes of more than 256 tiles: one CTA per (halo, digit) scans the column
+// in chunks of 256 tiles.
+__global__ void __launch_bounds__(256) g_digit_scan_big(uint32_t* __restrict__ tile_hist,
+                                                        const int* __restrict__ halo_tile0,
+                                                        const int* __restrict__ big, uint32_t* __restrict__ digit_base) {
   __shared__ uint32_t wt[8];
   __shared__ uint32_t carry;
-  const int k = blockIdx.x >> 8, d = blockIdx.x & 255;
+  const int k = big[blockIdx.x >> 8], d = blockIdx.x & 255;
   const int t0 = halo_tile0[k], th = halo_tile0[k + 1] - t0;
   uint32_t* col = tile_hist + (size_t)t0 * 256 + (size_t)d * th;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -332,24 +587,34 @@ __global__ void __launch_bounds__(256) g_digit_base(uint32_t* __restrict__ digit
   digit_base[(size_t)k * 256 + d] = base;
 }
 
-template <typename Key>
-__global__ void __launch_bounds__(T) g_scatter(const Key* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                               Key* __restrict__ kout, uint32_t* __restrict__ vout,
-                                               const int2* __restrict__ tile_range, const int* __restrict__ tile_halo,
-                                               const int* __restrict__ halo_tile0, const HaloDev* __restrict__ halos,
-                                               const uint32_t* __restrict__ tile_off,
-                                               const uint32_t* __restrict__ digit_base, int shift) {
-  __shared__ uint16_t hist[NWARP * 256];
-  __shared__ uint32_t doff[256];
+// Stable scatter of one tile by the digit at `shift`.  Each warp ranks its
+// 8 batches of 32 keys by warp ballots on the digit's bits (the lanes with
+// the same digit), the tile is re-ordered by digit in shared memory, and
+// consecutive threads then write consecutive positions of each digit's run.
+// FIRST: the values are the candidate positions (not read).  LAST: instead
+// of (key, value) the radial-order streams are written from the records:
+// (w, r), the mass (per-particle masses), u_th (gas) and the position; the
+// tile's members' exact sum m v goes to tile_mv.
+template <typename Key, typename R, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(T) g_scatter(GridLaunch L, const Key* __restrict__ kin,
+                                               const uint32_t* __restrict__ vin, Key* __restrict__ kout,
+                                               uint32_t* __restrict__ vout, int shift) {
+  using V4 = typename Prec<R>::V4;
+  using Acc = typename Prec<R>::Acc;
+  __shared__ uint16_t whist[NWARP][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t gofs[256];
+  __shared__ uint32_t red[NWARP];
+  __shared__ Key skey[TILE];
+  __shared__ uint32_t sval[TILE];
   const int t = blockIdx.x;
-  const int2 tr = tile_range[t];
-  const int kh = tile_halo[t];
-  const long long gb = halos[kh].gbase;
-  const int t0 = halo_tile0[kh], th = halo_tile0[kh + 1] - t0;
+  const int2 tr = L.tile_range[t];
+  const int kh = L.tile_halo[t];
+  const long long gb = L.halos[kh].gbase;
+  const int t0 = L.halo_tile0[kh], th = L.halo_tile0[kh + 1] - t0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < NWARP * 256; i += T) hist[i] = 0;
-  __syncthreads();
-  constexpr int CH = TILE / NWARP;      // 256 elements per warp, 8 batches of 32
+  for (int i = threadIdx.x; i < NWARP * 256; i += T) (&whist[0][0])[i] = 0;
+  constexpr int CH = TILE / NWARP;       // 256 elements per warp
   Key key[IPT];
   uint32_t val[IPT];
   uint16_t rank[IPT];
@@ -358,31 +623,44 @@ __global__ void __launch_bounds__(T) g_scatter(const Key* __restrict__ kin, cons
     const int e = warp * CH + b * 32 + lane;
     const bool valid = e < tr.y;
     key[b] = valid ? kin[tr.x + e] : (Key)0;
-    val[b] = valid ? vin[tr.x + e] : 0u;
+    if (FIRST) val[b] = (uint32_t)((long long)tr.x + e - gb);
+    else val[b] = valid ? vin[tr.x + e] : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < IPT; ++b) {
+    const int e = warp * CH + b * 32 + lane;
+    const bool valid = e < tr.y;
     const unsigned vmask = __ballot_sync(FULL_MASK, valid);
-    rank[b] = 0;
-    if (valid) {
-      const uint32_t dg = (uint32_t)(key[b] >> shift) & 0xffu;
-      const unsigned peers = __match_any_sync(vmask, dg);
-      const unsigned below = peers & lanemask_lt();
-      const uint16_t base = hist[warp * 256 + dg];
-      rank[b] = (uint16_t)(base + __popc(below));
-      __syncwarp(vmask);
-      if (below == 0) hist[warp * 256 + dg] = (uint16_t)(base + __popc(peers));
+    const uint32_t dg = (uint32_t)(key[b] >> shift) & 0xffu;
+    unsigned peers = vmask;
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const unsigned bb = __ballot_sync(FULL_MASK, (dg >> bit) & 1u);
+      peers &= ((dg >> bit) & 1u) ? bb : ~bb;
     }
+    const unsigned below = peers & lanemask_lt();
+    uint16_t base = 0;
+    if (valid) base = whist[warp][dg];
+    rank[b] = (uint16_t)(base + __popc(below));
+    __syncwarp();
+    if (valid && below == 0) whist[warp][dg] = (uint16_t)(base + __popc(peers));
     __syncwarp();
   }
   __syncthreads();
   {
-    // within-tile offsets of each (digit, warp) and the tile's global offsets
+    // per digit: offsets of each warp's run, the digit's start in the tile
+    // and its first global position (digit base + tiles before this one)
     const int d = threadIdx.x;
     uint32_t run = 0;
+#pragma unroll
     for (int w = 0; w < NWARP; ++w) {
-      const uint32_t c = hist[w * 256 + d];
-      hist[w * 256 + d] = (uint16_t)run;
+      const uint32_t c = whist[w][d];
+      whist[w][d] = (uint16_t)run;
       run += c;
     }
-    doff[d] = digit_base[(size_t)kh * 256 + d] + tile_off[(size_t)t0 * 256 + (size_t)d * th + (t - t0)];
+    dstart[d] = block_excl(run, red);
+    gofs[d] = L.digit_base[(size_t)kh * 256 + d] + L.tile_hist[(size_t)t0 * 256 + (size_t)d * th + (t - t0)];
   }
   __syncthreads();
 #pragma unroll
@@ -390,347 +668,602 @@ __global__ void __launch_bounds__(T) g_scatter(const Key* __restrict__ kin, cons
     const int e = warp * CH + b * 32 + lane;
     if (e < tr.y) {
       const uint32_t dg = (uint32_t)(key[b] >> shift) & 0xffu;
-      const long long dst = gb + (long long)doff[dg] + hist[warp * 256 + dg] + rank[b];
-      kout[dst] = key[b];
-      vout[dst] = val[b];
+      const uint32_t lp = dstart[dg] + whist[warp][dg] + rank[b];
+      skey[lp] = key[b];
+      sval[lp] = val[b];
+    }
+  }
+  __syncthreads();
+  Acc smv[3] = {0, 0, 0};
+  const int s_v = LAST ? L.state[kh].s_mv : 0;
+  for (int i = threadIdx.x; i < tr.y; i += T) {
+    const Key k = skey[i];
+    const uint32_t v = sval[i];
+    const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
+    const long long dst = gb + (long long)gofs[dg] + (i - (int)dstart[dg]);
+    if (!LAST) {
+      kout[dst] = k;
+      vout[dst] = v;
+    } else {
+      L.val_x[dst] = v;
+      if (k != ~(Key)0) {
+        const V4* rc = (const V4*)L.rec + 2 * (gb + v);
+        const V4 a = rc[0], q = rc[1];
+        ((V4*)L.wr)[dst] = a;
+        if (L.ms) ((R*)L.ms)[dst] = q.w;
+        if (L.uth) {
+          const long long slot = L.halos[kh].offset + v;
+          const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+          ((R*)L.uth)[dst] = (R)(L.p.coord_type == AHF_COORD_F64 ? __ldg((const double*)L.p.u_th + pi)
+                                                                 : (double)__ldg((const float*)L.p.u_th + pi));
+        }
+        smv[0] += fixr(mul_rn(q.w, q.x), s_v);
+        smv[1] += fixr(mul_rn(q.w, q.y), s_v);
+        smv[2] += fixr(mul_rn(q.w, q.z), s_v);
+      }
+    }
+  }
+  if (LAST) {
+    __shared__ Acc racc[NWARP];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const Acc s = block_sum(smv[a], racc);
+      if (threadIdx.x == 0) A<Acc>(L.tile_mv[3 * (size_t)t + a]) = s;
     }
   }
 }
 
-// ---- fill -------------------------------------------------------------------------
-
-template <int CT, typename R>
-__global__ void __launch_bounds__(T) g_fill(GridLaunch L) {
-  using Key = typename Prec<R>::Key;
+// No radix pass (every key equal): the radial order is the candidate order.
+template <typename R>
+__global__ void __launch_bounds__(T) g_fill_identity(GridLaunch L) {
   using V4 = typename Prec<R>::V4;
-  const Key* key = (const Key*)L.key_x;
-  const uint32_t* val = L.val_x;
-  V4* wm = (V4*)L.wm;
-  R* rr = (R*)L.r;
+  using Key = typename Prec<R>::Key;
+  using Acc = typename Prec<R>::Acc;
   const int t = blockIdx.x;
   const int2 tr = L.tile_range[t];
-  const int k = L.tile_halo[t];
-  const HaloDev H = L.halos[k];
-  const GridHaloState& S = L.state[k];
-  const int s_v = S.s_mv;
-  const long long nm = S.n_member;
-  long long smv[3] = {0, 0, 0};
+  const int kh = L.tile_halo[t];
+  const long long gb = L.halos[kh].gbase;
+  const int s_v = L.state[kh].s_mv;
+  const Key* key = (const Key*)L.key_a;
+  Acc smv[3] = {0, 0, 0};
   for (int e = threadIdx.x; e < tr.y; e += T) {
     const long long g = (long long)tr.x + e;
-    const long long p = g - H.gbase;
-    if (p < nm) {
-      const long long slot = H.offset + val[g];
-      const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-      R w[3], v[3], m;
-      w_of<CT>(L.p, pi, H, L.frame, L.prm, w, v, m);
-      V4 q;
-      q.x = w[0];
-      q.y = w[1];
-      q.z = w[2];
-      q.w = m;
-      wm[g] = q;
-      rr[g] = real_of(key[g], R());
-      if (L.uth) ((R*)L.uth)[g] = (R)(CT == AHF_COORD_F64 ? __ldg((const double*)L.p.u_th + pi)
-                                                         : (double)__ldg((const float*)L.p.u_th + pi));
-#pragma unroll
-      for (int a = 0; a < 3; ++a) smv[a] += fix_real(mul_rn(m, v[a]), s_v);
+    const uint32_t v = (uint32_t)(g - gb);
+    L.val_x[g] = v;
+    if (key[g] != ~(Key)0) {
+      const V4* rc = (const V4*)L.rec + 2 * g;
+      const V4 a = rc[0], q = rc[1];
+      ((V4*)L.wr)[g] = a;
+      if (L.ms) ((R*)L.ms)[g] = q.w;
+      if (L.uth) {
+        const long long slot = L.halos[kh].offset + v;
+        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+        ((R*)L.uth)[g] = (R)(L.p.coord_type == AHF_COORD_F64 ? __ldg((const double*)L.p.u_th + pi)
+                                                             : (double)__ldg((const float*)L.p.u_th + pi));
+      }
+      smv[0] += fixr(mul_rn(q.w, q.x), s_v);
+      smv[1] += fixr(mul_rn(q.w, q.y), s_v);
+      smv[2] += fixr(mul_rn(q.w, q.z), s_v);
     }
   }
+  __shared__ Acc racc[NWARP];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const long long x = warp_sum(smv[a]);
-    if ((threadIdx.x & 31) == 0 && x != 0)
-      atomicAdd((unsigned long long*)&L.state[k].mv[a], (unsigned long long)x);
+    const Acc s = block_sum(smv[a], racc);
+    if (threadIdx.x == 0) A<Acc>(L.tile_mv[3 * (size_t)t + a]) = s;
   }
 }
 
-// ---- iteration ------------------------------------------------------------------------
+// ---- sub-tiles: the unit of a pass -------------------------------------------------------
 
-// Per tile: exact sums of m and m/r over alive members, and their count.
+// Sub-tile u covers elements [(u % SPT) SUB, (u % SPT + 1) SUB) of tile u / SPT
+// (clipped to the tile); one warp handles it, element j of row i at position
+// 32 i + lane, so that each row is one coalesced access.
+constexpr int SUB = GRID_SUB;           // 256
+constexpr int SPT = TILE / SUB;         // 8 sub-tiles per tile
+constexpr int ROWS = SUB / 32;          // 8
+constexpr int HT_BIG = 1024;            // threads of the per-halo kernel (largest halo > 64 tiles)
+constexpr int HT_SMALL = 256;           // (otherwise)
+
+// Atomic add of an exact sum into a slot (the __int128 one from two 64-bit
+// atomics: the low word's carry goes into the high word, so the total is
+// exact once every addition has landed).
+__device__ __forceinline__ void atomic_acc(AccSlot& s, long long v) {
+  atomicAdd((unsigned long long*)&s.w[0], (unsigned long long)v);
+}
+__device__ __forceinline__ void atomic_acc(AccSlot& s, __int128 v) {
+  const unsigned long long lo = (unsigned long long)v;
+  const unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);
+  const unsigned long long old = atomicAdd((unsigned long long*)&s.w[0], lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  atomicAdd((unsigned long long*)&s.w[1], hi + carry);
+}
+
+// v_bulk = sum m v / sum m of the current set, into the halo state.
 template <typename R>
-__global__ void __launch_bounds__(T) g_tile_sums(GridLaunch L, int final_pass) {
+__device__ __forceinline__ void set_vbulk(GridHaloState& S, typename Prec<R>::Acc m,
+                                          const typename Prec<R>::Acc mv[3]) {
+  if (sizeof(R) == 4) {
+    const float mt = from_fix(m, S.s_m, R());
+    for (int a = 0; a < 3; ++a) S.vbulk[a] = (float)from_fix(mv[a], S.s_mv, R()) / mt;
+  } else {
+    const double mt = dfix(m, S.s_m);
+    for (int a = 0; a < 3; ++a) S.vbulk_d[a] = dfix(mv[a], S.s_mv) / mt;
+  }
+}
+
+// x 2^-s from an exact sum: in the mixed mode float_from_fix's bits, with
+// 2^-s passed as a float (0 when it is not a normal float: then the general
+// route); in the FP64 mode the nearest double.
+__device__ __forceinline__ float fix_to_real(long long v, int s, float sc, float) {
+  if (sc == 0.0f) return float_from_fix(v, s);
+  const float hi = (float)(int)(v >> 32);
+  const float lo = (float)(unsigned)(v & 0xffffffffll);
+  return fmaf(hi, 4294967296.0f, lo) * sc;
+}
+__device__ __forceinline__ double fix_to_real(__int128 v, int s, float, double) { return double_from_fix128(v, s); }
+__device__ __forceinline__ float pow2_neg(int s) {
+  return (s >= -127 && s <= 126) ? __int_as_float((127 - s) << 23) : 0.0f;
+}
+
+// Sums of the initial set (all members alive) per sub-tile, one warp each,
+// into copy 1 (the first pass's).
+template <typename R>
+__global__ void __launch_bounds__(T) g_sums(GridLaunch L) {
   using V4 = typename Prec<R>::V4;
-  const V4* wm = (const V4*)L.wm;
-  const R* rr = (const R*)L.r;
-  const int t = blockIdx.x;
-  const int k = L.tile_halo[t];
-  const GridHaloState& S = L.state[k];
-  if (!final_pass && !S.active) return;
-  const int2 tr = L.tile_range[t];
-  const long long lim = L.halos[k].gbase + S.n_member;
-  long long a = 0, b = 0, c = 0;
-  const int s_m = S.s_m, s_r = S.s_mr;
-  for (int e = threadIdx.x; e < tr.y; e += T) {
-    const long long g = (long long)tr.x + e;
-    if (g < lim) {
-      const R m = wm[g].w;
-      if (!neg(m)) {
-        a += fix_real(m, s_m);
-        b += fix_real(m * rinv_real(rr[g], L.prm), s_r);
-        c += 1;
+  using Acc = typename Prec<R>::Acc;
+  const int lane = threadIdx.x & 31;
+  const int n_sub = L.n_tiles * SPT;
+  const V4* wr = (const V4*)L.wr;
+  const R* ms = (const R*)L.ms;
+  const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
+  for (int u = (blockIdx.x * T + threadIdx.x) >> 5; u < n_sub; u += (gridDim.x * T) >> 5) {
+    const int t = u / SPT;
+    const int k = L.tile_halo[t];
+    const GridHaloState& S = L.state[k];
+    const int2 tr = L.tile_range[t];
+    const long long lim = L.halos[k].gbase + S.n_member;
+    const int e0 = (u % SPT) * SUB;
+    Acc a = 0, b = 0;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+      const int e = e0 + 32 * i + lane;
+      const long long g = (long long)tr.x + e;
+      if (e < tr.y && g < lim) {
+        const R r = wr[g].w;
+        const R m = ms ? ms[g] : m0;
+        a += fixp(m, S.s_m);
+        b += fixp(m * rinv_real(r, L.prm), S.s_mr);
+        ++c;
       }
     }
-  }
-  __shared__ long long red[NWARP][3];
-  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[warp][0] = a; red[warp][1] = b; red[warp][2] = c; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    long long s = 0;
-    for (int w = 0; w < NWARP; ++w) s += red[w][threadIdx.x];
-    L.tile_agg[(size_t)t * 3 + threadIdx.x] = s;
+    a = wsum(a);
+    b = wsum(b);
+    c = __reduce_add_sync(FULL_MASK, c);
+    if (lane == 0) {
+      ((Acc*)L.agg_m)[n_sub + u] = a;
+      ((Acc*)L.agg_r)[n_sub + u] = b;
+      L.agg_c[n_sub + u] = c;
+    }
   }
 }
 
-// One CTA per halo: exclusive prefix of the tile sums, totals, v_bulk.
-template <typename R>
-__global__ void __launch_bounds__(256) g_tile_scan(GridLaunch L, int final_pass) {
+// Per halo, after the initial sums (INIT, pass 0) or after pass `pass`: the
+// tiles' sums of the set left (copy (pass + 1) & 1 of the sub-tile sums),
+// their exclusive prefix over the halo (for the next pass and the final one),
+// the totals, and the halo's bookkeeping: iterations, particle-iterations,
+// band tests, sum m v, v_bulk, convergence (Sect. 2.1, Appendix A: the loop
+// ends when an iteration removes nothing).  Each thread takes a run of
+// consecutive tiles; the runs' sums are scanned over the CTA.
+// The sub-tiles of the haloes still active are listed for the next pass.
+template <typename R, bool INIT, int HT>
+__global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
+  using Acc = typename Prec<R>::Acc;
+  constexpr int CH = 1024;                 // tiles per chunk held in shared memory
+  constexpr int NW = HT / 32;
+  __shared__ Acc racc[NW];
+  __shared__ Acc wm_[NW], wr_[NW];
+  __shared__ long long wc_[NW];
+  __shared__ Acc tm_[CH], tr_[CH];
+  __shared__ long long tc_[CH];
+  __shared__ int s_nw, s_base;
+  __shared__ Acc s_tm, s_tr;
+  __shared__ long long s_tc;
   const int k = blockIdx.x;
   GridHaloState& S = L.state[k];
-  if (!final_pass && !S.active) return;
+  if (!INIT && !S.active) return;
+  const int n_sub = L.n_tiles * SPT;
+  const int cp = (pass + 1) & 1;
+  const Acc* am = (const Acc*)L.agg_m + (size_t)cp * n_sub;
+  const Acc* ar = (const Acc*)L.agg_r + (size_t)cp * n_sub;
+  const int* ac = L.agg_c + (size_t)cp * n_sub;
+  Acc* pm = (Acc*)L.pre_m;
+  Acc* pr = (Acc*)L.pre_r;
   const int t0 = L.halo_tile0[k], t1 = L.halo_tile0[k + 1];
-  __shared__ long long wt[8][3];
-  __shared__ long long carry[3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
-  __syncthreads();
-  for (int base = t0; base < t1; base += 256) {
-    const int t = base + threadIdx.x;
-    long long v[3] = {0, 0, 0};
-    if (t < t1)
-      for (int q = 0; q < 3; ++q) v[q] = L.tile_agg[(size_t)t * 3 + q];
-    long long inc[3];
-    for (int q = 0; q < 3; ++q) {
-      inc[q] = warp_inclusive_scan(v[q], lane);
-      if (lane == 31) wt[warp][q] = inc[q];
+  // only the sub-tiles holding members carry sums (the others are never
+  // written by a pass)
+  const int u_end = t0 * SPT + (int)((S.n_member + SUB - 1) / SUB);
+  Acc cm = 0, cr = 0;                      // carry: the sums of the chunks before
+  long long cc = 0;
+  for (int c0 = t0; c0 < t1; c0 += CH) {
+    const int cn = min(CH, t1 - c0);
+    // tile sums, SPT lanes per tile (coalesced), reduced by shuffles
+    for (int x0 = 0; x0 < cn * SPT; x0 += HT) {
+      const int x = x0 + threadIdx.x;
+      const int u = c0 * SPT + x;
+      Acc m = 0, r = 0;
+      long long c = 0;
+      if (x < cn * SPT && u < u_end) {
+        m = am[u];
+        r = ar[u];
+        c = ac[u];
+      }
+#pragma unroll
+      for (int o = 1; o < SPT; o <<= 1) {
+        m += shfl_xor_x(m, o);
+        r += shfl_xor_x(r, o);
+        c += shfl_xor_x(c, o);
+      }
+      if ((x % SPT) == 0 && x < cn * SPT) {
+        tm_[x / SPT] = m;
+        tr_[x / SPT] = r;
+        tc_[x / SPT] = c;
+      }
     }
     __syncthreads();
-    for (int q = 0; q < 3; ++q) {
-      long long b = carry[q];
-      for (int w = 0; w < warp; ++w) b += wt[w][q];
-      if (t < t1) L.tile_pre[(size_t)t * 3 + q] = b + inc[q] - v[q];
+    // exclusive scan of the chunk's tile sums: a run of consecutive tiles per thread
+    const int per = (cn + HT - 1) / HT;
+    const int j0 = min(cn, (int)threadIdx.x * per), j1 = min(j0 + per, cn);
+    Acc sm = 0, sr = 0;
+    long long sc = 0;
+    for (int j = j0; j < j1; ++j) {
+      sm += tm_[j];
+      sr += tr_[j];
+      sc += tc_[j];
+    }
+    const Acc im = wscan(sm, lane), ir = wscan(sr, lane);
+    const long long ic = wscan(sc, lane);
+    if (lane == 31) {
+      wm_[warp] = im;
+      wr_[warp] = ir;
+      wc_[warp] = ic;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-      long long s = 0;
-      for (int w = 0; w < 8; ++w) s += wt[w][threadIdx.x];
-      carry[threadIdx.x] += s;
+    if (warp == 0) {
+      const bool in = lane < NW;
+      const Acc xm = in ? wm_[lane] : (Acc)0, xr = in ? wr_[lane] : (Acc)0;
+      const long long xc = in ? wc_[lane] : 0ll;
+      const Acc ym = wscan(xm, lane), yr = wscan(xr, lane);
+      const long long yc = wscan(xc, lane);
+      __syncwarp();
+      if (in) {
+        wm_[lane] = ym - xm;
+        wr_[lane] = yr - xr;
+        wc_[lane] = yc - xc;
+      }
+      if (lane == 31) {
+        s_tm = ym;
+        s_tr = yr;
+        s_tc = yc;
+      }
     }
     __syncthreads();
+    Acc em = cm + wm_[warp] + im - sm, er = cr + wr_[warp] + ir - sr;
+    long long ec = cc + wc_[warp] + ic - sc;
+    for (int j = j0; j < j1; ++j) {
+      pm[c0 + j] = em;
+      pr[c0 + j] = er;
+      L.pre_c[c0 + j] = ec;
+      em += tm_[j];
+      er += tr_[j];
+      ec += tc_[j];
+    }
+    cm += s_tm;
+    cr += s_tr;
+    cc += s_tc;
+    __syncthreads();                       // the chunk's shared arrays are reused
+  }
+  const Acc M = cm, Rr = cr;
+  const long long C = cc;
+  Acc mvs[3] = {0, 0, 0};
+  if (INIT) {
+    // sum m v of the members, from the sort's per-tile sums
+    for (int j = t0 + threadIdx.x; j < t1; j += HT)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) mvs[q] += Ald<Acc>(L.tile_mv[3 * (size_t)j + q]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) mvs[q] = block_sum_n<Acc, HT>(mvs[q], racc);
   }
   if (threadIdx.x == 0) {
-    S.m_tot = carry[0];
-    S.t_tot = carry[1];
-    S.n_alive = carry[2];
-    if (!final_pass) {
-      // v_bulk of the current set (of the initial set with AHF_VAR_VBULK_INITIAL)
-      if (S.n_iter == 0 || !L.prm.vbulk_initial) {
-        if (sizeof(R) == 4) {
-          const float mt = float_from_fix(carry[0], S.s_m);
-          for (int a = 0; a < 3; ++a) S.vbulk[a] = float_from_fix(S.mv[a], S.s_mv) / mt;
-        } else {
-          const double mt = double_from_fix(carry[0], S.s_m);
-          for (int a = 0; a < 3; ++a) S.vbulk_d[a] = double_from_fix(S.mv[a], S.s_mv) / mt;
-        }
+    Acc mv[3];
+    int active;
+    if (INIT) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) mv[q] = mvs[q];
+      active = C > 0 ? 1 : 0;
+    } else {
+      const long long alive = S.n_alive;
+      S.part_iter += alive;
+      S.band += S.band_pass;
+      S.band_pass = 0;
+      S.n_iter = pass;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        mv[q] = Ald<Acc>(S.mv[q]) - Ald<Acc>(S.rem_mv[q]);
+        A<Acc>(S.rem_mv[q]) = 0;
       }
-      S.removed = 0;
-      S.rem_m = 0;
-      S.rem_mv[0] = S.rem_mv[1] = S.rem_mv[2] = 0;
-      S.band_iter = 0;
+      active = 1;
+      if (C == alive) {
+        active = 0;
+      } else if (C == 0) {
+        active = 0;
+        S.status |= AHF_HALO_EMPTY;
+      } else if (pass >= L.prm.max_iter) {
+        active = 0;
+        S.status |= AHF_HALO_NOT_CONVERGED;
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) A<Acc>(S.mv[q]) = mv[q];
+    A<Acc>(S.m_tot) = M;
+    A<Acc>(S.t_tot) = Rr;
+    S.n_alive = C;
+    if (active && (INIT || !L.prm.vbulk_initial)) set_vbulk<R>(S, M, mv);
+    S.active = active;
+    // the halo's sub-tiles holding members go on the next pass's list
+    s_nw = active ? (int)((S.n_member + SUB - 1) / SUB) : 0;
+    s_base = s_nw ? atomicAdd(&L.ctl->work_n[(pass + 1) & 1], s_nw) : 0;
+  }
+  __syncthreads();
+  const int nw = s_nw;
+  if (nw) {
+    const long long nm = S.n_member, gb = L.halos[k].gbase;
+    int4* list = L.work + (size_t)((pass + 1) & 1) * n_sub + s_base;
+    for (int j = threadIdx.x; j < nw; j += HT)
+      list[j] = make_int4(t0 * SPT + j, k, (int)(gb + (long long)j * SUB), (int)min((long long)SUB, nm - (long long)j * SUB));
   }
 }
 
-// Blocked per-thread run inside a tile: exclusive prefix of the thread's
-// first element from the tile prefix plus a block scan of thread totals.
-struct TileScan {
-  long long m, r, c;
-};
+// ---- one unbinding pass -----------------------------------------------------------------
 
-__device__ __forceinline__ TileScan block_scan_tile(long long a, long long b, long long c, long long pre_a,
-                                                     long long pre_b, long long pre_c) {
-  __shared__ long long wt[NWARP][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long ia = warp_inclusive_scan(a, lane);
-  const long long ib = warp_inclusive_scan(b, lane);
-  const long long ic = warp_inclusive_scan(c, lane);
-  if (lane == 31) { wt[warp][0] = ia; wt[warp][1] = ib; wt[warp][2] = ic; }
-  __syncthreads();
-  long long ba = pre_a, bb = pre_b, bc = pre_c;
-  for (int w = 0; w < warp; ++w) { ba += wt[w][0]; bb += wt[w][1]; bc += wt[w][2]; }
-  return TileScan{ba + ia - a, bb + ib - b, bc + ic - c};
+constexpr int EPL = SUB / 32;            // 8 consecutive elements per lane
+
+// Prefix sums of a sub-tile's start: the tile's prefix plus the sums of the
+// tile's sub-tiles before it in copy `cp` (lanes < u % SPT read one each).
+template <typename Acc>
+__device__ __forceinline__ void sub_prefix(const GridLaunch& L, int u, int t, int cp, Acc& M, Acc& P, long long* C) {
+  const int lane = threadIdx.x & 31;
+  const int n_sub = L.n_tiles * SPT;
+  const int ui = u % SPT;
+  Acc m = 0, r = 0;
+  int c = 0;
+  if (lane < ui) {
+    const size_t j = (size_t)cp * n_sub + (u - ui) + lane;
+    m = ((const Acc*)L.agg_m)[j];
+    r = ((const Acc*)L.agg_r)[j];
+    if (C) c = L.agg_c[j];
+  }
+  M = ((const Acc*)L.pre_m)[t] + wsum(m);
+  P = ((const Acc*)L.pre_r)[t] + wsum(r);
+  if (C) *C = L.pre_c[t] + __reduce_add_sync(FULL_MASK, c);
 }
 
-template <int CT, typename R>
-__global__ void __launch_bounds__(T) g_apply(GridLaunch L, int iter) {
+// Phi, escape test and removal over sub-tile u (tile t, halo k) in pass
+// `pass`, by one warp: lane l holds elements [8 l, 8 l + 8) of the sub-tile;
+// one warp scan of the lanes' sums places every element's prefix.
+template <typename R, bool UNIF, bool GAS>
+__device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int pass) {
   using V4 = typename Prec<R>::V4;
-  V4* wm = (V4*)L.wm;
-  const R* rr = (const R*)L.r;
-  const int t = blockIdx.x;
-  const int k = L.tile_halo[t];
+  using Acc = typename Prec<R>::Acc;
+  const int u = w.x, k = w.y, t = u / SPT;
   GridHaloState& S = L.state[k];
-  if (!S.active) return;
-  const int2 tr = L.tile_range[t];
+  const int lane = threadIdx.x & 31;
   const HaloDev& H = L.halos[k];
-  const long long lim = H.gbase + S.n_member;
   const int s_m = S.s_m, s_r = S.s_mr, s_v = S.s_mv;
   const ParamsDev& P = L.prm;
+  const int n_sub = L.n_tiles * SPT;
+  const int cp = pass & 1;
+  const long long gl = (long long)w.z + lane * EPL;   // the lane's first element
+  const int nl = w.w - lane * EPL;                    // its members (<= 0: none)
+  V4* wr = (V4*)L.wr;
+  const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
+  // the lane's elements, all in flight at once
+  V4 q[EPL];
+  R mq[EPL], uq[EPL];
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    const long long g = gl + i;
+    if (i < nl) {
+      q[i] = wr[g];
+      mq[i] = UNIF ? m0 : ((const R*)L.ms)[g];
+      uq[i] = GAS ? ((const R*)L.uth)[g] : (R)0;
+    } else {
+      q[i].x = q[i].y = q[i].z = (R)0;
+      q[i].w = neg0(R());
+      mq[i] = m0;
+      uq[i] = (R)0;
+    }
+  }
+  Acc M, Pp;
+  sub_prefix<Acc>(L, u, t, cp, M, Pp, nullptr);
   R vb[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) vb[a] = sizeof(R) == 4 ? (R)S.vbulk[a] : (R)S.vbulk_d[a];
   const R band = sizeof(R) == 4 ? (R)P.band_f : (R)P.band;
-  const long long Ttot = S.t_tot;
-  const long long g0 = (long long)tr.x + (long long)threadIdx.x * IPT;
-  // pass 1: thread totals over its IPT consecutive elements
-  V4 wmv[IPT];
-  R rv[IPT];
-  const R* uth = (const R*)L.uth;
-  long long a = 0, b = 0;
+  const Acc Ttot = Ald<Acc>(S.t_tot);
+  const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
+  const Acc mfix0 = fixr(m0, s_m);
+  // per element: 1/r and the exact terms; the lane's sums
+  R ri[EPL];
+  Acc rf[EPL];
+  Acc a = 0, b = 0;
 #pragma unroll
-  for (int q = 0; q < IPT; ++q) {
-    const long long g = g0 + q;
-    const bool in = (threadIdx.x * IPT + q < tr.y) && g < lim;
-    if (in) {
-      wmv[q] = wm[g];
-      rv[q] = rr[g];
-    } else {
-      wmv[q].x = wmv[q].y = wmv[q].z = (R)0;
-      wmv[q].w = -(R)0;
-      rv[q] = (R)1;
-    }
-    if (!neg(wmv[q].w)) {
-      a += fix_real(wmv[q].w, s_m);
-      b += fix_real(wmv[q].w * rinv_real(rv[q], P), s_r);
-    }
+  for (int i = 0; i < EPL; ++i) {
+    const bool alive = !signbit(q[i].w);
+    ri[i] = rinv_real(q[i].w, P);
+    rf[i] = alive ? fixp(mq[i] * ri[i], s_r) : (Acc)0;
+    if (alive) a += UNIF ? mfix0 : fixp(mq[i], s_m);
+    b += rf[i];
   }
-  TileScan ts = block_scan_tile(a, b, 0, L.tile_pre[(size_t)t * 3 + 0], L.tile_pre[(size_t)t * 3 + 1], 0);
-  long long M = ts.m, Pp = ts.r;
-  long long rm = 0, rv0 = 0, rv1 = 0, rv2 = 0;
-  int nrem = 0, nband = 0;
+  const Acc ia = wscan(a, lane), ib = wscan(b, lane);
+  M += ia - a;
+  Pp += ib - b;
+  const size_t jc = (size_t)cp * n_sub + u;
+  const Acc n_m = ((const Acc*)L.agg_m)[jc], n_r = ((const Acc*)L.agg_r)[jc];
+  const int n_c = L.agg_c[jc];
+  // phi and the escape test; the removed only marked here
+  unsigned rem = 0;
+  int nband = 0;
 #pragma unroll
-  for (int q = 0; q < IPT; ++q) {
-    const R m = wmv[q].w;
-    if (!neg(m)) {
-      const R ri = rinv_real(rv[q], P);
-      const long long mfix = fix_real(m, s_m);
-      const long long rfix = fix_real(m * ri, s_r);
-      const R phi = phi_real(from_fix<R>(M, s_m), ri, from_fix<R>(Ttot - Pp, s_r), P);
-      const R ux = wmv[q].x - vb[0], uy = wmv[q].y - vb[1], uz = wmv[q].z - vb[2];
-      R u2 = fma(uz, uz, fma(uy, uy, ux * ux));
-      if (uth) u2 += (R)2 * uth[g0 + q];              // gas: |u|^2 + 2 u_th (Sect. 2.1)
+  for (int i = 0; i < EPL; ++i) {
+    const R r = q[i].w;
+    if (!signbit(r)) {
+      const Acc mfix = UNIF ? mfix0 : fixp(mq[i], s_m);
+      const R phi = phi_real(fix_to_real(M, s_m, sc_m, R()), ri[i], fix_to_real(Ttot - Pp, s_r, sc_r, R()), P);
+      const R ux = q[i].x - vb[0], uy = q[i].y - vb[1], uz = q[i].z - vb[2];
+      R u2 = fma_x(uz, uz, fma_x(uy, uy, ux * ux));
+      if (GAS) u2 += (R)2 * uq[i];                 // gas: |u|^2 + 2 u_th (Sect. 2.1)
       const R two_phi = (R)-2 * phi;
       if (fabs(u2 - two_phi) < band * two_phi) ++nband;
-      if (u2 > two_phi) {
-        const long long g = g0 + q;
-        wm[g].w = -m;
-        ++nrem;
+      if (u2 > two_phi) rem |= 1u << i;
+      M += mfix;
+      Pp += rf[i];
+    }
+  }
+  // the removed: mark (sign bit of r), removal iteration, exact sums of
+  // what goes (m, m/r, m v with v from the candidate's record)
+  Acc rm = 0, rr = 0, rmv0 = 0, rmv1 = 0, rmv2 = 0;
+  const int nrem_l = __popc(rem);
+  const V4* rec = (const V4*)L.rec;
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    if (!(rem & (1u << i))) continue;
+    const long long g = gl + i;
+    const R r = q[i].w, m = mq[i];
+    wr[g].w = -r;
+    const uint32_t pos = L.val_x[g];
+    if (L.out.removed_iter) L.out.removed_iter[H.offset + pos] = pass;
+    const V4 vm = rec[2 * (H.gbase + pos) + 1];    // (v, m) of the candidate
+    rm += UNIF ? mfix0 : fixp(m, s_m);
+    rr += rf[i];
+    rmv0 += fixr(mul_rn(m, vm.x), s_v);
+    rmv1 += fixr(mul_rn(m, vm.y), s_v);
+    rmv2 += fixr(mul_rn(m, vm.z), s_v);
+  }
+  // the sub-tile's sums after the removals (next copy); what it removed goes to the halo
+  const int nrem = __reduce_add_sync(FULL_MASK, nrem_l);
+  nband = __reduce_add_sync(FULL_MASK, nband);
+  if (nrem) {                                      // uniform over the warp
+    rm = wsum(rm);
+    rr = wsum(rr);
+    rmv0 = wsum(rmv0);
+    rmv1 = wsum(rmv1);
+    rmv2 = wsum(rmv2);
+  }
+  if (lane == 0) {
+    const size_t j = (size_t)(cp ^ 1) * n_sub + u;
+    ((Acc*)L.agg_m)[j] = n_m - rm;
+    ((Acc*)L.agg_r)[j] = n_r - rr;
+    L.agg_c[j] = n_c - nrem;
+    if (nrem) {
+      atomic_acc(S.rem_mv[0], rmv0);
+      atomic_acc(S.rem_mv[1], rmv1);
+      atomic_acc(S.rem_mv[2], rmv2);
+    }
+    if (nband) atomicAdd((unsigned long long*)&S.band_pass, (unsigned long long)nband);
+  }
+}
+
+// One pass: warps take the listed sub-tiles (those of the active haloes)
+// round robin, and clear the count of the next pass's list.
+template <typename R, bool UNIF, bool GAS>
+__global__ void __launch_bounds__(T, sizeof(R) == 4 ? 2 : 1) g_pass(GridLaunch L, int pass) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) L.ctl->work_n[(pass + 1) & 1] = 0;
+  const int n = __ldcg(&L.ctl->work_n[pass & 1]);
+  const int4* list = L.work + (size_t)(pass & 1) * L.n_tiles * SPT;
+  for (int i = (blockIdx.x * T + threadIdx.x) >> 5; i < n; i += (gridDim.x * T) >> 5)
+    pass_sub<R, UNIF, GAS>(L, list[i], pass);
+}
+
+// ---- final pass --------------------------------------------------------------------------
+
+// Bound lists (radial order), phi of the final set, compacted radius and
+// inclusive mass for the virial search and the profile rows; one warp per
+// sub-tile, lanes holding consecutive elements as in a pass.
+template <typename R, bool UNIF>
+__global__ void __launch_bounds__(T) g_final(GridLaunch L) {
+  using V4 = typename Prec<R>::V4;
+  using Acc = typename Prec<R>::Acc;
+  const int lane = threadIdx.x & 31;
+  const int n_sub = L.n_tiles * SPT;
+  const V4* wr = (const V4*)L.wr;
+  R* rc = (R*)L.rc;
+  Acc* mc = (Acc*)L.mc;
+  const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
+  const ParamsDev& P = L.prm;
+  for (int u = (blockIdx.x * T + threadIdx.x) >> 5; u < n_sub; u += (gridDim.x * T) >> 5) {
+    const int t = u / SPT;
+    const int k = L.tile_halo[t];
+    const GridHaloState& S = L.state[k];
+    if (S.n_alive == 0) continue;
+    const int2 tr = L.tile_range[t];
+    const HaloDev& H = L.halos[k];
+    const long long lim = H.gbase + S.n_member;
+    const int s_m = S.s_m, s_r = S.s_mr;
+    const Acc Ttot = Ald<Acc>(S.t_tot);
+    const int e0 = (u % SPT) * SUB + lane * EPL;
+    R rq[EPL], mq[EPL];
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = e0 + i;
+      const long long g = (long long)tr.x + e;
+      const bool in = e < tr.y && g < lim;
+      rq[i] = in ? wr[g].w : neg0(R());
+      mq[i] = in ? (UNIF ? m0 : ((const R*)L.ms)[g]) : m0;
+    }
+    Acc M, Pp;
+    long long C;
+    sub_prefix<Acc>(L, u, t, (S.n_iter + 1) & 1, M, Pp, &C);
+    const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
+    R ri[EPL];
+    Acc a = 0, b = 0;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      ri[i] = rinv_real(rq[i], P);
+      if (!signbit(rq[i])) {
+        a += fixp(mq[i], s_m);
+        b += fixp(mq[i] * ri[i], s_r);
+        ++c;
+      }
+    }
+    const Acc ia = wscan(a, lane), ib = wscan(b, lane);
+    const int ic = (int)wscan((uint32_t)c, lane);
+    M += ia - a;
+    Pp += ib - b;
+    C += ic - c;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const R r = rq[i];
+      if (!signbit(r)) {
+        const long long g = (long long)tr.x + e0 + i;
+        const R m = mq[i];
+        const Acc mfix = fixp(m, s_m);
+        const R phi = phi_real(fix_to_real(M, s_m, sc_m, R()), ri[i], fix_to_real(Ttot - Pp, s_r, sc_r, R()), P);
         const long long slot = H.offset + L.val_x[g];
         const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-        R v[3];
-        velocity_real<CT>(L.p, pi, v);
-        rm += mfix;
-        rv0 += fix_real(mul_rn(m, v[0]), s_v);
-        rv1 += fix_real(mul_rn(m, v[1]), s_v);
-        rv2 += fix_real(mul_rn(m, v[2]), s_v);
-        if (L.out.removed_iter) L.out.removed_iter[slot] = iter;
+        const long long dst = H.offset + C;
+        L.out.bound_idx[dst] = pi;
+        if (L.out.phi) ((R*)L.out.phi)[dst] = phi;
+        if (L.out.removed_iter) L.out.removed_iter[slot] = 0;
+        rc[H.gbase + C] = r;
+        mc[H.gbase + C] = M + mfix;
+        M += mfix;
+        Pp += fixp(m * ri[i], s_r);
+        C += 1;
       }
-      M += mfix;
-      Pp += rfix;
-    }
-  }
-  nrem = __reduce_add_sync(FULL_MASK, nrem);
-  nband = __reduce_add_sync(FULL_MASK, nband);
-  if (__any_sync(FULL_MASK, nrem != 0)) {
-    rm = warp_sum(rm); rv0 = warp_sum(rv0); rv1 = warp_sum(rv1); rv2 = warp_sum(rv2);
-    if ((threadIdx.x & 31) == 0 && nrem) {
-      atomicAdd((unsigned long long*)&S.rem_m, (unsigned long long)rm);
-      atomicAdd((unsigned long long*)&S.rem_mv[0], (unsigned long long)rv0);
-      atomicAdd((unsigned long long*)&S.rem_mv[1], (unsigned long long)rv1);
-      atomicAdd((unsigned long long*)&S.rem_mv[2], (unsigned long long)rv2);
-      atomicAdd((unsigned long long*)&S.removed, (unsigned long long)nrem);
-    }
-  }
-  if ((threadIdx.x & 31) == 0 && nband) atomicAdd((unsigned long long*)&S.band_iter, (unsigned long long)nband);
-}
-
-__global__ void g_advance(GridLaunch L) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L.n_halos) return;
-  GridHaloState& S = L.state[k];
-  if (!S.active) return;
-  S.n_iter += 1;
-  S.part_iter += S.n_alive;
-  S.band += S.band_iter;
-  for (int a = 0; a < 3; ++a) S.mv[a] -= S.rem_mv[a];
-  const long long left = S.n_alive - S.removed;
-  if (S.removed == 0) {
-    S.active = 0;
-  } else if (left == 0) {
-    S.active = 0;
-    S.status |= AHF_HALO_EMPTY;
-    S.n_alive = 0;
-  } else if (S.n_iter >= L.prm.max_iter) {
-    S.active = 0;
-    S.status |= AHF_HALO_NOT_CONVERGED;
-  }
-  if (S.active) atomicAdd(L.any_active, 1);
-}
-
-// ---- finish ---------------------------------------------------------------------------
-
-template <typename R>
-__global__ void __launch_bounds__(T) g_emit(GridLaunch L) {
-  using V4 = typename Prec<R>::V4;
-  const V4* wm = (const V4*)L.wm;
-  const R* rr = (const R*)L.r;
-  R* rc = (R*)L.rc;
-  const int t = blockIdx.x;
-  const int k = L.tile_halo[t];
-  GridHaloState& S = L.state[k];
-  const int2 tr = L.tile_range[t];
-  const HaloDev& H = L.halos[k];
-  const long long lim = H.gbase + S.n_member;
-  const int s_m = S.s_m, s_r = S.s_mr;
-  const ParamsDev& P = L.prm;
-  const long long Ttot = S.t_tot;
-  const long long g0 = (long long)tr.x + (long long)threadIdx.x * IPT;
-  R mq[IPT], rq[IPT];
-  long long a = 0, b = 0, c = 0;
-#pragma unroll
-  for (int q = 0; q < IPT; ++q) {
-    const long long g = g0 + q;
-    const bool in = (threadIdx.x * IPT + q < tr.y) && g < lim;
-    mq[q] = in ? wm[g].w : -(R)0;
-    rq[q] = in ? rr[g] : (R)1;
-    if (!neg(mq[q])) {
-      a += fix_real(mq[q], s_m);
-      b += fix_real(mq[q] * rinv_real(rq[q], P), s_r);
-      c += 1;
-    }
-  }
-  const size_t tp = (size_t)t * 3;
-  TileScan ts = block_scan_tile(a, b, c, L.tile_pre[tp], L.tile_pre[tp + 1], L.tile_pre[tp + 2]);
-  long long M = ts.m, Pp = ts.r, C = ts.c;
-#pragma unroll
-  for (int q = 0; q < IPT; ++q) {
-    const R m = mq[q];
-    if (!neg(m)) {
-      const long long g = g0 + q;
-      const R ri = rinv_real(rq[q], P);
-      const long long mfix = fix_real(m, s_m);
-      const R phi = phi_real(from_fix<R>(M, s_m), ri, from_fix<R>(Ttot - Pp, s_r), P);
-      const long long slot = H.offset + L.val_x[g];
-      const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-      const long long dst = H.offset + C;
-      L.out.bound_idx[dst] = pi;
-      if (L.out.phi) ((R*)L.out.phi)[dst] = phi;
-      if (L.out.removed_iter) L.out.removed_iter[slot] = 0;
-      rc[H.gbase + C] = rq[q];
-      L.mc[H.gbase + C] = M + mfix;
-      M += mfix;
-      Pp += fix_real(m * ri, s_r);
-      C += 1;
     }
   }
 }
@@ -738,7 +1271,9 @@ __global__ void __launch_bounds__(T) g_emit(GridLaunch L) {
 // First compacted index k with M_k < delta_rho 4pi/3 r_{k+1}^3 (r_{N+1} = inf).
 template <typename R>
 __global__ void __launch_bounds__(T) g_virial(GridLaunch L) {
+  using Acc = typename Prec<R>::Acc;
   const R* rc = (const R*)L.rc;
+  const Acc* mc = (const Acc*)L.mc;
   const int t = blockIdx.x;
   const int k = L.tile_halo[t];
   GridHaloState& S = L.state[k];
@@ -753,34 +1288,38 @@ __global__ void __launch_bounds__(T) g_virial(GridLaunch L) {
     if (kk >= nb) break;
     bool cross = true;
     if (kk + 1 < nb) {
-      const long long mk = L.mc[g];
+      const Acc mk = mc[g];
       if (sizeof(R) == 4) {
         const float rn = (float)rc[g + 1];
-        const float lhs = float_from_fix(mk, S.s_m);
+        const float lhs = from_fix(mk, S.s_m, R());
         const float rhs = P.crit_f * rn * rn * rn;
         if (lhs < rhs * (1.0f - 1e-5f)) cross = true;
         else if (lhs > rhs * (1.0f + 1e-5f)) cross = false;
         else {
           const double rd = (double)rn;
-          cross = double_from_fix(mk, S.s_m) < P.crit * rd * rd * rd;
+          cross = dfix(mk, S.s_m) < P.crit * rd * rd * rd;
         }
       } else {
         const double rd = (double)rc[g + 1];
-        const double mkd = L.p.m == nullptr ? (double)(kk + 1) * L.p.m0 : double_from_fix(mk, S.s_m);
+        const double mkd = L.p.m == nullptr ? (double)(kk + 1) * L.p.m0 : dfix(mk, S.s_m);
         cross = mkd < P.crit * rd * rd * rd;
       }
     }
-    if (cross) { kf = kk; break; }
+    if (cross) {
+      kf = kk;
+      break;
+    }
   }
-  // warp min then one atomic per warp
   for (int o = 16; o > 0; o >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, o));
   if ((threadIdx.x & 31) == 0 && kf != 0x7fffffffffffffffll)
     atomicMin((unsigned long long*)&S.k_first, (unsigned long long)kf);
 }
 
-template <typename Real>
+template <typename R>
 __global__ void g_result(GridLaunch L) {
-  const Real* rc = (const Real*)L.rc;
+  using Acc = typename Prec<R>::Acc;
+  const R* rc = (const R*)L.rc;
+  const Acc* mcv = (const Acc*)L.mc;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L.n_halos) return;
   const GridHaloState& S = L.state[k];
@@ -801,13 +1340,13 @@ __global__ void g_result(GridLaunch L) {
     const long long kk = S.k_first;
     // M_vir: (k+1) m0 in FP64 for a uniform mass, else the exact sum
     const bool unim = L.p.m == nullptr;
-    const long long mkx = unim ? 0 : L.mc[H.gbase + kk];
-    const double mk = unim ? double_from_fix(kk + 1, 0) * L.p.m0 : double_from_fix(mkx, S.s_m);
+    const Acc mkx = unim ? (Acc)0 : mcv[H.gbase + kk];
+    const double mk = unim ? double_from_fix(kk + 1, 0) * L.p.m0 : dfix(mkx, S.s_m);
     if (kk == nb - 1) status |= AHF_HALO_RVIR_BEYOND_EDGE;
     bool none;
-    if (sizeof(Real) == 4) {
+    if (sizeof(R) == 4) {
       // the decision and the values as in the on-chip classes (the same bits)
-      const float mkf = unim ? (float)(kk + 1) * L.p.m0f : float_from_fix(mkx, S.s_m);
+      const float mkf = unim ? (float)(kk + 1) * L.p.m0f : (float)from_fix(mkx, S.s_m, R());
       none = below_threshold(mk, mkf, (float)rc[H.gbase + kk], L.prm.crit_f, L.prm.crit);
     } else {
       const double rk = (double)rc[H.gbase + kk];
@@ -820,9 +1359,9 @@ __global__ void g_result(GridLaunch L) {
       Rs.m_vir = mk;
       Rs.r_vir = virial_radius(mk, L.prm.inv_crit);
       if (L.prm.rise_edge && kk == nb - 1) {
-        auto at = [&](long long k, double& r, double& m) {
-          r = sizeof(Real) == 4 ? float_to_double((float)rc[H.gbase + k]) : (double)rc[H.gbase + k];
-          m = unim ? double_from_fix(k + 1, 0) * L.p.m0 : double_from_fix(L.mc[H.gbase + k], S.s_m);
+        auto at = [&](long long j, double& r, double& m) {
+          r = sizeof(R) == 4 ? float_to_double((float)rc[H.gbase + j]) : (double)rc[H.gbase + j];
+          m = unim ? double_from_fix(j + 1, 0) * L.p.m0 : dfix(mcv[H.gbase + j], S.s_m);
         };
         const long long ke = rise_edge_index(nb, at);
         if (ke >= 0) {
@@ -832,8 +1371,8 @@ __global__ void g_result(GridLaunch L) {
         }
       }
     }
-    const double mt = double_from_fix(S.m_tot, S.s_m);
-    for (int a = 0; a < 3; ++a) Rs.vbulk[a] = quotient(double_from_fix(S.mv[a], S.s_mv), mt);
+    const double mt = dfix(Ald<Acc>(S.m_tot), S.s_m);
+    for (int a = 0; a < 3; ++a) Rs.vbulk[a] = quotient(dfix(Ald<Acc>(S.mv[a]), S.s_mv), mt);
   } else {
     Rs.vbulk[0] = Rs.vbulk[1] = Rs.vbulk[2] = 0.0;
   }
@@ -841,80 +1380,170 @@ __global__ void g_result(GridLaunch L) {
   L.out.res[H.index] = Rs;
 }
 
+// Profile rows of every halo of the class from its compacted bound set (one
+// CTA per halo, the rows spread over the threads; Sect. 2.1's radially binned
+// output): each edge by binary search over the compacted radii.
+__global__ void __launch_bounds__(T) g_rows_mixed(GridLaunch L) {
+  const int k = blockIdx.x;
+  const HaloDev& H = L.halos[k];
+  const GridHaloState& S = L.state[k];
+  const ahf_result& Rs = L.out.res[H.index];
+  const double m0 = L.p.m0;
+  const long long gb = H.gbase;
+  profile_rows(L.rows, H.index, (const float*)L.rc, (const long long*)L.mc, [gb](long long j) { return gb + j; },
+               S.n_alive, Rs.r_vir, S.s_m, L.prm.G, L.prm.Gf, L.p.m == nullptr ? &m0 : nullptr, threadIdx.x, T);
+}
+
+// The all-FP64 rows: FP64 radii against the FP64 edges, __int128 masses.
+__global__ void __launch_bounds__(T) g_rows_f64(GridLaunch L) {
+  const int k = blockIdx.x;
+  const HaloDev& H = L.halos[k];
+  const GridHaloState& S = L.state[k];
+  const ahf_result& Rs = L.out.res[H.index];
+  const ProfileRows& Q = L.rows;
+  const int n = Q.n_bins;
+  double* out = Q.prof + (size_t)H.index * n * 4;
+  const long long nb = S.n_alive;
+  const double* rc = (const double*)L.rc + H.gbase;
+  const __int128* mc = (const __int128*)L.mc + H.gbase;
+  if (nb == 0) {
+    for (int i = threadIdx.x; i < 4 * n; i += T) out[i] = 0.0;
+    return;
+  }
+  const double r_out = Rs.r_vir > 0.0 ? Rs.r_vir : rc[nb - 1];
+  const float inv_r = 1.0f / double_to_float(r_out);
+  auto count_le = [&](int b) {               // first j with rc[j] > e_b (b = n: r_out)
+    const double e = b == n ? r_out : r_out * Q.factor[b];
+    long long lo = 0, hi = nb;
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (rc[mid] <= e) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  for (int b = threadIdx.x; b < n; b += T) {
+    const long long c0 = count_le(b), c1 = count_le(b + 1);
+    double M1, Mshell;
+    if (L.p.m == nullptr) {
+      M1 = double_from_fix(c1, 0) * L.p.m0;
+      Mshell = double_from_fix(c1 - c0, 0) * L.p.m0;
+    } else {
+      const __int128 f0 = c0 > 0 ? mc[c0 - 1] : (__int128)0;
+      const __int128 f1 = c1 > 0 ? mc[c1 - 1] : (__int128)0;
+      M1 = double_from_fix128(f1, S.s_m);
+      Mshell = double_from_fix128(f1 - f0, S.s_m);
+    }
+    out[4 * b + 0] = double_from_fix(c1 - c0, 0);
+    out[4 * b + 1] = M1;
+    out[4 * b + 2] = shell_density(Mshell, r_out, inv_r, Q.factor, Q.factor_f, n, b);
+    out[4 * b + 3] = circular_velocity(L.prm.G, L.prm.Gf, M1, r_out, inv_r, Q.factor, Q.factor_f, n, b);
+  }
+}
+
 inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
 
 template <typename R>
 cudaError_t prepare_t(const GridLaunch& L, cudaStream_t s) {
-  if (L.p.coord_type == AHF_COORD_F64) g_prepare<AHF_COORD_F64, R><<<L.n_tiles, T, 0, s>>>(L);
-  else g_prepare<AHF_COORD_F32_REL, R><<<L.n_tiles, T, 0, s>>>(L);
+  if (L.n_tiles == 0) {
+  } else if (sizeof(R) == 4) {
+    if (L.p.coord_type == AHF_COORD_F64) g_prepare_mixed<AHF_COORD_F64><<<L.n_tiles, T, 0, s>>>(L);
+    else g_prepare_mixed<AHF_COORD_F32_REL><<<L.n_tiles, T, 0, s>>>(L);
+  } else {
+    if (L.p.coord_type == AHF_COORD_F64) g_prepare_f64<AHF_COORD_F64><<<L.n_tiles, T, 0, s>>>(L);
+    else g_prepare_f64<AHF_COORD_F32_REL><<<L.n_tiles, T, 0, s>>>(L);
+  }
   g_scales<R><<<blocks_for(L.n_halos, 128), 128, 0, s>>>(L);
   return cudaGetLastError();
 }
 
-template <typename Key>
+template <typename R>
 cudaError_t sort_t(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, unsigned long long and_bits) {
+  using Key = typename Prec<R>::Key;
   const unsigned long long diff = or_bits ^ and_bits;
+  int digits[8];
+  int nd = 0;
+  for (int d = 0; d < (int)sizeof(Key); ++d)
+    if ((diff >> (8 * d)) & 0xffull) digits[nd++] = d;
+  if (L.n_tiles == 0) nd = 0;
+  L.sort_passes = nd;
+  if (L.n_tiles == 0) return cudaGetLastError();
   Key *ki = (Key*)L.key_a, *ko = (Key*)L.key_b;
   uint32_t *vi = L.val_a, *vo = L.val_b;
-  L.sort_passes = 0;
-  for (int d = 0; d < (int)sizeof(Key); ++d) {
-    if (!((diff >> (8 * d)) & 0xffull)) continue;
-    ++L.sort_passes;
-    const int shift = 8 * d;
+  for (int p = 0; p < nd; ++p) {
+    const int shift = 8 * digits[p];
     g_hist<Key><<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_halo, L.halo_tile0, L.tile_hist, shift);
-    g_digit_scan<<<L.n_halos * 256, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.digit_base);
+    g_digit_scan_small<<<L.n_halos, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.digit_base);
+    if (L.n_big) g_digit_scan_big<<<L.n_big * 256, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.big_halos, L.digit_base);
     g_digit_base<<<L.n_halos, 256, 0, s>>>(L.digit_base);
-    g_scatter<Key><<<L.n_tiles, T, 0, s>>>(ki, vi, ko, vo, L.tile_range, L.tile_halo, L.halo_tile0, L.halos,
-                                           L.tile_hist, L.digit_base, shift);
-    Key* x = ki; ki = ko; ko = x;
-    uint32_t* y = vi; vi = vo; vo = y;
+    const bool first = p == 0, last = p == nd - 1;
+    if (first && last) g_scatter<Key, R, true, true><<<L.n_tiles, T, 0, s>>>(L, ki, vi, ko, vo, shift);
+    else if (first) g_scatter<Key, R, true, false><<<L.n_tiles, T, 0, s>>>(L, ki, vi, ko, vo, shift);
+    else if (last) g_scatter<Key, R, false, true><<<L.n_tiles, T, 0, s>>>(L, ki, vi, ko, vo, shift);
+    else g_scatter<Key, R, false, false><<<L.n_tiles, T, 0, s>>>(L, ki, vi, ko, vo, shift);
+    Key* x = ki;
+    ki = ko;
+    ko = x;
+    uint32_t* y = vi;
+    vi = vo;
+    vo = y;
   }
-  L.key_x = ki;
-  L.val_x = vi;
+  if (nd == 0) g_fill_identity<R><<<L.n_tiles, T, 0, s>>>(L);
+  g_sums<R><<<L.iter_grid, T, 0, s>>>(L);
+  if (L.max_halo_tiles > 64) g_halo<R, true, HT_BIG><<<L.n_halos, HT_BIG, 0, s>>>(L, 0);
+  else g_halo<R, true, HT_SMALL><<<L.n_halos, HT_SMALL, 0, s>>>(L, 0);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t fill_t(const GridLaunch& L, cudaStream_t s) {
-  if (L.p.coord_type == AHF_COORD_F64) g_fill<AHF_COORD_F64, R><<<L.n_tiles, T, 0, s>>>(L);
-  else g_fill<AHF_COORD_F32_REL, R><<<L.n_tiles, T, 0, s>>>(L);
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t iterate_t(const GridLaunch& L, int iter, cudaStream_t s) {
-  g_tile_sums<R><<<L.n_tiles, T, 0, s>>>(L, 0);
-  g_tile_scan<R><<<L.n_halos, 256, 0, s>>>(L, 0);
-  if (L.p.coord_type == AHF_COORD_F64) g_apply<AHF_COORD_F64, R><<<L.n_tiles, T, 0, s>>>(L, iter);
-  else g_apply<AHF_COORD_F32_REL, R><<<L.n_tiles, T, 0, s>>>(L, iter);
-  g_advance<<<blocks_for(L.n_halos, 128), 128, 0, s>>>(L);
+cudaError_t iterate_t(const GridLaunch& L, int pass, cudaStream_t s) {
+  const bool unif = L.ms == nullptr, gas = L.uth != nullptr;
+  if (unif && !gas) g_pass<R, true, false><<<L.iter_grid, T, 0, s>>>(L, pass);
+  else if (!unif && !gas) g_pass<R, false, false><<<L.iter_grid, T, 0, s>>>(L, pass);
+  else if (unif) g_pass<R, true, true><<<L.iter_grid, T, 0, s>>>(L, pass);
+  else g_pass<R, false, true><<<L.iter_grid, T, 0, s>>>(L, pass);
+  if (L.max_halo_tiles > 64) g_halo<R, false, HT_BIG><<<L.n_halos, HT_BIG, 0, s>>>(L, pass);
+  else g_halo<R, false, HT_SMALL><<<L.n_halos, HT_SMALL, 0, s>>>(L, pass);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t finish_t(const GridLaunch& L, cudaStream_t s) {
-  g_tile_sums<R><<<L.n_tiles, T, 0, s>>>(L, 1);
-  g_tile_scan<R><<<L.n_halos, 256, 0, s>>>(L, 1);
-  g_emit<R><<<L.n_tiles, T, 0, s>>>(L);
-  g_virial<R><<<L.n_tiles, T, 0, s>>>(L);
+  if (L.n_tiles > 0) {
+    if (L.ms == nullptr) g_final<R, true><<<L.iter_grid, T, 0, s>>>(L);
+    else g_final<R, false><<<L.iter_grid, T, 0, s>>>(L);
+    g_virial<R><<<L.n_tiles, T, 0, s>>>(L);
+  }
   g_result<R><<<blocks_for(L.n_halos, 128), 128, 0, s>>>(L);
+  if (L.rows.prof) {
+    if (sizeof(R) == 4) g_rows_mixed<<<L.n_halos, T, 0, s>>>(L);
+    else g_rows_f64<<<L.n_halos, T, 0, s>>>(L);
+  }
   return cudaGetLastError();
 }
 
+template <typename R>
+int iter_grid_t(int device) {
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, g_pass<R, true, false>, T, 0) != cudaSuccess) return 0;
+  return sms * (per > 0 ? per : 1);
+}
+
 }  // namespace
+
+int grid_iter_grid(int device, int fp64) { return fp64 ? iter_grid_t<double>(device) : iter_grid_t<float>(device); }
 
 cudaError_t grid_prepare(const GridLaunch& L, cudaStream_t s) {
   return L.fp64 ? prepare_t<double>(L, s) : prepare_t<float>(L, s);
 }
 
 cudaError_t grid_sort(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, unsigned long long and_bits) {
-  return L.fp64 ? sort_t<unsigned long long>(L, s, or_bits, and_bits) : sort_t<uint32_t>(L, s, or_bits, and_bits);
+  return L.fp64 ? sort_t<double>(L, s, or_bits, and_bits) : sort_t<float>(L, s, or_bits, and_bits);
 }
 
-cudaError_t grid_fill(const GridLaunch& L, cudaStream_t s) { return L.fp64 ? fill_t<double>(L, s) : fill_t<float>(L, s); }
-
-cudaError_t grid_iterate(const GridLaunch& L, int iter, cudaStream_t s) {
-  return L.fp64 ? iterate_t<double>(L, iter, s) : iterate_t<float>(L, iter, s);
+cudaError_t grid_iterate(const GridLaunch& L, int pass, cudaStream_t s) {
+  return L.fp64 ? iterate_t<double>(L, pass, s) : iterate_t<float>(L, pass, s);
 }
 
 cudaError_t grid_finish(const GridLaunch& L, cudaStream_t s) {

@@ -69,32 +69,45 @@ struct OutputsDev {
 
 // Device error bits reported back through the error word.
 constexpr int ERR_BAD_INDEX = 1;     // a member index was out of range
-constexpr int ERR_TIMEOUT = 2;       // a bounded wait gave up
 constexpr int ERR_CAPACITY = 4;      // a halo exceeded its class capacity
+
+// An exact fixed-point sum of the multi-CTA class: a long long (mixed
+// precision) or an __int128 (all-FP64 mode) held in the first bytes.
+struct alignas(16) AccSlot {
+  long long w[2];
+};
 
 // Per-halo state of the multi-CTA class, kept in the context's workspace.
 struct GridHaloState {
-  unsigned long long mass_max_bits;  // float bits of the largest member mass
-  unsigned long long mr_max_bits;    // float bits of the largest m/r
-  unsigned long long mv_max_bits;    // float bits of the largest |m v_k|
+  unsigned long long mass_max_bits;  // bits of the largest member mass
+  unsigned long long mr_max_bits;    // bits of the largest m/r
+  unsigned long long mv_max_bits;    // bits of the largest |m v_k|
   long long n_member;
-  long long n_alive;
-  long long m_tot;                   // exact sum of alive masses (fixed point)
-  long long mv[3];                   // exact sum of m v of the alive set
-  long long t_tot;                   // exact sum of m/r of the alive set
-  long long removed;                 // removed in the current iteration
-  long long rem_m;                   // exact mass removed in the current iteration
-  long long rem_mv[3];               // exact m v removed in the current iteration
-  long long band_iter;               // band tests in the current iteration
-  long long band;                    // band tests so far
+  long long n_alive;                 // members alive at the start of the next pass
   long long part_iter;
+  long long band;                    // band tests so far
   long long k_first;                 // first virial crossing (compacted index)
+  AccSlot m_tot;                     // exact sum of the alive masses
+  AccSlot t_tot;                     // exact sum of m/r over the alive set
+  AccSlot mv[3];                     // exact sum of m v over the alive set
   int n_iter;
   int status;
   int active;
   int s_m, s_mr, s_mv;               // fixed-point scales
+  int pad0, pad;
+  AccSlot rem_mv[3];                 // exact sum m v of what the current pass removed
+  long long band_pass;               // band tests of the current pass
   float vbulk[3];                    // v_bulk of the current set (mixed precision)
+  float pad2;
   double vbulk_d[3];                 // v_bulk of the current set (all-FP64 mode)
+};
+
+// Device control words of one multi-CTA call.
+struct GridCtl {
+  int work_n[2];                     // sub-tiles to process in the passes of each parity
+  int pad0[2];
+  unsigned long long key_or, key_and;  // OR and AND of every radius key
+  int pad[8];
 };
 
 // Record a static message as the thread's last error (no allocation).
@@ -155,42 +168,66 @@ struct GridLaunch {
   FrameDev frame;
   ParamsDev prm;
   OutputsDev out;
-  HaloDev *halos;          // device copy of the class's haloes
+  HaloDev* halos;          // device copy of the class's haloes
   int n_halos;
   long long n_flat;        // sum of candidate counts of the class
-  GridHaloState *state;    // n_halos
+  GridHaloState* state;    // n_halos
   int fp64;                // 0: mixed precision (float), 1: all-FP64 (double)
+  GridCtl* ctl;
   // flat arrays (n_flat each unless noted); element types follow fp64
+  void* rec;               // 2 per candidate: (w.x, w.y, w.z, r), (v.x, v.y, v.z, m)
+                           // as float4 / 4 doubles, by candidate position
   void *key_a, *key_b;     // radius keys: uint32 / uint64
-  uint32_t *val_a, *val_b;
-  void *key_x;             // the sorted keys (one of a / b)
-  uint32_t *val_x;         // the sorted candidate positions
-  void *wm;                // (w.x, w.y, w.z, m), m's sign bit = removed: float4 / 4 doubles
-  void *r;                 // radius: float / double
-  void *uth;               // gas: thermal energy in radial order (float / double), or NULL
-  long long *mc;           // compacted inclusive mass (final pass)
-  void *rc;                // compacted radius (final pass): float / double
+  uint32_t *val_a, *val_b; // candidate positions riding along the sort
+  void* wr;                // radial order: (w.x, w.y, w.z, r), r's sign bit = removed
+  void* ms;                // radial order masses (float / double), NULL for a uniform mass
+  void* uth;               // gas: thermal energy in radial order (float / double), or NULL
+  uint32_t* val_x;         // radial order -> candidate position
+  void* mc;                // compacted inclusive mass (final pass): long long / __int128
+  void* rc;                // compacted radius (final pass): float / double
   // tiles
   int n_tiles;
-  int2 *tile_range;        // (first flat index, length)
-  int *tile_halo;
-  int *halo_tile0;         // first tile of each halo (n_halos + 1)
-  uint32_t *tile_hist;     // n_tiles * 256, per halo digit-major
-  uint32_t *digit_base;    // n_halos * 256
-  long long *tile_agg;     // n_tiles * 3
-  long long *tile_pre;     // n_tiles * 3
-  int *any_active;         // device flag read by the host loop
-  unsigned long long *key_or_and;  // OR and AND of every key
+  int2* tile_range;        // (first flat index, length)
+  int* tile_halo;
+  int* halo_tile0;         // first tile of each halo (n_halos + 1)
+  uint32_t* tile_hist;     // n_tiles * 256, per halo digit-major
+  uint32_t* digit_base;    // n_halos * 256
+  int* big_halos;          // haloes of more than 256 tiles (digit scans spread over CTAs)
+  int n_big;
+  int max_halo_tiles;      // tiles of the largest halo
+  // per sub-tile of GRID_SUB elements (GRID_TILE / GRID_SUB per tile), two
+  // copies by pass parity (pass p reads copy p & 1 and writes the other): the
+  // exact sums (m, m/r as long long / __int128) and count of its alive members
+  void *agg_m, *agg_r;
+  int* agg_c;
+  // per tile: exclusive prefix of the alive sums over the halo's tiles before
+  // it (for the next pass, then the final one)
+  void *pre_m, *pre_r;
+  long long* pre_c;
+  AccSlot* tile_mv;        // [n_tiles][3]: sum m v of each tile's members (initial set)
+  int4* work;              // [2][n_tiles * GRID_TILE / GRID_SUB]: the sub-tiles of the active
+                           // haloes for the passes of each parity: (sub-tile, halo, first
+                           // flat element, members in it)
+  int iter_grid;           // CTAs of the persistent iteration pass
   int sort_passes;         // radix passes the last grid_sort launched
+  ProfileRows rows;        // rows.prof != NULL: profile rows from the final pass
 };
 
 constexpr int GRID_TILE = 2048;
 constexpr int GRID_THREADS = 256;
+constexpr int GRID_SUB = 256;      // elements of a sub-tile (one warp's share of a pass)
 
+// CTAs of the multi-CTA class's persistent iteration pass that fit on
+// `device` at once.
+int grid_iter_grid(int device, int fp64);
 cudaError_t grid_prepare(const GridLaunch &L, cudaStream_t s);
+// Radix passes over the bits where the keys differ (or_bits ^ and_bits);
+// the last pass also lays out the radial-order streams.  Then the sums of
+// the initial set.
 cudaError_t grid_sort(GridLaunch &L, cudaStream_t s, unsigned long long or_bits, unsigned long long and_bits);
-cudaError_t grid_fill(const GridLaunch &L, cudaStream_t s);
-cudaError_t grid_iterate(const GridLaunch &L, int iter, cudaStream_t s);
+// One unbinding pass over every active halo (pass = iteration number).
+cudaError_t grid_iterate(const GridLaunch &L, int pass, cudaStream_t s);
+// Bound lists, phi, virial crossing, records and (rows.prof) profile rows.
 cudaError_t grid_finish(const GridLaunch &L, cudaStream_t s);
 
 struct ProfileLaunch {

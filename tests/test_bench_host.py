@@ -87,9 +87,10 @@ def test_phase_bytes_of_a_small_batch():
     assert out[0] == 28 * 300 + 12 * 250 + 88
     assert out[3] == 28 * 6000 + 12 * 5000 + 88
     assert out[1] == out[2] == out[4] == out[5] == out[6] == out[7] == 0
-    assert out[8] == 28 * 200_000 + 24 * 180_000
+    # multi-CTA class: the radial stream (w.x, w.y, w.z, r) + m, 20 B per member
+    assert out[8] == 28 * 200_000 + 20 * 180_000
     assert out[9] == 20 * 720_000
-    assert out[10] == 20 * 180_000 + 12 * 150_000 + 88
+    assert out[10] == 20 * 180_000 + 12 * 150_000 + 88 + 32 * bench.N_BINS
     assert out[11] == (16 + 8) * (250 + 5000 + 150_000) + 32 * bench.N_BINS * 3
     # float64 coordinates, uniform mass: 6 x 8 B per candidate
     pop64 = types.SimpleNamespace(coord_type=0, m=None, count=pop.count)
