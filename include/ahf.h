@@ -360,16 +360,21 @@ int ahf_get_option(ahf_ctx *ctx, int option, int64_t *value);
  *
  * Set-up: the first call on a device (the current device, cudaGetDevice)
  * looks up the array's device address with cudaGetSymbolAddress; make that
- * first call before any stream capture.  The call runs on `stream` and
- * returns without waiting.  An out-of-range member index makes that
- * candidate a non-member and is not reported here (ahf_sync needs a
- * context).  Errors: AHF_ERR_INVALID, AHF_ERR_CUDA; ahf_last_error() has
- * the message. */
+ * first call before any stream capture.  The descriptors are staged through
+ * a host array that the next call overwrites, so the call returns
+ * AHF_ERR_INVALID, having enqueued nothing, while `stream` is being
+ * captured.  The call runs on `stream` and returns without waiting.
+ *
+ * error_out: device int32, nullable.  When given, a last kernel on `stream`
+ * writes AHF_OK there, or AHF_ERR_INVALID when a member index was out of
+ * range (that candidate was treated as outside the gather sphere).
+ * Errors: AHF_ERR_INVALID, AHF_ERR_CUDA; ahf_last_error() has the message. */
 #define AHF_STATIC_MAX_HALOS 32768
 #define AHF_STATIC_MAX_COUNT 8192
 int ahf_unbind_batch_static(const ahf_particles *p, const ahf_halo *halos, int64_t n_halos,
                             const int64_t *member_idx, const ahf_params *prm, ahf_result *out,
-                            int64_t *bound_idx, void *phi, int32_t *removed_iter, void *stream);
+                            int64_t *bound_idx, void *phi, int32_t *removed_iter, int32_t *error_out,
+                            void *stream);
 
 /* ---- hosts and subhaloes ------------------------------------------------------ */
 

@@ -101,7 +101,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = sig
     lib.ahf_unbind_batch_host.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     lib.ahf_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
-    lib.ahf_unbind_batch_static.argtypes = sig[1:]
+    lib.ahf_unbind_batch_static.argtypes = sig[1:-1] + [vp, vp]
     lib.ahf_unbind_hierarchy.argtypes = sig[:4] + [vp] + sig[4:]
     lib.ahf_unbind_profile_batch.argtypes = sig[:-1] + [i32, ctypes.c_double, vp, vp]
     if hasattr(lib, "ahf_profile_batch"):

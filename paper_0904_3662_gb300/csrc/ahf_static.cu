@@ -39,6 +39,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_B
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;                               // guards the tables and the host staging
 void* g_scratch_addr[MAX_DEVICES] = {};        // device address of the array, per device
+int g_grid[MAX_DEVICES][3] = {};               // resident CTAs of the three variants, per device
 
 // Host staging (fixed size, no allocation): descriptors in launch order.
 HaloDev g_stage[AHF_STATIC_MAX_HALOS];
@@ -47,6 +48,14 @@ int g_order[AHF_STATIC_MAX_HALOS];
 int fail_static(int code, const char* msg) {
   set_last_error_static(msg);     // a string literal: nothing is allocated
   return code;
+}
+
+// The device error word of this call (bad member indices) into the caller's
+// int, cleared for the next call.
+__global__ void report_error_word(int* word, int32_t* out) {
+  const int e = *word;
+  *out = e ? AHF_ERR_INVALID : AHF_OK;
+  *word = 0;
 }
 
 
@@ -58,7 +67,8 @@ using namespace ahf;
 
 extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                                        const int64_t* member_idx, const ahf_params* prm, ahf_result* out,
-                                       int64_t* bound_idx, void* phi, int32_t* removed_iter, void* stream) {
+                                       int64_t* bound_idx, void* phi, int32_t* removed_iter, int32_t* error_out,
+                                       void* stream) {
   // ---- arguments (no CUDA call before they are known to be valid) ----
   if (!p || !prm) return fail_static(AHF_ERR_INVALID, "particles and params must not be NULL");
   if (n_halos < 0) return fail_static(AHF_ERR_INVALID, "n_halos < 0");
@@ -97,6 +107,16 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
       return fail_static(AHF_ERR_INVALID, "centre and radius must be finite");
   }
   if (n_halos == 0) return AHF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the descriptor copy below reads g_stage, which every later call
+  // overwrites: a captured copy would replay with another call's haloes
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_static(AHF_ERR_CUDA, "cudaStreamIsCapturing failed");
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail_static(AHF_ERR_INVALID, "ahf_unbind_batch_static does not run while its stream is being captured");
 
   std::lock_guard<std::mutex> guard(g_mu);
   // slots must not be shared: order by offset in the fixed index array
@@ -123,7 +143,10 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
       return fail_static(AHF_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
     }
     g_scratch_addr[dev] = a;
+    for (int v = 0; v < 3; ++v) g_grid[dev][v] = onchip_max_grid(v, dev);
   }
+  for (int v = 0; v < 3; ++v)
+    if (g_grid[dev][v] <= 0) return fail_static(AHF_ERR_CUDA, "an on-chip variant cannot run on this device");
   char* scratch = (char*)g_scratch_addr[dev];
   int* counters = (int*)scratch;                                 // [0..2] queues, [8] error word
   HaloDev* hd = (HaloDev*)(scratch + STATIC_COUNTER_BYTES);
@@ -144,7 +167,6 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
     n_class[cls(H.count)]++;
     fill_halo_dev(H, p->coord_type, prm->box, h, g_stage[k]);
   }
-  cudaStream_t s = (cudaStream_t)stream;
   // pageable source: the copy has taken the bytes when the call returns
   if (cudaMemcpyAsync(hd, g_stage, sizeof(HaloDev) * (size_t)n_halos, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(counters, 0, STATIC_COUNTER_BYTES, s) != cudaSuccess) {
@@ -181,13 +203,17 @@ extern "C" int ahf_unbind_batch_static(const ahf_particles* p, const ahf_halo* h
       L.halos = hd + base;
       L.n_halos = n;
       L.queue = counters + v;
-      const int grid = std::min(n, onchip_max_grid(v, dev));
+      const int grid = std::min(n, g_grid[dev][v]);
       if (launch_onchip(L, v, grid, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_static(AHF_ERR_CUDA, "kernel launch failed");
       }
     }
     base += n;
+  }
+  if (error_out) {
+    report_error_word<<<1, 1, 0, s>>>(L.out.err, error_out);
+    if (cudaGetLastError() != cudaSuccess) return fail_static(AHF_ERR_CUDA, "kernel launch failed");
   }
   return AHF_OK;
 }

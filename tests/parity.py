@@ -22,6 +22,17 @@ from oracle import ahf_oracle as O
 
 PHI_RTOL = 1e-5
 VIR_RTOL = 1e-5
+
+
+def fp64_rtol(pop):
+    """Relative tolerance of phi, M_vir and R_vir for the all-FP64 mode.  The
+    GPU's sums there are exact (128-bit fixed point) and rounded once; the
+    oracle's are sequential FP64 sums (np.cumsum), whose relative error is at
+    most (n - 1) u for n positive terms (u = 2^-53; recursive summation).
+    With n the largest candidate count, twice that bound plus a few roundings
+    of the final combination."""
+    n = float(np.max(pop.count)) if len(pop.count) else 1.0
+    return 2.0 * n * 2.0 ** -53 + 1e-14
 # The mixed-precision kernels sort by r = sqrt(fma(dz, dz, fma(dy, dy, dx dx)))
 # in float, each offset d the correctly rounded float of the exact offset.
 # With u = 2^-24: the offsets add at most 2u to r^2, the three roundings of

@@ -1,7 +1,8 @@
 """The 2,000-halo batch at its full size, in the launch configuration bench.py
-times (ahf_unbind_profile_batch, 32 bins from 0.01 r_vir): sampled haloes of
-every size class against the oracle one by one, and properties that hold for
-every halo at any size."""
+times (ahf_unbind_profile_batch, 32 bins from 0.01 r_vir): every halo against
+the oracle (removal iteration of every candidate, bound sets, phi, M_vir,
+R_vir, v_bulk, profile rows), and properties that hold for every halo at any
+size."""
 import math
 
 import numpy as np
@@ -30,7 +31,7 @@ def _sample(counts, per_class=4, seed=7):
     return sorted(set(out))
 
 
-def test_full_batch_sampled():
+def test_full_batch_every_halo():
     torch = require_gpu()
     from paper_0904_3662_gb300 import ahf
     pop = synth.halo_batch(seed=synth.SEED_BASE + 2)
@@ -48,10 +49,11 @@ def test_full_batch_sampled():
     rem = out["removed_iter"].cpu().numpy()
     prof = out["prof"].cpu().numpy()
 
-    sample = _sample(pop.count)
-    assert len(sample) >= 25
-    compare(pop, prm, res, bound, phi, rem, halos=sample)
-    check_profiles(pop, prm, res, prof, N_BINS, R_MIN_FRAC, halos=sample)
+    # every size class is present, and every halo is compared
+    assert len(_sample(pop.count)) >= 25
+    s = compare(pop, prm, res, bound, phi, rem)
+    assert s["halos"] == 2000
+    check_profiles(pop, prm, res, prof, N_BINS, R_MIN_FRAC)
 
     # every halo: record invariants and consistency of the per-slot outputs
     crit = prm.delta_rho * 4.0 * math.pi / 3.0

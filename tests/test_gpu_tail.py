@@ -11,7 +11,7 @@ import pytest
 
 from paper_0904_3662_gb300 import synth
 from tests.gpu_util import require_gpu, run_gpu
-from tests.parity import check_profiles, compare
+from tests.parity import check_profiles, compare, fp64_rtol
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def test_tail_hosts_full_size(tail_pop, mode):
     pop = tail_pop
     assert pop.coord_type == synth.COORD_F32_BOX and pop.box == 5e5
     prec = ahf.PREC_MIXED if mode == "mixed" else ahf.PREC_FP64
-    tol = 1e-5 if mode == "mixed" else 1e-11
+    tol = 1e-5 if mode == "mixed" else fp64_rtol(pop)
     prm = ahf.params_for(pop, precision=prec)
     out, prm, ctx, _ = run_gpu(pop, params=prm)
     st = ctx.stats()
