@@ -54,11 +54,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ahf", "reference"], default="ahf")
-    ap.add_argument("--workload", choices=["batch", "single", "tail", "sweep", "serve", "latency"], default="batch")
+    ap.add_argument("--workload", choices=["batch", "single", "tail", "tail4", "sweep", "serve", "latency"],
+                    default="batch")
     ap.add_argument("--requests", type=int, default=50_000, help="serve workload: requests per rate")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000",
                     help="serve workload: Poisson arrival rates (requests/s)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-halo-per-launch path")
+    ap.add_argument("--no-tune", action="store_true", help="library default routing (no autotuner file)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--properties", action="store_true",
@@ -81,6 +83,10 @@ def make_workload(name, rank):
     elif name == "tail":
         pop = synth.large_tail(seed=synth.SEED_BASE + 3 + 1000 * rank)
         desc = "64 hosts of 1e6-1e7 particles + 20 subhaloes each, float32 box coordinates, 500 Mpc/h box"
+    elif name == "tail4":
+        pop = synth.large_tail(seed=synth.SEED_BASE + 301 + 1000 * rank, counts=[4_000_000, 3_000_000, 2_500_000,
+                                                                                1_500_000])
+        desc = "4 large-tail hosts of 4e6, 3e6, 2.5e6, 1.5e6 particles + 20 subhaloes each (profiling case)"
     else:
         pop = synth.precision_sweep(seed=synth.SEED_BASE + 4 + 1000 * rank)
         desc = "1e5 NFW haloes, N_p ~ N^-1.9 on [1e2, 1e5] + 10% background, float64"
@@ -363,15 +369,16 @@ def run_ahf(args):
     t0 = time.perf_counter()
     pop, desc = make_workload(args.workload, rank)
     log(f"workload {pop.n_halos} haloes / {pop.n_particles} particles in {time.perf_counter() - t0:.1f} s")
-    ctx = ahf.Context(local)
     parts = ahf.particles_from_population(pop)
     hal = ahf.halos_from_population(pop)
     prm = ahf.params_for(pop)
     n_slots = pop.n_particles
-    out = ctx.alloc_outputs(pop.n_halos, n_slots, with_phi=True, with_removed=False)
     prof = torch.empty((pop.n_halos, N_BINS, 4), dtype=torch.float64, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    tuning = ensure_tuning(args, ahf, torch, local, pop, parts, hal, prm, flush)
+    ctx = ahf.Context(local)
+    out = ctx.alloc_outputs(pop.n_halos, n_slots, with_phi=True, with_removed=False)
     ctx.set_option(ahf.OPT_TIMING, 1)
 
     def step():
@@ -470,7 +477,7 @@ def run_ahf(args):
                        "parallelism": f"replicas x{world}, haloes independent, no collective",
                        "launch": "CUDA graph replay (AHF_OPT_GRAPHS)" if args.graphs else "plain launches"},
             "gpu_launches": launches, "roofline": roofline,
-            "timed_wall_s": t_wall}
+            "timed_wall_s": t_wall, "tuning": tuning}
     clocks = clk.summary()
     if clocks:
         clocks["window"] = "the timed steps and the same steps right after them (200 ms sampling)"
@@ -508,6 +515,48 @@ def run_ahf(args):
         print(json.dumps(line))
     barrier(world)
     return 0
+
+
+def ensure_tuning(args, ahf, torch, local, pop, parts, hal, prm, flush):
+    """The routing the step runs with: the autotuner's file for this device
+    and build (paper_0904_3662_gb300/tuning/<device>.txt), made first by a
+    bounded search on this workload when it is missing or stale (the default
+    batch workload only), and handed to the library through AHF_TUNING."""
+    from paper_0904_3662_gb300 import autotune
+    if args.no_tune:
+        os.environ.pop("AHF_TUNING", None)
+        return {"file": None, "options": "library defaults"}
+    key = autotune.device_key(torch.cuda.get_device_name(local))
+    path = autotune.tuning_path(key)
+    build = ahf.build_id()
+    made = False
+    if not autotune.valid_for(path, key, build) and args.workload == "batch":
+        ctx = ahf.Context(local)
+        ctx.set_option(ahf.OPT_GRAPHS, 1)
+        out = ctx.alloc_outputs(pop.n_halos, pop.n_particles, with_phi=True, with_removed=False)
+        prof = torch.empty((pop.n_halos, N_BINS, 4), dtype=torch.float64, device="cuda")
+
+        def step():
+            ctx.unbind_profile_batch(parts, hal, prm, n_bins=N_BINS, r_min_frac=R_MIN_FRAC, out=out, prof=prof)
+
+        t0 = time.perf_counter()
+        cfg, d, t, trials = autotune.tune(ctx, step, ahf, bool(pop.count.max() > ahf.VARIANT_CAPS[-1]), flush,
+                                          budget_s=45.0, log=log)
+        autotune.write(path, key, build, cfg, f"2,000-halo batch; default {d:.4f} ms, tuned {t:.4f} ms, "
+                                              f"{len(trials)} settings timed")
+        log(f"autotune: default {d:.4f} ms, tuned {t:.4f} ms ({len(trials)} settings, "
+            f"{time.perf_counter() - t0:.0f} s)")
+        made = True
+        del ctx
+    if not autotune.valid_for(path, key, build):
+        os.environ.pop("AHF_TUNING", None)
+        return {"file": None, "options": "library defaults (no tuning for this device and build)"}
+    os.environ["AHF_TUNING"] = path
+    t = autotune.read(path)
+    names = {ahf.OPT_PROMOTE: "promote", ahf.OPT_PASS_CHUNK: "pass_chunk"}
+    names.update({ahf.OPT_CLASS_CUT + v: f"class_cut_{ahf.PHASE_NAMES[v]}" for v in range(len(ahf.VARIANT_CAPS))})
+    return {"file": os.path.relpath(path, ROOT), "build": build, "made_in_this_run": made,
+            "options": {names.get(o, str(o)): v for o, v in t["options"].items()}, "note": t["comment"]}
 
 
 def time_properties(ctx, parts, hal, prm, pop, stream, flush, steps=5):
@@ -626,14 +675,16 @@ def run_serve(args):
         parts = ahf.Particles(pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz, None, pop.m0, pop.coord_type)
         hal = ahf.halos_from_population(pop)
         pools.append([ahf.Serve.request(parts, hal[h:h + 1]) for h in range(pop.n_halos)])
-    reqs, k_small, k_big, cand = [], 0, 0, 0
+    reqs, reqs_src, k_small, k_big, cand = [], [], 0, 0, 0
     for b in big:
         if b:
             reqs.append(pools[1][k_big % len(pools[1])])
+            reqs_src.append((large, k_big % large.n_halos))
             cand += int(large.count[k_big % large.n_halos])
             k_big += 1
         else:
             reqs.append(pools[0][k_small % len(pools[0])])
+            reqs_src.append((small, k_small % small.n_halos))
             cand += int(small.count[k_small % small.n_halos])
             k_small += 1
     log(f"serve pool ready in {time.perf_counter() - t0:.1f} s; {len(reqs)} requests, {cand} candidates")
@@ -679,6 +730,7 @@ def run_serve(args):
             f"p50 {st['p50_us']:.0f} us, p99 {st['p99_us']:.0f} us, {st['batches']} batches")
         sweep.append(row)
     srv.close()
+    plain = time_plain_requests(reqs_src, ahf, prm, sweep, t_unit)
     best = max(sweep, key=lambda r: r["throughput"])
     line = {"metric": "requests/s", "value": best["throughput"], "unit": "requests/s", "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64",
@@ -686,9 +738,69 @@ def run_serve(args):
             "config": {"workload": "Poisson stream of one-halo requests, 95% N_p on [100, 1e4), 5% on [1e4, 1e5], "
                                    "+15% contaminants, float32 relative, HBM cap 60 GB",
                        "requests_per_rate": len(reqs), "candidates_per_pass": cand},
-            "sweep": sweep}
+            "sweep": sweep, "plain": plain}
     print(json.dumps(line))
     return 0
+
+
+def time_plain_requests(reqs_src, ahf, prm, sweep, t_unit):
+    """The plain launch-per-request arm on the same request stream: each
+    request alone, from host memory, through the one-halo-per-launch form
+    (ahf_unbind_plain: separate gather / sort / pass kernels, a host wait on
+    every pass's change flag): its candidates copied in from page-locked host
+    memory, the unbinding, its record and bound list copied back.  Every
+    request's service time is measured on the GPU machine back to back (wall
+    clock, a stream synchronisation on both sides); a single FIFO server with
+    those service times then gives each request's latency (completion minus
+    arrival) for the arrival times of every rate of the sweep."""
+    import torch
+    dev = torch.device("cuda")
+    pinned = {}
+    for pop, _ in reqs_src:
+        if id(pop) not in pinned:
+            pinned[id(pop)] = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                               for a in (pop.x, pop.y, pop.z, pop.vx, pop.vy, pop.vz)]
+    nmax = max(int(pop.count[h]) for pop, h in reqs_src)
+    stage = [torch.empty(nmax, dtype=torch.float32, device=dev) for _ in range(6)]
+    ctx = ahf.Context(0)
+    out = ctx.alloc_outputs(1, nmax, with_phi=False, with_removed=False)
+    res_h = torch.empty(ahf.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    bound_h = torch.empty(nmax, dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream()
+    service = np.empty(len(reqs_src))
+    for i, (pop, h) in enumerate(reqs_src):
+        o, n = int(pop.offset[h]), int(pop.count[h])
+        hal = ahf.halos_from_population(pop)[h:h + 1].copy()
+        hal["offset"] = 0
+        src = pinned[id(pop)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a in range(6):
+            stage[a][:n].copy_(src[a][o:o + n], non_blocking=True)
+        parts = ahf.Particles(*[t[:n] for t in stage], None, pop.m0, pop.coord_type)
+        ctx.unbind_batch(parts, hal, prm, out=out, stream=stream, plain=True)
+        res_h.copy_(out["res"], non_blocking=True)
+        bound_h[:n].copy_(out["bound_idx"][:n], non_blocking=True)
+        torch.cuda.synchronize()
+        service[i] = time.perf_counter() - t0
+    rows = []
+    for r in sweep:
+        arr = t_unit / r["rate"]
+        done = 0.0
+        lat = np.empty(len(arr))
+        for i in range(len(arr)):
+            done = max(arr[i], done) + service[i]
+            lat[i] = done - arr[i]
+        rows.append({"rate": r["rate"], "throughput": len(arr) / (done - arr[0]),
+                     "p50_us": float(np.percentile(lat, 50, method="inverted_cdf") * 1e6),
+                     "p99_us": float(np.percentile(lat, 99, method="inverted_cdf") * 1e6)})
+        log(f"plain at {r['rate']:.0f}/s: {rows[-1]['throughput']:.0f} req/s, p50 {rows[-1]['p50_us']:.0f} us, "
+            f"p99 {rows[-1]['p99_us']:.0f} us")
+    return {"api": "ahf_unbind_plain per request, candidates from page-locked host memory, record and bound list "
+                   "copied back", "service_us_mean": float(service.mean() * 1e6),
+            "service_us_p50": float(np.median(service) * 1e6),
+            "latency": "FIFO single server with the measured per-request service times, same arrival stream",
+            "sweep": rows}
 
 
 def run_latency(args):

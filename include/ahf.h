@@ -50,7 +50,7 @@ extern "C" {
 #define AHF_PENDING       1
 #define AHF_ERR_INVALID   (-1)   /* bad argument, size or layout           */
 #define AHF_ERR_NOMEM     (-2)   /* device allocation failed / above a cap */
-/* (-3 is not used: no kernel of the library waits for another CTA)         */
+#define AHF_ERR_TIMEOUT   (-3)   /* a bounded device wait gave up          */
 #define AHF_ERR_CUDA      (-4)   /* a CUDA runtime call failed             */
 #define AHF_ERR_FULL      (-5)   /* serving queue full                     */
 #define AHF_ERR_NOT_FOUND (-6)   /* unknown request id                     */
@@ -167,8 +167,18 @@ const char *ahf_last_error(void);
 
 /* Create a context on CUDA device `device`.  The context owns its device
  * workspace (grown on demand, released by ahf_destroy) and its streams.
- * Errors: AHF_ERR_INVALID (ctx NULL, bad device), AHF_ERR_CUDA. */
+ * Tuning: when the environment variable AHF_TUNING names a file written by
+ * the autotuner (paper_0904_3662_gb300/autotune.py: lines "device <name>",
+ * "build <id>", "option <number> <value>"), its options are applied if its
+ * device name and build id are this device's and ahf_build_id()'s, and
+ * ignored otherwise; ahf_set_option overrides them afterwards.
+ * Errors: AHF_ERR_INVALID (ctx NULL, bad device, a tuning file that does
+ * not parse), AHF_ERR_CUDA. */
 int ahf_create(ahf_ctx **ctx, int device);
+
+/* Identifier of this build of the library (a hash of its sources), which
+ * tuning files are keyed by. */
+const char *ahf_build_id(void);
 
 /* Release the context and its workspace; waits for its work to finish.
  * NULL is accepted. */
@@ -189,8 +199,8 @@ int ahf_destroy(ahf_ctx *ctx);
  * Slots of a halo beyond offset + n_bound are left unspecified in bound_idx
  * and phi.  Errors: AHF_ERR_INVALID (NULL pointers, negative sizes, n_halos
  * of 2^27 or more, slots out of range or shared, bad coord_type/precision/
- * max_iter), AHF_ERR_NOMEM, AHF_ERR_CUDA.  Outputs are undefined after an
- * error. */
+ * max_iter), AHF_ERR_NOMEM, AHF_ERR_CUDA (AHF_ERR_TIMEOUT through ahf_sync).
+ * Outputs are undefined after an error. */
 int ahf_unbind_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halos,
                      int64_t n_halos, const int64_t *member_idx, const ahf_params *prm,
                      ahf_result *out, int64_t *bound_idx, void *phi,
@@ -235,10 +245,11 @@ int ahf_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_halo *halo
 
 /* Wait for the context's enqueued work and report problems the device
  * found while running it: AHF_ERR_INVALID for an out-of-range member index
- * or a halo routed to a class it did not fit.  The device error word is
- * cleared by the call.  No kernel waits for another CTA (the multi-CTA
- * class's look-back reads only sums an earlier kernel finished), so there is
- * no device-side timeout. */
+ * or a halo routed to a class it did not fit, AHF_ERR_TIMEOUT when a warp of
+ * the multi-CTA passes gave up waiting for its tensor copy into shared
+ * memory (AHF_OPT_WAIT_LIMIT; the results of that call are then undefined).
+ * The device error word is cleared by the call.  No kernel waits for
+ * another CTA. */
 int ahf_sync(ahf_ctx *ctx);
 
 /* ahf_unbind_batch and ahf_profile_batch in one call: the same arguments
@@ -258,6 +269,10 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *   AHF_OPT_ONCHIP_MAX   largest candidate count handled in shared memory (by one
  *                        CTA or one thread-block cluster); larger haloes take the
  *                        multi-CTA class (default and maximum 131072)
+ *   AHF_OPT_WAIT_LIMIT   polls a warp of the multi-CTA passes makes of the
+ *                        barrier of its shared-memory tensor copy before it
+ *                        gives up and reports AHF_ERR_TIMEOUT (through
+ *                        ahf_sync); 0 = give up at once.  Default 2^22.
  *   AHF_OPT_TIMING       1 = record CUDA events around every phase of the
  *                        following calls (read with ahf_get_stats), 0 = off
  *   AHF_OPT_GRAPHS       1 = a batch whose haloes all take the on-chip classes
@@ -278,6 +293,20 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        whole batch still runs at once; 0 = every halo in the
  *                        smallest class that holds it.  Results are the same
  *                        bits either way.
+ *   AHF_OPT_PASS_CHUNK   multi-CTA passes enqueued between reads of the count
+ *                        of still-active haloes (1..64, default 8; a pass with
+ *                        nothing left to do returns at once)
+ *   AHF_OPT_WORKSPACE_CAP largest device workspace (bytes) the context may
+ *                        hold; a call that needs more fails with
+ *                        AHF_ERR_NOMEM before enqueuing anything (0, the
+ *                        default: no cap)
+ *   AHF_OPT_CLASS_CUT+v  largest candidate count routed to on-chip variant v
+ *                        (v = 0..7, the phases 0-7 of ahf_stats; 0..its
+ *                        capacity, default the capacity; 0 = none): haloes go
+ *                        to the first variant whose cut holds them, else to
+ *                        the multi-CTA class.  Every routing gives the same
+ *                        results bit for bit (exact sums); only the time
+ *                        changes.  These are the autotuner's knobs.
  *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
  *                        arrays that are page-locked (cudaHostAlloc,
  *                        cudaHostRegister) and write page-locked outputs in
@@ -288,13 +317,16 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        radial order.  Pageable buffers are always staged.
  * Errors: AHF_ERR_INVALID (unknown option or value). */
 #define AHF_OPT_ONCHIP_MAX 1
-/* (option 2 is not used) */
+#define AHF_OPT_WAIT_LIMIT 2
 #define AHF_OPT_TIMING     3
 #define AHF_OPT_HOST_DIRECT 4
 #define AHF_OPT_GRAPHS     5
 #define AHF_OPT_TRACE      6
 #define AHF_OPT_SERIAL     7
 #define AHF_OPT_PROMOTE    8
+#define AHF_OPT_PASS_CHUNK 9
+#define AHF_OPT_WORKSPACE_CAP 10
+#define AHF_OPT_CLASS_CUT  16   /* 16 + v, v = 0..7 */
 
 /* Per-call statistics of the most recent unbinding or profile call.
  * Phases: 0 the warp variant (one warp per halo, 512 slots), 1-3 the
@@ -449,11 +481,14 @@ int ahf_match_catalogs(ahf_ctx *ctx, int64_t n_ids, const int64_t *ids_a, const 
  * request's result is identical to unbinding that halo alone: every halo is
  * computed independently and order-independently.
  *
- * Memory: ring buffers of S candidate slots in pinned host memory and in
- * device memory, S fixed at creation from hbm_cap_bytes (device bytes for the
- * rings, the result records and the context's workspace; S is at most 2^23).
- * A request holds max(count, 1) slots from submission until its batch has
- * completed; slots return in submission order. */
+ * Memory: a request holds candidate slots from submission until its batch
+ * has completed, in two rings.  The device ring is sized from hbm_cap_bytes
+ * (device bytes for the particle state and bound lists of every request in
+ * flight, the result records and the context's workspace): a request that
+ * does not fit in the device memory left is refused with AHF_ERR_FULL.  A
+ * pinned host ring of at most 2^23 slots stages the candidates and takes the
+ * bound lists back; it refuses the same way when full.  A request holds
+ * max(count, 1) slots of each; slots return in submission order. */
 typedef struct ahf_serve ahf_serve;
 
 /* Create a serving instance on `device` with parameters `prm` (copied).

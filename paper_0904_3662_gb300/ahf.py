@@ -19,14 +19,17 @@ LIB_PATH = os.path.join(_HERE, "libahfgpu.so")
 
 # status / codes (values from include/ahf.h)
 OK, PENDING = 0, 1
-ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2, -4, -5, -6
+ERR_INVALID, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_FULL, ERR_NOT_FOUND = -1, -2, -3, -4, -5, -6
 HALO_OK, HALO_NOT_CONVERGED, HALO_EMPTY, HALO_RVIR_BEYOND_EDGE, HALO_RVIR_NONE = 0, 1, 2, 4, 8
 HALO_RISE_EDGE = 16
 COORD_F64, COORD_F32_REL, COORD_F32_BOX = 0, 1, 2
 PREC_MIXED, PREC_FP64 = 0, 1
 VAR_VBULK_INITIAL, VAR_RETRUNCATE, VAR_RISE_EDGE = 1, 2, 4
-OPT_ONCHIP_MAX, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE, OPT_SERIAL = 1, 3, 4, 5, 6, 7
+OPT_ONCHIP_MAX, OPT_WAIT_LIMIT, OPT_TIMING, OPT_HOST_DIRECT, OPT_GRAPHS, OPT_TRACE, OPT_SERIAL = 1, 2, 3, 4, 5, 6, 7
 OPT_PROMOTE = 8
+OPT_PASS_CHUNK = 9
+OPT_WORKSPACE_CAP = 10
+OPT_CLASS_CUT = 16                 # + variant (0..7)
 TRACE_FIELDS = 8
 N_PHASES = 12
 PHASE_NAMES = ("warp_512", "cta_1k", "cta_4k", "cta_8k", "cluster2_16k", "cluster4_32k", "cluster8_64k",
@@ -46,7 +49,7 @@ EXPORTS = ("ahf_version", "ahf_last_error", "ahf_create", "ahf_destroy", "ahf_un
            "ahf_get_option", "ahf_sync", "ahf_get_stats", "ahf_unbind_batch_static", "ahf_unbind_profile_batch",
            "ahf_serve_create", "ahf_serve_submit", "ahf_serve_poll", "ahf_serve_stats", "ahf_serve_counters",
            "ahf_serve_reset_stats", "ahf_serve_destroy", "ahf_get_trace", "ahf_halo_properties",
-           "ahf_match_catalogs", "ahf_unbind_hierarchy")
+           "ahf_match_catalogs", "ahf_unbind_hierarchy", "ahf_build_id")
 PROP_FIELDS = 12
 SERVE_MAX_COUNT = 131072
 STATIC_MAX_HALOS, STATIC_MAX_COUNT = 32768, 8192
@@ -94,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     lib.ahf_version.restype = ctypes.c_int
     lib.ahf_last_error.restype = ctypes.c_char_p
+    lib.ahf_build_id.restype = ctypes.c_char_p
     lib.ahf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     lib.ahf_destroy.argtypes = [vp]
     sig = [vp, ctypes.POINTER(_Particles), vp, i64, vp, ctypes.POINTER(_Params), vp, vp, vp, vp, vp]
@@ -483,6 +487,11 @@ def particles_from_population(pop, device="cuda"):
 
 def halos_from_population(pop):
     return halo_array(pop.centre, pop.radius, pop.offset, pop.count)
+
+
+def build_id() -> str:
+    """The library's build id (a hash of its sources; tuning files are keyed by it)."""
+    return load_library().ahf_build_id().decode()
 
 
 def params_for(pop, **kw):

@@ -8,6 +8,7 @@ linked into paper_0904_3662_gb300/libahfgpu.so.  Objects live in _build/.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -35,6 +36,18 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def source_hash() -> str:
+    """Identifier of the library's sources (the .cu/.cuh/.h files and the
+    public header): the build id tuning files are keyed by."""
+    h = hashlib.sha256()
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files + [os.path.join(INCLUDE, "ahf.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _stale(obj, deps):
     if not os.path.exists(obj):
         return True
@@ -47,13 +60,21 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "ahf.h"))
     nv = nvcc()
+    build_id = source_hash()
+    id_file = os.path.join(BUILD, "build_id.txt")
+    api_obj = os.path.join(BUILD, "ahf_api.o")
+    old_id = open(id_file).read().strip() if os.path.exists(id_file) else ""
+    if old_id != build_id and os.path.exists(api_obj):
+        os.remove(api_obj)                 # the id is compiled into ahf_api.o
+    with open(id_file, "w") as fh:
+        fh.write(build_id + "\n")
     jobs = []
     objs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if _stale(obj, [src] + headers) or ptxas_info:
-            cmd = [nv, *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [nv, *ARCH, *FLAGS, f'-DAHF_BUILD_ID="{build_id}"', "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

@@ -10,6 +10,9 @@
 // persistent CTAs pulling from a device counter (longest-processing-time
 // order), so the biggest halo starts first and the tail is short.
 #include <algorithm>
+#include <cctype>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -22,6 +25,10 @@
 #include "ahf_internal.h"
 
 using namespace ahf;
+
+#ifndef AHF_BUILD_ID
+#define AHF_BUILD_ID "unknown"
+#endif
 
 namespace {
 
@@ -122,6 +129,11 @@ struct ahf_ctx {
   cudaEvent_t last = nullptr;    // end of the previous call's device work
   bool last_valid = false;
   int64_t onchip_max = 16 * 8192;    // largest candidate count of the shared-memory classes
+  int64_t wait_limit = 1 << 22;      // polls of a tensor copy's barrier before a timeout
+  int64_t class_cut[NV] = {-1, -1, -1, -1, -1, -1, -1, -1};  // largest count per on-chip variant (-1: capacity)
+  int pass_chunk = 8;                // multi-CTA passes per read of the active count
+  int64_t ws_cap = 0;                // largest workspace the context may hold (0: no cap)
+  char tuning[512] = {};             // tuning file applied at creation ("" = none)
   std::mutex mu;
   // pinned staging for host descriptors: a ring of slots, each released by
   // an event after the copies that read it, so a call never waits for the
@@ -161,6 +173,7 @@ struct ahf_ctx {
   cudaEvent_t join[NV] = {};
   int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
   int iter_grid[2] = {-1, -1};       // CTAs of the multi-CTA pass (mixed, FP64; -1: not queried)
+  int tma_grid = -1;                 // CTAs of the pass with tensor copies (-1: not queried)
 };
 
 namespace {
@@ -196,11 +209,15 @@ int pin_release(ahf_ctx* c, cudaStream_t s) {
 
 int ensure_workspace(ahf_ctx* c, size_t bytes) {
   if (bytes <= c->ws_bytes) return AHF_OK;
+  if (c->ws_cap > 0 && bytes > (size_t)c->ws_cap)
+    return fail(AHF_ERR_NOMEM, "the call needs %zu bytes of workspace, above the cap of %lld", bytes,
+                (long long)c->ws_cap);
   if (c->last_valid) AHF_CUDA(cudaEventSynchronize(c->last));
   if (c->ws) cudaFree(c->ws);
   c->ws = nullptr;
   c->ws_bytes = 0;
   size_t want = std::max(align_up(bytes + bytes / 8, 1 << 20), (size_t)1 << 22);
+  if (c->ws_cap > 0) want = std::max(bytes, std::min(want, (size_t)c->ws_cap));
   if (cudaMalloc(&c->ws, want) != cudaSuccess) {
     cudaGetLastError();
     return fail(AHF_ERR_NOMEM, "device workspace of %zu bytes", want);
@@ -336,6 +353,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   for (int v = 0; v < NV; ++v) {
     if (c->variant_grid[v] < 0) c->variant_grid[v] = variant_max_grid(v, c->device);
     caps[v] = c->variant_grid[v] > 0 ? (int)std::min<int64_t>(variant_capacity(v), c->onchip_max) : 0;
+    if (c->class_cut[v] >= 0) caps[v] = (int)std::min<int64_t>(caps[v], c->class_cut[v]);
   }
   std::vector<int> cls((size_t)n_halos);
   for (int64_t h = 0; h < n_halos; ++h) {
@@ -345,7 +363,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     // multi-CTA class only
     if (prm->precision == AHF_PREC_MIXED && !p->u_th)
       for (int v = 0; v < NV; ++v)
-        if (n <= caps[v]) { k = v; break; }
+        if (caps[v] > 0 && n <= caps[v]) { k = v; break; }
     cls[h] = k;
   }
   // latency: a batch that leaves SMs idle moves its haloes to larger classes
@@ -395,7 +413,8 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     const ahf_halo& H = halos[h];
     HaloDev& d = P.hd[k];
     fill_halo_dev(H, p->coord_type, prm->box, h, d);
-    if (cls[h] == NV) { d.gbase = gbase; gbase += H.count; }
+    // multi-CTA haloes start on 8-element rows (the passes' tensor copies)
+    if (cls[h] == NV) { d.gbase = gbase; gbase = (gbase + H.count + 7) & ~7ll; }
     else { d.gbase = rbase; rbase += H.count; }
   }
   P.grid_flat = gbase;
@@ -485,6 +504,7 @@ void grid_take(Bump& B, GridLaunch* G, const GridSizes& z) {
   char* prr = B.take<char>((size_t)z.n_tiles * as);
   long long* prc = B.take<long long>((size_t)z.n_tiles);
   int4* work = B.take<int4>(2 * n_sub);
+  uint8_t* rmask = B.take<uint8_t>(32 * n_sub);
   AccSlot* tmv = B.take<AccSlot>(3 * (size_t)z.n_tiles);
   if (!G) return;
   G->state = st; G->ctl = ctl; G->rec = rec; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb;
@@ -493,6 +513,7 @@ void grid_take(Bump& B, GridLaunch* G, const GridSizes& z) {
   G->n_big = z.n_big; G->tile_hist = hist; G->digit_base = dbase;
   G->agg_m = agm; G->agg_r = agr; G->agg_c = agc; G->pre_m = prm_; G->pre_r = prr; G->pre_c = prc;
   G->work = work;
+  G->rem_mask = rmask;
   G->tile_mv = tmv; G->max_halo_tiles = z.max_halo_tiles; G->n_halos = z.n_grid; G->n_flat = (long long)z.nf; G->n_tiles = z.n_tiles;
   G->fp64 = z.fp64 ? 1 : 0;
 }
@@ -519,6 +540,15 @@ int grid_pass_ctas(ahf_ctx* c, bool fp64) {
 // do returns at once).
 int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s, int chunk) {
   int rc;
+  // the passes stage the stream through tensor copies (mixed mode, a uniform
+  // mass, no gas) when the device takes them
+  G.wait_limit = c->wait_limit;
+  G.use_tma = 0;
+  if (!G.fp64 && !G.ms && !G.uth) {
+    if (c->tma_grid < 0) c->tma_grid = grid_tma_grid(c->device);
+    G.tma_grid = c->tma_grid;
+    if (G.tma_grid > 0 && grid_wr_map(G, (G.n_flat + 7) / 8)) G.use_tma = 1;
+  }
   AHF_CUDA(cudaMemcpyAsync(c->flag_host, &G.ctl->key_or, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   AHF_CUDA(cudaStreamSynchronize(s));
   c->stats.host_syncs += 1;
@@ -533,7 +563,7 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s, i
     const int n = std::min(chunk, prm->max_iter - pass + 1);
     for (int i = 0; i < n; ++i) {
       AHF_CUDA(grid_iterate(G, pass++, s));
-      c->stats.launches += 2;
+      c->stats.launches += 3;
       c->stats.grid_iterations += 1;
     }
     if (pass > prm->max_iter) break;
@@ -828,7 +858,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   } else {
     if ((rc = enqueue_onchip(s, false))) return rc;
     if (n_grid) {
-      if ((rc = run_grid(c, G, prm, s, 8))) return rc;
+      if ((rc = run_grid(c, G, prm, s, c->pass_chunk))) return rc;
     }
     if (!c->serial)
       for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
@@ -979,7 +1009,7 @@ int plain_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_
   if ((rc = make_plan(c, p, halos, n_halos, prm, P))) return rc;
   long long maxc = 1;
   for (const HaloDev& d : P.hd) maxc = std::max(maxc, d.count);
-  const size_t nf = (size_t)maxc;
+  const size_t nf = (size_t)((maxc + 7) & ~7ll);
   const int max_tiles = (int)((maxc + GRID_TILE - 1) / GRID_TILE);
   GridSizes gz;
   gz.nf = nf; gz.n_tiles = max_tiles; gz.n_grid = 1; gz.n_big = max_tiles > 256 ? 1 : 0;
@@ -1449,6 +1479,64 @@ int ahf_version(void) { return 100; }
 
 const char* ahf_last_error(void) { return g_last_ptr; }
 
+const char* ahf_build_id(void) { return AHF_BUILD_ID; }
+
+namespace {
+
+// The device's name with every character outside [A-Za-z0-9._-] as '_'.
+void device_key(int device, char* out, size_t cap) {
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof prop);
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    std::snprintf(out, cap, "unknown");
+    return;
+  }
+  size_t k = 0;
+  for (const char* p = prop.name; *p && k + 1 < cap; ++p)
+    out[k++] = (std::isalnum((unsigned char)*p) || *p == '.' || *p == '-' || *p == '_') ? *p : '_';
+  out[k] = 0;
+}
+
+// Tuned options from the file named by the environment variable AHF_TUNING
+// (lines "device <key>", "build <id>", "option <number> <value>"; '#'
+// comments).  The options are applied only when the device key and the
+// build id match this device and this library; otherwise the file is
+// ignored.  A file that does not parse is an error.
+int apply_tuning(ahf_ctx* c) {
+  const char* path = std::getenv("AHF_TUNING");
+  if (!path || !*path) return AHF_OK;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return AHF_OK;                     // no tuning yet
+  char key[256];
+  device_key(c->device, key, sizeof key);
+  char line[512], dev[256] = {}, build[128] = {};
+  std::vector<std::pair<int, long long>> opts;
+  int rc = AHF_OK;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int opt = 0;
+    long long val = 0;
+    char word[256];
+    if (std::sscanf(line, "device %255s", word) == 1) std::snprintf(dev, sizeof dev, "%s", word);
+    else if (std::sscanf(line, "build %127s", word) == 1) std::snprintf(build, sizeof build, "%s", word);
+    else if (std::sscanf(line, "option %d %lld", &opt, &val) == 2) opts.emplace_back(opt, val);
+    else if (std::sscanf(line, "%255s", word) == 1 && word[0] != '#') {
+      rc = fail(AHF_ERR_INVALID, "tuning file %s: cannot read '%s'", path, word);
+      break;
+    }
+  }
+  std::fclose(f);
+  if (rc != AHF_OK) return rc;
+  if (std::strcmp(dev, key) != 0 || std::strcmp(build, AHF_BUILD_ID) != 0) return AHF_OK;
+  for (const auto& o : opts)
+    if ((rc = ahf_set_option(c, o.first, o.second)) != AHF_OK) return rc;
+  std::snprintf(c->tuning, sizeof c->tuning, "%s", path);
+  return AHF_OK;
+}
+
+}  // namespace
+
 int ahf_create(ahf_ctx** ctx, int device) {
   if (!ctx) return fail(AHF_ERR_INVALID, "ctx is NULL");
   *ctx = nullptr;
@@ -1496,6 +1584,10 @@ int ahf_create(ahf_ctx** ctx, int device) {
     ahf_destroy(c);
     return rc;
   }
+  if ((rc = apply_tuning(c)) != AHF_OK) {
+    ahf_destroy(c);
+    return rc;
+  }
   *ctx = c;
   return AHF_OK;
 }
@@ -1540,6 +1632,10 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value < 0 || value > variant_capacity(NV - 1)) return fail(AHF_ERR_INVALID, "onchip max out of range");
       c->onchip_max = value;
       return AHF_OK;
+    case AHF_OPT_WAIT_LIMIT:
+      if (value < 0) return fail(AHF_ERR_INVALID, "wait limit < 0");
+      c->wait_limit = value;
+      return AHF_OK;
     case AHF_OPT_TIMING:
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "timing is 0 or 1");
       c->timing = value == 1;
@@ -1564,7 +1660,22 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "promote is 0 or 1");
       c->promote = value == 1;
       return AHF_OK;
+    case AHF_OPT_PASS_CHUNK:
+      if (value < 1 || value > 64) return fail(AHF_ERR_INVALID, "pass chunk must be in [1, 64]");
+      c->pass_chunk = (int)value;
+      return AHF_OK;
+    case AHF_OPT_WORKSPACE_CAP:
+      if (value < 0) return fail(AHF_ERR_INVALID, "workspace cap < 0");
+      c->ws_cap = value;
+      return AHF_OK;
     default:
+      if (option >= AHF_OPT_CLASS_CUT && option < AHF_OPT_CLASS_CUT + NV) {
+        const int v = option - AHF_OPT_CLASS_CUT;
+        if (value < 0 || value > variant_capacity(v))
+          return fail(AHF_ERR_INVALID, "class cut of variant %d must be in [0, %d]", v, variant_capacity(v));
+        c->class_cut[v] = value;
+        return AHF_OK;
+      }
       return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }
@@ -1573,13 +1684,22 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
   if (!c || !value) return fail(AHF_ERR_INVALID, "NULL argument");
   switch (option) {
     case AHF_OPT_ONCHIP_MAX: *value = c->onchip_max; return AHF_OK;
+    case AHF_OPT_WAIT_LIMIT: *value = c->wait_limit; return AHF_OK;
     case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
     case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
     case AHF_OPT_TRACE: *value = c->trace ? 1 : 0; return AHF_OK;
     case AHF_OPT_SERIAL: *value = c->serial ? 1 : 0; return AHF_OK;
     case AHF_OPT_PROMOTE: *value = c->promote ? 1 : 0; return AHF_OK;
-    default: return fail(AHF_ERR_INVALID, "unknown option %d", option);
+    case AHF_OPT_PASS_CHUNK: *value = c->pass_chunk; return AHF_OK;
+    case AHF_OPT_WORKSPACE_CAP: *value = c->ws_cap; return AHF_OK;
+    default:
+      if (option >= AHF_OPT_CLASS_CUT && option < AHF_OPT_CLASS_CUT + NV) {
+        const int v = option - AHF_OPT_CLASS_CUT;
+        *value = c->class_cut[v] >= 0 ? c->class_cut[v] : variant_capacity(v);
+        return AHF_OK;
+      }
+      return fail(AHF_ERR_INVALID, "unknown option %d", option);
   }
 }
 
@@ -1591,6 +1711,7 @@ int ahf_sync(ahf_ctx* c) {
   AHF_CUDA(cudaMemcpy(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
   const int e = *c->err_host;
   if (e) AHF_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+  if (e & ERR_TIMEOUT) return fail(AHF_ERR_TIMEOUT, "a multi-CTA pass gave up waiting for a tensor copy");
   if (e & ERR_BAD_INDEX) return fail(AHF_ERR_INVALID, "a member index was out of range");
   if (e & ERR_CAPACITY) return fail(AHF_ERR_INVALID, "a halo exceeded its size class");
   if (e & ERR_ID_RANGE) return fail(AHF_ERR_INVALID, "a catalogue particle id was out of range");

@@ -34,6 +34,7 @@
 // Exact sums: long long fixed point in the mixed mode (the same scales and
 // bits as the on-chip classes), __int128 in the all-FP64 mode, where a
 // 64-bit quantum would limit large haloes to ~1e-11 relative in sum m/r.
+#include <atomic>
 #include <cstdint>
 
 #include "ahf_device.cuh"
@@ -765,6 +766,11 @@ constexpr int ROWS = SUB / 32;          // 8
 constexpr int HT_BIG = 1024;            // threads of the per-halo kernel (largest halo > 64 tiles)
 constexpr int HT_SMALL = 256;           // (otherwise)
 
+// True once a pass of this call gave up waiting for a tensor copy: the
+// sums it left are incomplete, so every later kernel of the class skips its
+// work (the call's outputs are undefined and ahf_sync reports the timeout).
+__device__ __forceinline__ bool gave_up(const GridLaunch& L) { return (__ldcg(L.out.err) & ERR_TIMEOUT) != 0; }
+
 // Atomic add of an exact sum into a slot (the __int128 one from two 64-bit
 // atomics: the low word's carry goes into the high word, so the total is
 // exact once every addition has landed).
@@ -802,6 +808,12 @@ __device__ __forceinline__ float fix_to_real(long long v, int s, float sc, float
   return fmaf(hi, 4294967296.0f, lo) * sc;
 }
 __device__ __forceinline__ double fix_to_real(__int128 v, int s, float, double) { return double_from_fix128(v, s); }
+// float_from_fix when 2^-s is the normal float sc (no other route compiled in)
+__device__ __forceinline__ float fix_to_float_sc(long long v, float sc) {
+  const float hi = (float)(int)(v >> 32);
+  const float lo = (float)(unsigned)(v & 0xffffffffll);
+  return fmaf(hi, 4294967296.0f, lo) * sc;
+}
 __device__ __forceinline__ float pow2_neg(int s) {
   return (s >= -127 && s <= 126) ? __int_as_float((127 - s) << 23) : 0.0f;
 }
@@ -859,6 +871,7 @@ __global__ void __launch_bounds__(T) g_sums(GridLaunch L) {
 // The sub-tiles of the haloes still active are listed for the next pass.
 template <typename R, bool INIT, int HT>
 __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
+  if (gave_up(L)) return;
   using Acc = typename Prec<R>::Acc;
   constexpr int CH = 1024;                 // tiles per chunk held in shared memory
   constexpr int NW = HT / 32;
@@ -889,17 +902,26 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
   long long cc = 0;
   for (int c0 = t0; c0 < t1; c0 += CH) {
     const int cn = min(CH, t1 - c0);
-    // tile sums, SPT lanes per tile (coalesced), reduced by shuffles
-    for (int x0 = 0; x0 < cn * SPT; x0 += HT) {
-      const int x = x0 + threadIdx.x;
+    // tile sums, SPT lanes per tile (coalesced), reduced by shuffles; the
+    // chunk's loads (CH * SPT / HT per thread) go out together
+    constexpr int LPT = 8;
+    for (int xr = 0; xr < cn * SPT; xr += LPT * HT) {
+    Acc lm[LPT], lr[LPT];
+    int lc[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+      const int x = xr + q * HT + threadIdx.x;
       const int u = c0 * SPT + x;
-      Acc m = 0, r = 0;
-      long long c = 0;
-      if (x < cn * SPT && u < u_end) {
-        m = am[u];
-        r = ar[u];
-        c = ac[u];
-      }
+      const bool in = x < cn * SPT && u < u_end;
+      lm[q] = in ? am[u] : (Acc)0;
+      lr[q] = in ? ar[u] : (Acc)0;
+      lc[q] = in ? ac[u] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+      const int x = xr + q * HT + threadIdx.x;
+      Acc m = lm[q], r = lr[q];
+      int c = lc[q];
 #pragma unroll
       for (int o = 1; o < SPT; o <<= 1) {
         m += shfl_xor_x(m, o);
@@ -911,6 +933,7 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
         tr_[x / SPT] = r;
         tc_[x / SPT] = c;
       }
+    }
     }
     __syncthreads();
     // exclusive scan of the chunk's tile sums: a run of consecutive tiles per thread
@@ -1050,24 +1073,27 @@ __device__ __forceinline__ void sub_prefix(const GridLaunch& L, int u, int t, in
   if (C) *C = L.pre_c[t] + __reduce_add_sync(FULL_MASK, c);
 }
 
-// Phi, escape test and removal over sub-tile u (tile t, halo k) in pass
-// `pass`, by one warp: lane l holds elements [8 l, 8 l + 8) of the sub-tile;
-// one warp scan of the lanes' sums places every element's prefix.
-template <typename R, bool UNIF, bool GAS>
+// Phi and the escape test over sub-tile w.x (halo w.y) in pass `pass`, by
+// one warp: lane l holds elements [8 l, 8 l + 8) of the sub-tile; one warp
+// scan of the lanes' sums places every element's prefix.  The pass only
+// decides: it leaves the sub-tile's sums after the removals for the next
+// pass and one byte of removal flags per lane; g_removed does the rest.
+// FAST: the scales 2^-s of the halo are normal floats (the conversions of
+// the exact sums to float are then a multiply; same bits).
+template <typename R, bool UNIF, bool GAS, bool FAST>
 __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int pass) {
   using V4 = typename Prec<R>::V4;
   using Acc = typename Prec<R>::Acc;
   const int u = w.x, k = w.y, t = u / SPT;
   GridHaloState& S = L.state[k];
   const int lane = threadIdx.x & 31;
-  const HaloDev& H = L.halos[k];
-  const int s_m = S.s_m, s_r = S.s_mr, s_v = S.s_mv;
+  const int s_m = S.s_m, s_r = S.s_mr;
   const ParamsDev& P = L.prm;
   const int n_sub = L.n_tiles * SPT;
   const int cp = pass & 1;
   const long long gl = (long long)w.z + lane * EPL;   // the lane's first element
   const int nl = w.w - lane * EPL;                    // its members (<= 0: none)
-  V4* wr = (V4*)L.wr;
+  const V4* wr = (const V4*)L.wr;
   const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
   // the lane's elements, all in flight at once
   V4 q[EPL];
@@ -1093,8 +1119,8 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
   for (int a = 0; a < 3; ++a) vb[a] = sizeof(R) == 4 ? (R)S.vbulk[a] : (R)S.vbulk_d[a];
   const R band = sizeof(R) == 4 ? (R)P.band_f : (R)P.band;
   const Acc Ttot = Ald<Acc>(S.t_tot);
-  const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
-  const Acc mfix0 = fixr(m0, s_m);
+  const float sc_m = FAST ? pow2_neg(s_m) : 0.0f, sc_r = FAST ? pow2_neg(s_r) : 0.0f;
+  const Acc mfix0 = fixp(m0, s_m);
   // per element: 1/r and the exact terms; the lane's sums
   R ri[EPL];
   Acc rf[EPL];
@@ -1113,65 +1139,46 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
   const size_t jc = (size_t)cp * n_sub + u;
   const Acc n_m = ((const Acc*)L.agg_m)[jc], n_r = ((const Acc*)L.agg_r)[jc];
   const int n_c = L.agg_c[jc];
-  // phi and the escape test; the removed only marked here
+  // phi and the escape test
   unsigned rem = 0;
   int nband = 0;
+  Acc rm = 0, rr = 0;
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const R r = q[i].w;
     if (!signbit(r)) {
       const Acc mfix = UNIF ? mfix0 : fixp(mq[i], s_m);
-      const R phi = phi_real(fix_to_real(M, s_m, sc_m, R()), ri[i], fix_to_real(Ttot - Pp, s_r, sc_r, R()), P);
+      const R Mf = (FAST && sizeof(R) == 4) ? (R)fix_to_float_sc((long long)M, sc_m) : from_fix(M, s_m, R());
+      const R Sf = (FAST && sizeof(R) == 4) ? (R)fix_to_float_sc((long long)(Ttot - Pp), sc_r)
+                                            : from_fix(Ttot - Pp, s_r, R());
+      const R phi = phi_real(Mf, ri[i], Sf, P);
       const R ux = q[i].x - vb[0], uy = q[i].y - vb[1], uz = q[i].z - vb[2];
       R u2 = fma_x(uz, uz, fma_x(uy, uy, ux * ux));
       if (GAS) u2 += (R)2 * uq[i];                 // gas: |u|^2 + 2 u_th (Sect. 2.1)
       const R two_phi = (R)-2 * phi;
       if (fabs(u2 - two_phi) < band * two_phi) ++nband;
-      if (u2 > two_phi) rem |= 1u << i;
+      if (u2 > two_phi) {
+        rem |= 1u << i;
+        rm += mfix;
+        rr += rf[i];
+      }
       M += mfix;
       Pp += rf[i];
     }
   }
-  // the removed: mark (sign bit of r), removal iteration, exact sums of
-  // what goes (m, m/r, m v with v from the candidate's record)
-  Acc rm = 0, rr = 0, rmv0 = 0, rmv1 = 0, rmv2 = 0;
-  const int nrem_l = __popc(rem);
-  const V4* rec = (const V4*)L.rec;
-#pragma unroll
-  for (int i = 0; i < EPL; ++i) {
-    if (!(rem & (1u << i))) continue;
-    const long long g = gl + i;
-    const R r = q[i].w, m = mq[i];
-    wr[g].w = -r;
-    const uint32_t pos = L.val_x[g];
-    if (L.out.removed_iter) L.out.removed_iter[H.offset + pos] = pass;
-    const V4 vm = rec[2 * (H.gbase + pos) + 1];    // (v, m) of the candidate
-    rm += UNIF ? mfix0 : fixp(m, s_m);
-    rr += rf[i];
-    rmv0 += fixr(mul_rn(m, vm.x), s_v);
-    rmv1 += fixr(mul_rn(m, vm.y), s_v);
-    rmv2 += fixr(mul_rn(m, vm.z), s_v);
-  }
-  // the sub-tile's sums after the removals (next copy); what it removed goes to the halo
-  const int nrem = __reduce_add_sync(FULL_MASK, nrem_l);
+  // the sub-tile's sums after the removals (next copy) and its removal flags
+  const int nrem = __reduce_add_sync(FULL_MASK, __popc(rem));
   nband = __reduce_add_sync(FULL_MASK, nband);
+  L.rem_mask[(size_t)u * 32 + lane] = (uint8_t)rem;
   if (nrem) {                                      // uniform over the warp
     rm = wsum(rm);
     rr = wsum(rr);
-    rmv0 = wsum(rmv0);
-    rmv1 = wsum(rmv1);
-    rmv2 = wsum(rmv2);
   }
   if (lane == 0) {
     const size_t j = (size_t)(cp ^ 1) * n_sub + u;
     ((Acc*)L.agg_m)[j] = n_m - rm;
     ((Acc*)L.agg_r)[j] = n_r - rr;
     L.agg_c[j] = n_c - nrem;
-    if (nrem) {
-      atomic_acc(S.rem_mv[0], rmv0);
-      atomic_acc(S.rem_mv[1], rmv1);
-      atomic_acc(S.rem_mv[2], rmv2);
-    }
     if (nband) atomicAdd((unsigned long long*)&S.band_pass, (unsigned long long)nband);
   }
 }
@@ -1181,10 +1188,252 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
 template <typename R, bool UNIF, bool GAS>
 __global__ void __launch_bounds__(T, sizeof(R) == 4 ? 2 : 1) g_pass(GridLaunch L, int pass) {
   if (blockIdx.x == 0 && threadIdx.x == 0) L.ctl->work_n[(pass + 1) & 1] = 0;
+  if (gave_up(L)) return;
   const int n = __ldcg(&L.ctl->work_n[pass & 1]);
   const int4* list = L.work + (size_t)(pass & 1) * L.n_tiles * SPT;
-  for (int i = (blockIdx.x * T + threadIdx.x) >> 5; i < n; i += (gridDim.x * T) >> 5)
-    pass_sub<R, UNIF, GAS>(L, list[i], pass);
+  for (int i = (blockIdx.x * T + threadIdx.x) >> 5; i < n; i += (gridDim.x * T) >> 5) {
+    const int4 w = list[i];
+    const GridHaloState& S = L.state[w.y];
+    if (sizeof(R) == 4 && pow2_neg(S.s_m) != 0.0f && pow2_neg(S.s_mr) != 0.0f)
+      pass_sub<R, UNIF, GAS, true>(L, w, pass);
+    else
+      pass_sub<R, UNIF, GAS, false>(L, w, pass);
+  }
+}
+
+// After a pass, the particles it removed (the flags of the listed sub-tiles):
+// the sign bit of r, their removal iteration, and the exact sum m v of what
+// each halo lost (v from the candidate's record), one warp per sub-tile.
+template <typename R, bool UNIF>
+__global__ void __launch_bounds__(T) g_removed(GridLaunch L, int pass) {
+  if (gave_up(L)) return;
+  using V4 = typename Prec<R>::V4;
+  using Acc = typename Prec<R>::Acc;
+  const int lane = threadIdx.x & 31;
+  const int n = __ldcg(&L.ctl->work_n[pass & 1]);
+  const int4* list = L.work + (size_t)(pass & 1) * L.n_tiles * SPT;
+  V4* wr = (V4*)L.wr;
+  const V4* rec = (const V4*)L.rec;
+  const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
+  // 32 listed sub-tiles per step: lane j checks entry i0 + j's flags (32
+  // bytes), then the warp takes the flagged ones one after another
+  const int nwarps = (gridDim.x * T) >> 5;
+  for (int i0 = ((blockIdx.x * T + threadIdx.x) >> 5) * 32; i0 < n; i0 += nwarps * 32) {
+    const int ij = i0 + lane;
+    int4 wj = make_int4(0, 0, 0, 0);
+    bool any = false;
+    if (ij < n) {
+      wj = list[ij];
+      const uint4* mk = (const uint4*)(L.rem_mask + (size_t)wj.x * 32);
+      const uint4 m0 = mk[0], m1 = mk[1];
+      any = (m0.x | m0.y | m0.z | m0.w | m1.x | m1.y | m1.z | m1.w) != 0u;
+    }
+    unsigned todo = __ballot_sync(FULL_MASK, any);
+    while (todo) {
+    const int jj = __ffs(todo) - 1;
+    todo &= todo - 1;
+    int4 w;
+    w.x = __shfl_sync(FULL_MASK, wj.x, jj);
+    w.y = __shfl_sync(FULL_MASK, wj.y, jj);
+    w.z = __shfl_sync(FULL_MASK, wj.z, jj);
+    w.w = __shfl_sync(FULL_MASK, wj.w, jj);
+    unsigned rem = L.rem_mask[(size_t)w.x * 32 + lane];
+    GridHaloState& S = L.state[w.y];
+    const HaloDev& H = L.halos[w.y];
+    const int s_v = S.s_mv;
+    Acc mv0 = 0, mv1 = 0, mv2 = 0;
+    while (rem) {
+      const int e = __ffs(rem) - 1;
+      rem &= rem - 1;
+      const long long g = (long long)w.z + lane * EPL + e;
+      // removed: the sign bit of r, set without reading r
+      if (sizeof(R) == 4) atomicOr((unsigned*)&wr[g].w, 0x80000000u);
+      else atomicOr((unsigned long long*)&wr[g].w, 0x8000000000000000ull);
+      const uint32_t pos = L.val_x[g];
+      if (L.out.removed_iter) L.out.removed_iter[H.offset + pos] = pass;
+      const V4 vm = rec[2 * (H.gbase + pos) + 1];  // (v, m) of the candidate
+      const R m = UNIF ? m0 : ((const R*)L.ms)[g];
+      mv0 += fixr(mul_rn(m, vm.x), s_v);
+      mv1 += fixr(mul_rn(m, vm.y), s_v);
+      mv2 += fixr(mul_rn(m, vm.z), s_v);
+    }
+    mv0 = wsum(mv0);
+    mv1 = wsum(mv1);
+    mv2 = wsum(mv2);
+    if (lane == 0) {
+      atomic_acc(S.rem_mv[0], mv0);
+      atomic_acc(S.rem_mv[1], mv1);
+      atomic_acc(S.rem_mv[2], mv2);
+    }
+    }
+  }
+}
+
+// ---- the pass with tensor copies into shared memory (mixed mode) -----------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// One 4 KB box (32 rows of 8 elements) of the stream into dst; bar counts it.
+__device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int row, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 4096;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(0), "r"(row), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Wait for a barrier phase with at most `limit` polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long limit) {
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_test(bar, phase)) return true;
+  return false;
+}
+constexpr long long DRAIN_POLLS = 1ll << 24;   // a warp that gave up still lets its copies land
+
+// Element i of lane `lane` of a box copied with the 128-byte swizzle: row
+// `lane`, 16-byte chunk i stored at chunk i ^ (lane & 7).
+__device__ __forceinline__ float4 box_at(const float4* box, int lane, int i) { return box[lane * 8 + (i ^ (lane & 7))]; }
+
+// One sub-tile from its box in shared memory (the mixed mode, a uniform
+// particle mass, no gas): the arithmetic of pass_sub.
+template <bool FAST>
+__device__ __forceinline__ void pass_box(const GridLaunch& L, const int4 w, int pass, const float4* box) {
+  using Acc = long long;
+  const int u = w.x, k = w.y, t = u / SPT;
+  GridHaloState& S = L.state[k];
+  const int lane = threadIdx.x & 31;
+  const int s_m = S.s_m, s_r = S.s_mr;
+  const ParamsDev& P = L.prm;
+  const int n_sub = L.n_tiles * SPT;
+  const int cp = pass & 1;
+  const int nl = w.w - lane * EPL;                    // the lane's members (<= 0: none)
+  Acc M, Pp;
+  sub_prefix<Acc>(L, u, t, cp, M, Pp, nullptr);
+  const float vb0 = S.vbulk[0], vb1 = S.vbulk[1], vb2 = S.vbulk[2];
+  const float band = P.band_f;
+  const Acc Ttot = Ald<Acc>(S.t_tot);
+  const float sc_m = FAST ? pow2_neg(s_m) : 0.0f, sc_r = FAST ? pow2_neg(s_r) : 0.0f;
+  const float m0 = L.p.m0f;
+  const Acc mfix0 = fixp(m0, s_m);
+  float ri[EPL];
+  Acc rf[EPL];
+  Acc a = 0, b = 0;
+  unsigned alive = 0;
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    const float r = box_at(box, lane, i).w;
+    const bool al = i < nl && !signbit(r);
+    alive |= (al ? 1u : 0u) << i;
+    ri[i] = rinv_real(r, P);
+    rf[i] = al ? fixp(m0 * ri[i], s_r) : 0ll;
+    a += al ? mfix0 : 0ll;
+    b += rf[i];
+  }
+  const Acc ia = wscan(a, lane), ib = wscan(b, lane);
+  M += ia - a;
+  Pp += ib - b;
+  const size_t jc = (size_t)cp * n_sub + u;
+  const Acc n_m = ((const Acc*)L.agg_m)[jc], n_r = ((const Acc*)L.agg_r)[jc];
+  const int n_c = L.agg_c[jc];
+  unsigned rem = 0;
+  int nband = 0;
+  Acc rr = 0;
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    if (alive & (1u << i)) {
+      const float4 q = box_at(box, lane, i);
+      const float Mf = FAST ? fix_to_float_sc(M, sc_m) : float_from_fix(M, s_m);
+      const float Sf = FAST ? fix_to_float_sc(Ttot - Pp, sc_r) : float_from_fix(Ttot - Pp, s_r);
+      const float phi = phi_of(Mf, ri[i], Sf, P.Gf);
+      const float ux = q.x - vb0, uy = q.y - vb1, uz = q.z - vb2;
+      const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+      const float two_phi = -2.0f * phi;
+      if (fabsf(u2 - two_phi) < band * two_phi) ++nband;
+      if (u2 > two_phi) {
+        rem |= 1u << i;
+        rr += rf[i];
+      }
+      M += mfix0;
+      Pp += rf[i];
+    }
+  }
+  const int nrem = __reduce_add_sync(FULL_MASK, __popc(rem));
+  nband = __reduce_add_sync(FULL_MASK, nband);
+  L.rem_mask[(size_t)u * 32 + lane] = (uint8_t)rem;
+  if (nrem) rr = wsum(rr);
+  if (lane == 0) {
+    const size_t j = (size_t)(cp ^ 1) * n_sub + u;
+    ((Acc*)L.agg_m)[j] = n_m - (Acc)nrem * mfix0;
+    ((Acc*)L.agg_r)[j] = n_r - rr;
+    L.agg_c[j] = n_c - nrem;
+    if (nband) atomicAdd((unsigned long long*)&S.band_pass, (unsigned long long)nband);
+  }
+}
+
+// One pass with the sub-tiles streamed into shared memory by tensor copies:
+// each warp keeps two 4 KB boxes, fetching its next sub-tile while it
+// computes the current one.  Waits are bounded by L.wait_limit polls; a warp
+// that gives up sets ERR_TIMEOUT, lets its copies land and stops.
+constexpr int TMA_SMEM = NWARP * 2 * 4096 + NWARP * 2 * 8;
+__global__ void __launch_bounds__(T, 3) g_pass_tma(const __grid_constant__ GridLaunch L, int pass) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* box0 = (float4*)(smem + warp * 8192);
+  uint64_t* bar = (uint64_t*)(smem + NWARP * 8192) + 2 * warp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) L.ctl->work_n[(pass + 1) & 1] = 0;
+  if (gave_up(L)) return;
+  const int n = __ldcg(&L.ctl->work_n[pass & 1]);
+  const int4* list = L.work + (size_t)(pass & 1) * L.n_tiles * SPT;
+  const int stride = gridDim.x * NWARP;
+  int i = blockIdx.x * NWARP + warp;
+  if (i >= n) return;
+  if (smem_u32(smem) & 1023) {                       // the swizzled boxes need 1 KB alignment
+    if (lane == 0) atomicOr(L.out.err, ERR_TIMEOUT);
+    return;
+  }
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_async_smem();
+  }
+  __syncwarp();
+  uint32_t phase0 = 0, phase1 = 0;
+  int4 w = list[i];
+  if (lane == 0) tma_box(box0, &L.wr_map, w.z >> 3, &bar[0]);
+  for (int b = 0; i < n; i += stride, b ^= 1) {
+    const int inext = i + stride;
+    const int4 wn = inext < n ? list[inext] : make_int4(0, 0, 0, 0);
+    __syncwarp();
+    if (inext < n && lane == 0) {
+      fence_async_smem();
+      tma_box(box0 + (b ^ 1) * 256, &L.wr_map, wn.z >> 3, &bar[b ^ 1]);
+    }
+    const uint32_t ph = b ? phase1 : phase0;
+    if (!mbar_wait(&bar[b], ph, L.wait_limit)) {
+      if (lane == 0) atomicOr(L.out.err, ERR_TIMEOUT);
+      mbar_wait(&bar[b], ph, DRAIN_POLLS);
+      if (inext < n) mbar_wait(&bar[b ^ 1], b ? phase0 : phase1, DRAIN_POLLS);
+      return;
+    }
+    if (b) phase1 ^= 1;
+    else phase0 ^= 1;
+    const GridHaloState& S = L.state[w.y];
+    if (pow2_neg(S.s_m) != 0.0f && pow2_neg(S.s_mr) != 0.0f) pass_box<true>(L, w, pass, box0 + b * 256);
+    else pass_box<false>(L, w, pass, box0 + b * 256);
+    w = wn;
+  }
 }
 
 // ---- final pass --------------------------------------------------------------------------
@@ -1194,6 +1443,7 @@ __global__ void __launch_bounds__(T, sizeof(R) == 4 ? 2 : 1) g_pass(GridLaunch L
 // sub-tile, lanes holding consecutive elements as in a pass.
 template <typename R, bool UNIF>
 __global__ void __launch_bounds__(T) g_final(GridLaunch L) {
+  if (gave_up(L)) return;
   using V4 = typename Prec<R>::V4;
   using Acc = typename Prec<R>::Acc;
   const int lane = threadIdx.x & 31;
@@ -1271,6 +1521,7 @@ __global__ void __launch_bounds__(T) g_final(GridLaunch L) {
 // First compacted index k with M_k < delta_rho 4pi/3 r_{k+1}^3 (r_{N+1} = inf).
 template <typename R>
 __global__ void __launch_bounds__(T) g_virial(GridLaunch L) {
+  if (gave_up(L)) return;
   using Acc = typename Prec<R>::Acc;
   const R* rc = (const R*)L.rc;
   const Acc* mc = (const Acc*)L.mc;
@@ -1317,6 +1568,7 @@ __global__ void __launch_bounds__(T) g_virial(GridLaunch L) {
 
 template <typename R>
 __global__ void g_result(GridLaunch L) {
+  if (gave_up(L)) return;
   using Acc = typename Prec<R>::Acc;
   const R* rc = (const R*)L.rc;
   const Acc* mcv = (const Acc*)L.mc;
@@ -1384,6 +1636,7 @@ __global__ void g_result(GridLaunch L) {
 // CTA per halo, the rows spread over the threads; Sect. 2.1's radially binned
 // output): each edge by binary search over the compacted radii.
 __global__ void __launch_bounds__(T) g_rows_mixed(GridLaunch L) {
+  if (gave_up(L)) return;
   const int k = blockIdx.x;
   const HaloDev& H = L.halos[k];
   const GridHaloState& S = L.state[k];
@@ -1396,6 +1649,7 @@ __global__ void __launch_bounds__(T) g_rows_mixed(GridLaunch L) {
 
 // The all-FP64 rows: FP64 radii against the FP64 edges, __int128 masses.
 __global__ void __launch_bounds__(T) g_rows_f64(GridLaunch L) {
+  if (gave_up(L)) return;
   const int k = blockIdx.x;
   const HaloDev& H = L.halos[k];
   const GridHaloState& S = L.state[k];
@@ -1495,13 +1749,24 @@ cudaError_t sort_t(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, un
   return cudaGetLastError();
 }
 
+std::atomic<unsigned long long> g_tma_attr{0};
+
 template <typename R>
 cudaError_t iterate_t(const GridLaunch& L, int pass, cudaStream_t s) {
   const bool unif = L.ms == nullptr, gas = L.uth != nullptr;
-  if (unif && !gas) g_pass<R, true, false><<<L.iter_grid, T, 0, s>>>(L, pass);
+  if (sizeof(R) == 4 && L.use_tma && unif && !gas) {
+    if (first_use_on_device(g_tma_attr)) {
+      const cudaError_t e = cudaFuncSetAttribute(g_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM);
+      if (e != cudaSuccess) return e;
+      mark_used_on_device(g_tma_attr);
+    }
+    g_pass_tma<<<L.tma_grid, T, TMA_SMEM, s>>>(L, pass);
+  } else if (unif && !gas) g_pass<R, true, false><<<L.iter_grid, T, 0, s>>>(L, pass);
   else if (!unif && !gas) g_pass<R, false, false><<<L.iter_grid, T, 0, s>>>(L, pass);
   else if (unif) g_pass<R, true, true><<<L.iter_grid, T, 0, s>>>(L, pass);
   else g_pass<R, false, true><<<L.iter_grid, T, 0, s>>>(L, pass);
+  if (unif) g_removed<R, true><<<L.iter_grid, T, 0, s>>>(L, pass);
+  else g_removed<R, false><<<L.iter_grid, T, 0, s>>>(L, pass);
   if (L.max_halo_tiles > 64) g_halo<R, false, HT_BIG><<<L.n_halos, HT_BIG, 0, s>>>(L, pass);
   else g_halo<R, false, HT_SMALL><<<L.n_halos, HT_SMALL, 0, s>>>(L, pass);
   return cudaGetLastError();
@@ -1533,6 +1798,41 @@ int iter_grid_t(int device) {
 }  // namespace
 
 int grid_iter_grid(int device, int fp64) { return fp64 ? iter_grid_t<double>(device) : iter_grid_t<float>(device); }
+
+int grid_tma_grid(int device) {
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(g_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, g_pass_tma, T, TMA_SMEM) != cudaSuccess) return 0;
+  return sms * per;
+}
+
+// The stream (w, r) of n_rows 8-element rows as a 2-D float tensor of 32
+// columns, copied in boxes of 32 x 32 (4 KB) with the 128-byte swizzle.
+bool grid_wr_map(GridLaunch& L, long long n_rows) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = (Encode)fn;
+    cudaGetLastError();
+  }
+  if (!encode || n_rows <= 0 || ((uintptr_t)L.wr & 15)) return false;
+  const cuuint64_t dims[2] = {32, (cuuint64_t)n_rows};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(&L.wr_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, L.wr, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t grid_prepare(const GridLaunch& L, cudaStream_t s) {
   return L.fp64 ? prepare_t<double>(L, s) : prepare_t<float>(L, s);

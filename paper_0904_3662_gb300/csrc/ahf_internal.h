@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ahf.h"
@@ -69,6 +70,7 @@ struct OutputsDev {
 
 // Device error bits reported back through the error word.
 constexpr int ERR_BAD_INDEX = 1;     // a member index was out of range
+constexpr int ERR_TIMEOUT = 2;       // a bounded wait on a tensor copy gave up
 constexpr int ERR_CAPACITY = 4;      // a halo exceeded its class capacity
 
 // An exact fixed-point sum of the multi-CTA class: a long long (mixed
@@ -164,6 +166,12 @@ cudaError_t launch_onchip(const OnchipLaunch &L, int variant, int grid, cudaStre
 int onchip_max_grid(int variant, int device);
 
 struct GridLaunch {
+  // the radial-order stream (w, r) as a 2-D tensor of 8-element rows (128
+  // bytes), for the passes' tensor copies into shared memory (mixed mode)
+  alignas(64) CUtensorMap wr_map;
+  int use_tma;             // the passes stage sub-tiles through wr_map
+  int tma_grid;            // CTAs of that pass kernel
+  long long wait_limit;    // polls of a copy's barrier before giving up (ERR_TIMEOUT)
   ParticlesDev p;
   FrameDev frame;
   ParamsDev prm;
@@ -205,6 +213,8 @@ struct GridLaunch {
   void *pre_m, *pre_r;
   long long* pre_c;
   AccSlot* tile_mv;        // [n_tiles][3]: sum m v of each tile's members (initial set)
+  uint8_t* rem_mask;       // [n_tiles * GRID_TILE / GRID_SUB][32]: removal flags of the last
+                           // pass, one byte per lane (bit i: the lane's element i)
   int4* work;              // [2][n_tiles * GRID_TILE / GRID_SUB]: the sub-tiles of the active
                            // haloes for the passes of each parity: (sub-tile, halo, first
                            // flat element, members in it)
@@ -220,6 +230,10 @@ constexpr int GRID_SUB = 256;      // elements of a sub-tile (one warp's share o
 // CTAs of the multi-CTA class's persistent iteration pass that fit on
 // `device` at once.
 int grid_iter_grid(int device, int fp64);
+int grid_tma_grid(int device);
+// Fill L.wr_map for the stream L.wr of n_rows 8-element rows; false if the
+// tensor map cannot be made (the passes then read the stream directly).
+bool grid_wr_map(GridLaunch &L, long long n_rows);
 cudaError_t grid_prepare(const GridLaunch &L, cudaStream_t s);
 // Radix passes over the bits where the keys differ (or_bits ^ and_bits);
 // the last pass also lays out the radial-order streams.  Then the sums of

@@ -7,14 +7,16 @@
 // batches and runs each batch through ahf_unbind_batch, forming and copying
 // the next batch while the previous one computes (two batches in flight).
 //
-// Memory.  At submission the request's candidates are copied into a pinned
-// host ring; a device ring with the same slot numbering receives a batch's
-// slice of the ring with one copy per array, and the bound lists come back
-// into a pinned ring of the same numbering.  The rings have S slots, fixed at
-// creation from the caller's device-memory cap, so admission is one ring
-// allocation: a request that does not fit is refused with AHF_ERR_FULL
-// (the caller retries after polling).  Slots are released in submission
-// order once the batch holding them has completed.
+// Memory.  A request holds slots in two rings from submission until its
+// batch has completed.  The device ring, sized from the caller's
+// device-memory cap (particle state of every request in flight, its bound
+// list, the result records and the context's workspace), is the admission
+// rule: a request whose candidates do not fit in the device memory left is
+// refused with AHF_ERR_FULL (the caller polls and retries).  The pinned host
+// ring (at most 2^23 slots) stages the candidates at submission and takes
+// the bound lists back; it refuses the same way when it is full.  A batch is
+// a run of requests contiguous in both rings: one copy per array in, one
+// copy of the bound lists out.  Slots return in submission order.
 //
 // Latency of a request = time from entering ahf_serve_submit to the moment
 // its result became visible to ahf_serve_poll.
@@ -41,14 +43,16 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int DEPTH = 2;                        // batches in flight
-constexpr int64_t MAX_SLOTS = 1LL << 23;        // ring size cap (host pinned memory)
+constexpr int64_t MAX_HOST_SLOTS = 1LL << 23;   // host staging ring (pinned memory)
+constexpr int64_t MAX_DEV_SLOTS = 1LL << 31;    // device ring
 constexpr int64_t MAX_BATCH_HALOS = 8192;
 constexpr int64_t MAX_REQUEST = 131072;         // the on-chip classes' largest halo
 constexpr size_t WS_RESERVE = 64ull << 20;      // allowance for the context's workspace
 
 struct Req {
   uint64_t id = 0;
-  int64_t start = 0, n = 0;  // ring slots [start, start + max(n, 1))
+  int64_t start = 0, n = 0;  // device ring slots [start, start + max(n, 1))
+  int64_t hstart = 0;        // host ring slots [hstart, hstart + max(n, 1))
   int64_t first = 0;         // caller's index of the first candidate
   double c[3] = {0.0, 0.0, 0.0};
   double radius = 0.0;
@@ -88,11 +92,16 @@ struct Ring {
     live.pop_front();
     if (live.empty()) head = 0;
   }
+  void undo_last() {                          // take back the range alloc just handed out
+    live.pop_back();
+    head = live.empty() ? 0 : live.back().second;
+  }
 };
 
 struct Batch {
   std::vector<Req*> reqs;
-  int64_t b0 = 0, b1 = 0;  // ring range
+  int64_t b0 = 0, b1 = 0;  // device ring range
+  int64_t h0 = 0, h1 = 0;  // host ring range
   int slot = 0;
   int rc = AHF_OK;
   std::string err;
@@ -107,7 +116,8 @@ struct ahf_serve {
   double m0 = 0.0;        // > 0: uniform particle mass, requests carry no masses
   size_t es = 4;          // bytes per coordinate / velocity / mass element
   int n_arr = 6;          // arrays per candidate (7 with masses)
-  int64_t S = 0;          // ring slots
+  int64_t S = 0;          // device ring slots
+  int64_t SH = 0;         // host ring slots
   int64_t max_batch_slots = 0;
   ahf_ctx* ctx = nullptr;
   cudaStream_t ks = nullptr, cs = nullptr;  // compute / copy streams
@@ -124,7 +134,8 @@ struct ahf_serve {
   std::deque<Req*> queue;
   std::atomic<int64_t> queued{0};
   std::unordered_map<uint64_t, Req*> reqs;
-  Ring ring;
+  Ring ring;              // device slots (the HBM cap)
+  Ring hring;             // host staging slots
   uint64_t next_id = 1;
   bool stop = false;
   std::thread worker;
@@ -135,9 +146,9 @@ struct ahf_serve {
   bool have_first = false;
 
   char* d_array(int a) const { return d_arena + (size_t)a * S * es; }
-  char* h_array(int a) const { return h_arena + (size_t)a * S * es; }
+  char* h_array(int a) const { return h_arena + (size_t)a * SH * es; }
   int64_t* d_bound() const { return (int64_t*)(d_arena + (size_t)n_arr * S * es); }
-  int64_t* h_bound() const { return (int64_t*)(h_arena + (size_t)n_arr * S * es); }
+  int64_t* h_bound() const { return (int64_t*)(h_arena + (size_t)n_arr * SH * es); }
 };
 
 namespace {
@@ -150,7 +161,7 @@ void launch(ahf_serve* s, Batch* b) {
   b->err.clear();
   cudaError_t e = cudaSuccess;
   for (int a = 0; a < s->n_arr && e == cudaSuccess; ++a)
-    e = cudaMemcpyAsync(s->d_array(a) + (size_t)b->b0 * s->es, s->h_array(a) + (size_t)b->b0 * s->es,
+    e = cudaMemcpyAsync(s->d_array(a) + (size_t)b->b0 * s->es, s->h_array(a) + (size_t)b->h0 * s->es,
                         (size_t)n * s->es, cudaMemcpyHostToDevice, s->cs);
   if (e == cudaSuccess) e = cudaEventRecord(s->ev_in[k], s->cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ks, s->ev_in[k], 0);
@@ -186,7 +197,7 @@ void launch(ahf_serve* s, Batch* b) {
       e = cudaMemcpyAsync(s->h_res + (size_t)k * MAX_BATCH_HALOS, dres, H.size() * sizeof(ahf_result),
                           cudaMemcpyDeviceToHost, s->ks);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->h_bound() + b->b0, s->d_bound() + b->b0, (size_t)n * sizeof(int64_t),
+        e = cudaMemcpyAsync(s->h_bound() + b->h0, s->d_bound() + b->b0, (size_t)n * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s->ks);
       if (e != cudaSuccess) {
         b->rc = AHF_ERR_CUDA;
@@ -219,7 +230,7 @@ void finalize(ahf_serve* s, Batch* b, cudaError_t q) {
     r->res = R[i];
     const int64_t nb = std::max<int64_t>(0, std::min<int64_t>(R[i].n_bound, r->n));
     r->bound.resize((size_t)nb);
-    for (int64_t j = 0; j < nb; ++j) r->bound[(size_t)j] = hb[r->start + j] - r->start + r->first;
+    for (int64_t j = 0; j < nb; ++j) r->bound[(size_t)j] = hb[r->hstart + j] - r->start + r->first;
   }
   const Clock::time_point now = Clock::now();
   std::lock_guard<std::mutex> g(s->mu);
@@ -228,6 +239,7 @@ void finalize(ahf_serve* s, Batch* b, cudaError_t q) {
     r->t_done = now;
     s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
     s->ring.release_front();
+    s->hring.release_front();
   }
   s->completed += (int64_t)b->reqs.size();
   s->batches += 1;
@@ -251,13 +263,15 @@ void worker_main(ahf_serve* s) {
         nb->slot = slot;
         nb->reqs.clear();
         nb->b0 = nb->b1 = s->queue.front()->start;
+        nb->h0 = nb->h1 = s->queue.front()->hstart;
         while (!s->queue.empty() && (int64_t)nb->reqs.size() < MAX_BATCH_HALOS) {
           Req* r = s->queue.front();
-          const int64_t end = r->start + std::max<int64_t>(r->n, 1);
-          if (r->start != nb->b1) break;                       // the ring wrapped: next batch
-          if (!nb->reqs.empty() && end - nb->b0 > s->max_batch_slots) break;
+          const int64_t len = std::max<int64_t>(r->n, 1);
+          if (r->start != nb->b1 || r->hstart != nb->h1) break;   // a ring wrapped: next batch
+          if (!nb->reqs.empty() && r->start + len - nb->b0 > s->max_batch_slots) break;
           nb->reqs.push_back(r);
-          nb->b1 = end;
+          nb->b1 = r->start + len;
+          nb->h1 = r->hstart + len;
           s->queue.pop_front();
         }
         s->queued.fetch_sub((int64_t)nb->reqs.size(), std::memory_order_release);
@@ -325,7 +339,8 @@ int ahf_serve_create(ahf_serve** out, int device, size_t hbm_cap_bytes, const ah
   const size_t per_slot = (size_t)n_arr * es + sizeof(int64_t);
   const size_t fixed = WS_RESERVE + (size_t)DEPTH * MAX_BATCH_HALOS * sizeof(ahf_result);
   int64_t S = hbm_cap_bytes > fixed ? (int64_t)((hbm_cap_bytes - fixed) / per_slot) : 0;
-  S = std::min(S, MAX_SLOTS) / 256 * 256;
+  S = std::min(S, MAX_DEV_SLOTS) / 256 * 256;
+  const int64_t SH = std::min(S, MAX_HOST_SLOTS);
   if (S < MAX_REQUEST)
     return set_last_error_fmt(AHF_ERR_INVALID, "hbm_cap_bytes %zu leaves %lld slots, below the %lld a request may need",
                               hbm_cap_bytes, (long long)S, (long long)MAX_REQUEST);
@@ -338,8 +353,10 @@ int ahf_serve_create(ahf_serve** out, int device, size_t hbm_cap_bytes, const ah
   s->es = es;
   s->n_arr = n_arr;
   s->S = S;
-  s->max_batch_slots = S / 2;
+  s->SH = SH;
+  s->max_batch_slots = SH / 2;
   s->ring.cap = S;
+  s->hring.cap = SH;
   rc = ahf_create(&s->ctx, device);
   if (rc != AHF_OK) {
     release(s);
@@ -348,7 +365,7 @@ int ahf_serve_create(ahf_serve** out, int device, size_t hbm_cap_bytes, const ah
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, (size_t)S * per_slot);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_res, (size_t)DEPTH * MAX_BATCH_HALOS * sizeof(ahf_result));
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_arena, (size_t)S * per_slot);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_arena, (size_t)SH * per_slot);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, (size_t)DEPTH * MAX_BATCH_HALOS * sizeof(ahf_result));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ks, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking);
@@ -400,19 +417,29 @@ int ahf_serve_submit(ahf_serve* s, const ahf_particles* p, const ahf_halo* h, ui
     delete r;
     return set_last_error_fmt(AHF_ERR_INVALID, "serving instance is shutting down");
   }
-  const int64_t start = s->ring.alloc(std::max<int64_t>(h->count, 1));
+  const int64_t len = std::max<int64_t>(h->count, 1);
+  const int64_t start = s->ring.alloc(len);
   if (start < 0) {
     delete r;
     s->rejected += 1;
-    return set_last_error_fmt(AHF_ERR_FULL, "no room for %lld candidates in the %lld-slot ring; poll and retry",
-                              (long long)h->count, (long long)s->S);
+    return set_last_error_fmt(AHF_ERR_FULL, "no room for %lld candidates in the device memory cap (%lld slots); "
+                              "poll and retry", (long long)h->count, (long long)s->S);
+  }
+  const int64_t hstart = s->hring.alloc(len);
+  if (hstart < 0) {
+    s->ring.undo_last();
+    delete r;
+    s->rejected += 1;
+    return set_last_error_fmt(AHF_ERR_FULL, "no room for %lld candidates in the %lld-slot host staging ring; "
+                              "poll and retry", (long long)h->count, (long long)s->SH);
   }
   const void* src[7] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m};
   for (int a = 0; a < s->n_arr; ++a)
-    std::memcpy(s->h_array(a) + (size_t)start * s->es, (const char*)src[a] + (size_t)h->offset * s->es,
+    std::memcpy(s->h_array(a) + (size_t)hstart * s->es, (const char*)src[a] + (size_t)h->offset * s->es,
                 (size_t)h->count * s->es);
   r->id = s->next_id++;
   r->start = start;
+  r->hstart = hstart;
   r->n = h->count;
   r->first = h->offset;
   r->c[0] = h->cx;
