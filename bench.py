@@ -23,7 +23,6 @@ and the scaling is weak.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
@@ -37,6 +36,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+
+from paper_0904_3662_gb300 import ncu_traffic  # noqa: E402
 
 METRIC = "particle-iterations/s"
 N_BINS = 32
@@ -197,7 +198,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---- algorithmic bytes per phase (see the design notes) --------------------------------
+# ---- algorithmic bytes per phase: what each phase must move at least (inputs read once,
+# ---- outputs written once, the multi-CTA radial stream read once per pass) ------------
 
 def traced_classes(ctx, step, pop):
     """The size class each halo ran in (the library may promote the haloes
@@ -250,24 +252,15 @@ def phase_bytes(pop, res, cls):
 
 
 def source_hash(files):
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    return ncu_traffic.source_hash(files, ROOT)
 
 
-_DEV = "paper_0904_3662_gb300/csrc/ahf_device.cuh"
-_ONCHIP = ["paper_0904_3662_gb300/csrc/ahf_onchip.cu", _DEV]
-_GRID = ["paper_0904_3662_gb300/csrc/ahf_grid.cu", _DEV]
-PHASE_SOURCES = {0: ["paper_0904_3662_gb300/csrc/ahf_warp.cu", _DEV], 1: _ONCHIP, 2: _ONCHIP, 3: _ONCHIP,
-                 4: _ONCHIP, 5: _ONCHIP, 6: _ONCHIP, 7: _ONCHIP, 8: _GRID, 9: _GRID, 10: _GRID,
-                 11: ["paper_0904_3662_gb300/csrc/ahf_profile.cu", _DEV]}
+PHASE_SOURCES = ncu_traffic.PHASE_SOURCES
 
 
-def measured_traffic(phase, workload):
-    """DRAM bytes per launch of a phase from the committed ncu summary, or
-    None when there is none or the kernel source changed since."""
+def measured_entry(phase, workload):
+    """The committed ncu figures of a phase (profiles/traffic.json), or None
+    when there are none or the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -276,7 +269,27 @@ def measured_traffic(phase, workload):
     e = t.get(f"{workload}:{phase}")
     if not e or e.get("source_hash") != source_hash(PHASE_SOURCES[phase]):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def measured_traffic(phase, workload):
+    """DRAM bytes per launch of a phase from the committed ncu summary, or
+    None when there is none or the kernel source changed since."""
+    e = measured_entry(phase, workload)
+    return e.get("dram_bytes_per_launch") if e else None
+
+
+def issue_roofline(entry, ms_per_launch, sm_mhz, n_sm):
+    """Issue-slot roofline of a phase: its warp instructions (ncu) per launch
+    over its live duration, against every SM sub-partition issuing one warp
+    instruction per clock (SMs x 4 x SM clock).  None without a count."""
+    if not entry or not entry.get("warp_instructions_per_launch") or ms_per_launch <= 0:
+        return None
+    inst = float(entry["warp_instructions_per_launch"])
+    achieved = inst / (ms_per_launch / 1e3) / 1e9
+    peak = n_sm * 4 * sm_mhz * 1e6 / 1e9
+    return {"warp_instructions": inst, "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak, "peak_from": f"{n_sm} SMs x 4 issue slots x {sm_mhz:.0f} MHz"}
 
 
 def peaks():
@@ -461,7 +474,8 @@ def run_ahf(args):
     dom = int(np.argmax(avg))
     peak, peak_kind = peaks()
     achieved = pbytes[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
-    traffic = measured_traffic(dom, args.workload)
+    entry = measured_entry(dom, args.workload)
+    traffic = entry.get("dram_bytes_per_launch") if entry else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": ahf.PHASE_NAMES[dom], "algorithmic_bytes": float(pbytes[dom]),
                 "ms_per_launch": float(avg[dom]), "peak_source": peak_kind,
@@ -482,6 +496,15 @@ def run_ahf(args):
     if clocks:
         clocks["window"] = "the timed steps and the same steps right after them (200 ms sampling)"
     line["clocks"] = clocks
+    # the same phase against the issue slots (on-chip classes are issue- and
+    # latency-bound rather than HBM-bound), and every phase with a count
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = float(clocks["sm_mhz"]) if clocks else 2070.0
+    roofline["issue"] = issue_roofline(entry, float(avg[dom]), sm_mhz, n_sm)
+    roofline["issue_by_phase"] = {
+        ahf.PHASE_NAMES[k]: round(r["frac"], 4) for k in range(ahf.N_PHASES) if phase_n[k] > 0
+        for r in [issue_roofline(measured_entry(k, args.workload), float(avg[k]), sm_mhz, n_sm)] if r}
     if rank == 0 and args.properties:
         line["properties"] = time_properties(ctx, parts, hal, prm, pop, stream, flush)
         log(f"properties {line['properties']['properties_ms']:.3f} ms, matching {line['properties']['match_ms']:.3f} ms")

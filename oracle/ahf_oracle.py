@@ -27,7 +27,7 @@ What it computes (Knollmann & Knebe 2009, "AHF: Amiga's Halo Finder"):
 * Virial radius (Sect. 2.1): mean enclosed density = Delta * rho_b, so
   M_vir = 4 pi rho_b Delta r_vir^3 / 3.
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
 
 1. Bulk velocity: mass-weighted mean velocity of the current set, recomputed
    every iteration; the escape test uses u = v - v_bulk + H d (Hubble flow).

@@ -277,28 +277,25 @@ __device__ __forceinline__ long long wrap_fix(long long d, long long box) {
   return d;
 }
 
-// Round an int64 to the nearest float (ties to even) with integer
-// operations only.
+// Round an int64 to the nearest float (ties to even) without the 64-bit
+// conversion (which runs on the narrow FP64 pipe of this part): below 2^32 one
+// 32-bit conversion; above, the top 32 bits (msb at bit 31, so 8 bits below
+// the float's last place) with every bit shifted out ORed into bit 0 (sticky),
+// so that the one rounding of the 32-bit conversion sees the whole value, then
+// an exact scaling by 2^sh.
 __device__ __forceinline__ float f32_from_i64_rn(long long v) {
-  if (v == 0) return 0.0f;
-  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  int msb = 63 - __clzll((long long)a);
-  unsigned long long m;
-  if (msb <= 23) {
-    m = a << (23 - msb);
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const uint32_t hi = (uint32_t)(a >> 32);
+  float f;
+  if (hi == 0u) {
+    f = __uint2float_rn((uint32_t)a);
   } else {
-    const int sh = msb - 23;
-    m = a >> sh;
-    const unsigned long long rem = a & ((1ull << sh) - 1ull);
-    const unsigned long long half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (m & 1ull))) {
-      m += 1ull;
-      if (m == (1ull << 24)) { m >>= 1; msb += 1; }
-    }
+    const int sh = 32 - __clz(hi);                        // 1 .. 32
+    uint32_t top = (uint32_t)(a >> sh);
+    if (a & ((1ull << sh) - 1ull)) top |= 1u;
+    f = __uint2float_rn(top) * __int_as_float((sh + 127) << 23);
   }
-  uint32_t bits = ((uint32_t)m & 0x7fffffu) | ((uint32_t)(msb + 127) << 23);
-  if (v < 0) bits |= 0x80000000u;
-  return __uint_as_float(bits);
+  return v < 0 ? -f : f;
 }
 
 // Fixed-point offset of one candidate from the halo centre (per axis).

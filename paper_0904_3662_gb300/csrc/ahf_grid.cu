@@ -321,10 +321,52 @@ __device__ __forceinline__ double load_mass_f64(const ParticlesDev& p, long long
 
 // ---- prepare ---------------------------------------------------------------------
 
+// The CTA's key range, per-halo maxima and member count merged into the call's
+// words.  Every thread passes its warp's reduced values; the CTA reduces them
+// once more and thread 0 issues an atomic only where it can change the word
+// (OR, AND and max are idempotent, so a stale read costs an extra atomic,
+// never a wrong value).  Thousands of tiles share a handful of words, so one
+// atomic per warp and word would queue on the same addresses.
+__device__ __forceinline__ void merge_prepare(const GridLaunch& L, int k, unsigned long long orb,
+                                              unsigned long long andb, unsigned long long mxm,
+                                              unsigned long long mxr, unsigned long long mxv, int nmem) {
+  __shared__ unsigned long long red[5][NWARP];
+  __shared__ int rn[NWARP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = orb;
+    red[1][warp] = andb;
+    red[2][warp] = mxm;
+    red[3][warp] = mxr;
+    red[4][warp] = mxv;
+    rn[warp] = nmem;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  unsigned long long o = 0, a = ~0ull, m0 = 0, m1 = 0, m2 = 0;
+  long long n = 0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) {
+    o |= red[0][w];
+    a &= red[1][w];
+    m0 = max(m0, red[2][w]);
+    m1 = max(m1, red[3][w]);
+    m2 = max(m2, red[4][w]);
+    n += rn[w];
+  }
+  GridHaloState* st = L.state + k;
+  if (o & ~__ldcg(&L.ctl->key_or)) atomicOr(&L.ctl->key_or, o);
+  if (~a & __ldcg(&L.ctl->key_and)) atomicAnd(&L.ctl->key_and, a);
+  if (m0 > __ldcg(&st->mass_max_bits)) atomicMax(&st->mass_max_bits, m0);
+  if (m1 > __ldcg(&st->mr_max_bits)) atomicMax(&st->mr_max_bits, m1);
+  if (m2 > __ldcg(&st->mv_max_bits)) atomicMax(&st->mv_max_bits, m2);
+  if (n) atomicAdd((unsigned long long*)&st->n_member, (unsigned long long)n);
+}
+
 // Mixed precision: the on-chip classes' float offsets (exact recentring),
 // membership and radius; the record holds w = v + H d and r, then v and m.
 template <int CT>
-__global__ void __launch_bounds__(T) g_prepare_mixed(GridLaunch L) {
+__global__ void __launch_bounds__(T, 4) g_prepare_mixed(GridLaunch L) {
   const int t = blockIdx.x;
   const int2 tr = L.tile_range[t];
   const int k = L.tile_halo[t];
@@ -379,7 +421,7 @@ __global__ void __launch_bounds__(T) g_prepare_mixed(GridLaunch L) {
         ++nmem;
       }
     }
-    if (key == KEY_NONMEMBER && L.out.removed_iter) L.out.removed_iter[H.offset + (g - H.gbase)] = -1;
+    if (L.out.removed_iter) L.out.removed_iter[H.offset + (g - H.gbase)] = key == KEY_NONMEMBER ? -1 : 0;
     key_a[g] = key;
     orb |= key;
     andb &= key;
@@ -392,15 +434,7 @@ __global__ void __launch_bounds__(T) g_prepare_mixed(GridLaunch L) {
     mxv = max(mxv, __shfl_xor_sync(FULL_MASK, mxv, o));
   }
   nmem = __reduce_add_sync(FULL_MASK, nmem);
-  if ((threadIdx.x & 31) == 0) {
-    GridHaloState* st = L.state + k;
-    atomicOr(&L.ctl->key_or, (unsigned long long)orb);
-    atomicAnd(&L.ctl->key_and, (unsigned long long)andb | 0xffffffff00000000ull);
-    if (mxm) atomicMax(&st->mass_max_bits, mxm);
-    if (mxr) atomicMax(&st->mr_max_bits, mxr);
-    if (mxv) atomicMax(&st->mv_max_bits, mxv);
-    if (nmem) atomicAdd((unsigned long long*)&st->n_member, (unsigned long long)nmem);
-  }
+  merge_prepare(L, k, orb, (unsigned long long)andb | 0xffffffff00000000ull, mxm, mxr, mxv, nmem);
 }
 
 // All-FP64 mode: d = x - c in FP64 (minimum image), r^2 = (dx^2 + dy^2) + dz^2.
@@ -456,7 +490,7 @@ __global__ void __launch_bounds__(T) g_prepare_f64(GridLaunch L) {
         ++nmem;
       }
     }
-    if (key == ~0ull && L.out.removed_iter) L.out.removed_iter[slot] = -1;
+    if (L.out.removed_iter) L.out.removed_iter[slot] = key == ~0ull ? -1 : 0;
     key_a[g] = key;
     orb |= key;
     andb &= key;
@@ -469,15 +503,7 @@ __global__ void __launch_bounds__(T) g_prepare_f64(GridLaunch L) {
     mxv = max(mxv, __shfl_xor_sync(FULL_MASK, mxv, o));
   }
   nmem = __reduce_add_sync(FULL_MASK, nmem);
-  if ((threadIdx.x & 31) == 0) {
-    GridHaloState* st = L.state + k;
-    atomicOr(&L.ctl->key_or, orb);
-    atomicAnd(&L.ctl->key_and, andb);
-    if (mxm) atomicMax(&st->mass_max_bits, mxm);
-    if (mxr) atomicMax(&st->mr_max_bits, mxr);
-    if (mxv) atomicMax(&st->mv_max_bits, mxv);
-    if (nmem) atomicAdd((unsigned long long*)&st->n_member, (unsigned long long)nmem);
-  }
+  merge_prepare(L, k, orb, andb, mxm, mxr, mxv, nmem);
 }
 
 template <typename R>
@@ -597,7 +623,7 @@ __global__ void __launch_bounds__(256) g_digit_base(uint32_t* __restrict__ digit
 // (w, r), the mass (per-particle masses), u_th (gas) and the position; the
 // tile's members' exact sum m v goes to tile_mv.
 template <typename Key, typename R, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(T) g_scatter(GridLaunch L, const Key* __restrict__ kin,
+__global__ void __launch_bounds__(T, LAST ? 3 : 5) g_scatter(GridLaunch L, const Key* __restrict__ kin,
                                                const uint32_t* __restrict__ vin, Key* __restrict__ kout,
                                                uint32_t* __restrict__ vout, int shift) {
   using V4 = typename Prec<R>::V4;
@@ -615,6 +641,10 @@ __global__ void __launch_bounds__(T) g_scatter(GridLaunch L, const Key* __restri
   const int t0 = L.halo_tile0[kh], th = L.halo_tile0[kh + 1] - t0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < NWARP * 256; i += T) (&whist[0][0])[i] = 0;
+  // this tile's first global position of digit threadIdx.x (digit base + the
+  // tiles before this one), loaded while the tile is ranked
+  const uint32_t my_gofs =
+      L.digit_base[(size_t)kh * 256 + threadIdx.x] + L.tile_hist[(size_t)t0 * 256 + (size_t)threadIdx.x * th + (t - t0)];
   constexpr int CH = TILE / NWARP;       // 256 elements per warp
   Key key[IPT];
   uint32_t val[IPT];
@@ -661,7 +691,7 @@ __global__ void __launch_bounds__(T) g_scatter(GridLaunch L, const Key* __restri
       run += c;
     }
     dstart[d] = block_excl(run, red);
-    gofs[d] = L.digit_base[(size_t)kh * 256 + d] + L.tile_hist[(size_t)t0 * 256 + (size_t)d * th + (t - t0)];
+    gofs[d] = my_gofs;
   }
   __syncthreads();
 #pragma unroll
@@ -677,23 +707,53 @@ __global__ void __launch_bounds__(T) g_scatter(GridLaunch L, const Key* __restri
   __syncthreads();
   Acc smv[3] = {0, 0, 0};
   const int s_v = LAST ? L.state[kh].s_mv : 0;
-  for (int i = threadIdx.x; i < tr.y; i += T) {
-    const Key k = skey[i];
-    const uint32_t v = sval[i];
-    const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
-    const long long dst = gb + (long long)gofs[dg] + (i - (int)dstart[dg]);
-    if (!LAST) {
+  if (!LAST) {
+    for (int i = threadIdx.x; i < tr.y; i += T) {
+      const Key k = skey[i];
+      const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
+      const long long dst = gb + (long long)gofs[dg] + (i - (int)dstart[dg]);
       kout[dst] = k;
-      vout[dst] = v;
-    } else {
-      L.val_x[dst] = v;
-      if (k != ~(Key)0) {
-        const V4* rc = (const V4*)L.rec + 2 * (gb + v);
-        const V4 a = rc[0], q = rc[1];
+      vout[dst] = sval[i];
+    }
+  } else {
+    // the records are gathered in batches of GB, every load of a batch issued
+    // before its first use (the gathers are random within the halo)
+    constexpr int GB = sizeof(R) == 4 ? 4 : 2;
+    const V4* __restrict__ rec = (const V4*)L.rec;
+#pragma unroll
+    for (int b0 = 0; b0 < IPT; b0 += GB) {
+      V4 ra[GB], rq[GB];
+      uint32_t vv[GB];
+      long long dd[GB];
+      bool mem[GB];
+#pragma unroll
+      for (int j = 0; j < GB; ++j) {
+        const int i = (b0 + j) * T + threadIdx.x;
+        mem[j] = false;
+        dd[j] = -1;
+        if (i < tr.y) {
+          const Key k = skey[i];
+          vv[j] = sval[i];
+          const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
+          dd[j] = gb + (long long)gofs[dg] + (i - (int)dstart[dg]);
+          mem[j] = k != ~(Key)0;
+          if (mem[j]) {
+            ra[j] = rec[2 * (gb + vv[j])];
+            rq[j] = rec[2 * (gb + vv[j]) + 1];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < GB; ++j) {
+        if (dd[j] < 0) continue;
+        const long long dst = dd[j];
+        L.val_x[dst] = vv[j];
+        if (!mem[j]) continue;
+        const V4 a = ra[j], q = rq[j];
         ((V4*)L.wr)[dst] = a;
         if (L.ms) ((R*)L.ms)[dst] = q.w;
         if (L.uth) {
-          const long long slot = L.halos[kh].offset + v;
+          const long long slot = L.halos[kh].offset + vv[j];
           const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
           ((R*)L.uth)[dst] = (R)(L.p.coord_type == AHF_COORD_F64 ? __ldg((const double*)L.p.u_th + pi)
                                                                  : (double)__ldg((const float*)L.p.u_th + pi));
@@ -826,38 +886,46 @@ __global__ void __launch_bounds__(T) g_sums(GridLaunch L) {
   using Acc = typename Prec<R>::Acc;
   const int lane = threadIdx.x & 31;
   const int n_sub = L.n_tiles * SPT;
+  const int u = (blockIdx.x * T + threadIdx.x) >> 5;     // one warp per sub-tile
+  if (u >= n_sub) return;
   const V4* wr = (const V4*)L.wr;
   const R* ms = (const R*)L.ms;
   const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
-  for (int u = (blockIdx.x * T + threadIdx.x) >> 5; u < n_sub; u += (gridDim.x * T) >> 5) {
-    const int t = u / SPT;
-    const int k = L.tile_halo[t];
-    const GridHaloState& S = L.state[k];
-    const int2 tr = L.tile_range[t];
-    const long long lim = L.halos[k].gbase + S.n_member;
-    const int e0 = (u % SPT) * SUB;
-    Acc a = 0, b = 0;
-    int c = 0;
+  const int t = u / SPT;
+  const int2 tr = L.tile_range[t];
+  const int e0 = (u % SPT) * SUB;
+  // the rows are read before the halo's state arrives (the loads depend on
+  // the tile only); elements past the last member are dropped afterwards
+  R rq[ROWS], mq[ROWS];
 #pragma unroll
-    for (int i = 0; i < ROWS; ++i) {
-      const int e = e0 + 32 * i + lane;
-      const long long g = (long long)tr.x + e;
-      if (e < tr.y && g < lim) {
-        const R r = wr[g].w;
-        const R m = ms ? ms[g] : m0;
-        a += fixp(m, S.s_m);
-        b += fixp(m * rinv_real(r, L.prm), S.s_mr);
-        ++c;
-      }
+  for (int i = 0; i < ROWS; ++i) {
+    const int e = e0 + 32 * i + lane;
+    const long long g = (long long)tr.x + e;
+    rq[i] = e < tr.y ? wr[g].w : (R)0;
+    mq[i] = (e < tr.y && ms) ? ms[g] : m0;
+  }
+  const int k = L.tile_halo[t];
+  const GridHaloState& S = L.state[k];
+  const long long lim = L.halos[k].gbase + S.n_member;
+  Acc a = 0, b = 0;
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) {
+    const int e = e0 + 32 * i + lane;
+    const long long g = (long long)tr.x + e;
+    if (e < tr.y && g < lim) {
+      a += fixp(mq[i], S.s_m);
+      b += fixp(mq[i] * rinv_real(rq[i], L.prm), S.s_mr);
+      ++c;
     }
-    a = wsum(a);
-    b = wsum(b);
-    c = __reduce_add_sync(FULL_MASK, c);
-    if (lane == 0) {
-      ((Acc*)L.agg_m)[n_sub + u] = a;
-      ((Acc*)L.agg_r)[n_sub + u] = b;
-      L.agg_c[n_sub + u] = c;
-    }
+  }
+  a = wsum(a);
+  b = wsum(b);
+  c = __reduce_add_sync(FULL_MASK, c);
+  if (lane == 0) {
+    ((Acc*)L.agg_m)[n_sub + u] = a;
+    ((Acc*)L.agg_r)[n_sub + u] = b;
+    L.agg_c[n_sub + u] = c;
   }
 }
 
@@ -1442,79 +1510,71 @@ __global__ void __launch_bounds__(T, 3) g_pass_tma(const __grid_constant__ GridL
 // inclusive mass for the virial search and the profile rows; one warp per
 // sub-tile, lanes holding consecutive elements as in a pass.
 template <typename R, bool UNIF>
-__global__ void __launch_bounds__(T) g_final(GridLaunch L) {
+__global__ void __launch_bounds__(T, sizeof(R) == 4 ? 4 : 2) g_final(GridLaunch L) {
   if (gave_up(L)) return;
   using V4 = typename Prec<R>::V4;
   using Acc = typename Prec<R>::Acc;
   const int lane = threadIdx.x & 31;
   const int n_sub = L.n_tiles * SPT;
+  const int u = (blockIdx.x * T + threadIdx.x) >> 5;     // one warp per sub-tile
+  if (u >= n_sub) return;
   const V4* wr = (const V4*)L.wr;
   R* rc = (R*)L.rc;
   Acc* mc = (Acc*)L.mc;
   const R m0 = sizeof(R) == 4 ? (R)L.p.m0f : (R)L.p.m0;
   const ParamsDev& P = L.prm;
-  for (int u = (blockIdx.x * T + threadIdx.x) >> 5; u < n_sub; u += (gridDim.x * T) >> 5) {
-    const int t = u / SPT;
-    const int k = L.tile_halo[t];
-    const GridHaloState& S = L.state[k];
-    if (S.n_alive == 0) continue;
-    const int2 tr = L.tile_range[t];
-    const HaloDev& H = L.halos[k];
-    const long long lim = H.gbase + S.n_member;
-    const int s_m = S.s_m, s_r = S.s_mr;
-    const Acc Ttot = Ald<Acc>(S.t_tot);
-    const int e0 = (u % SPT) * SUB + lane * EPL;
-    R rq[EPL], mq[EPL];
+  const int t = u / SPT;
+  const int2 tr = L.tile_range[t];
+  const int e0 = (u % SPT) * SUB;
+  // rows of 32 consecutive elements (coalesced), read before the halo's
+  // state arrives; elements past the last member count as removed
+  R rq[ROWS], mq[ROWS];
+  uint32_t vq[ROWS];
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) {
-      const int e = e0 + i;
-      const long long g = (long long)tr.x + e;
-      const bool in = e < tr.y && g < lim;
-      rq[i] = in ? wr[g].w : neg0(R());
-      mq[i] = in ? (UNIF ? m0 : ((const R*)L.ms)[g]) : m0;
-    }
-    Acc M, Pp;
-    long long C;
-    sub_prefix<Acc>(L, u, t, (S.n_iter + 1) & 1, M, Pp, &C);
-    const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
-    R ri[EPL];
-    Acc a = 0, b = 0;
-    int c = 0;
+  for (int i = 0; i < ROWS; ++i) {
+    const int e = e0 + 32 * i + lane;
+    const long long g = (long long)tr.x + e;
+    rq[i] = e < tr.y ? wr[g].w : neg0(R());
+    mq[i] = (!UNIF && e < tr.y) ? ((const R*)L.ms)[g] : m0;
+    vq[i] = e < tr.y ? L.val_x[g] : 0u;
+  }
+  const int k = L.tile_halo[t];
+  const GridHaloState& S = L.state[k];
+  if (S.n_alive == 0) return;
+  const HaloDev& H = L.halos[k];
+  const long long lim = H.gbase + S.n_member;
+  const int s_m = S.s_m, s_r = S.s_mr;
+  const Acc Ttot = Ald<Acc>(S.t_tot);
+  Acc M, Pp;
+  long long C;
+  sub_prefix<Acc>(L, u, t, (S.n_iter + 1) & 1, M, Pp, &C);
+  const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
+  const unsigned below = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) {
-      ri[i] = rinv_real(rq[i], P);
-      if (!signbit(rq[i])) {
-        a += fixp(mq[i], s_m);
-        b += fixp(mq[i] * ri[i], s_r);
-        ++c;
-      }
-    }
+  for (int i = 0; i < ROWS; ++i) {
+    const R r = rq[i];
+    const bool alive = !signbit(r) && (long long)tr.x + e0 + 32 * i + lane < lim;
+    const R ri = rinv_real(r, P);
+    const Acc a = alive ? (Acc)fixp(mq[i], s_m) : (Acc)0;
+    const Acc b = alive ? (Acc)fixp(mq[i] * ri, s_r) : (Acc)0;
+    const unsigned bal = __ballot_sync(FULL_MASK, alive);
+    if (bal == 0u) continue;
     const Acc ia = wscan(a, lane), ib = wscan(b, lane);
-    const int ic = (int)wscan((uint32_t)c, lane);
-    M += ia - a;
-    Pp += ib - b;
-    C += ic - c;
-#pragma unroll
-    for (int i = 0; i < EPL; ++i) {
-      const R r = rq[i];
-      if (!signbit(r)) {
-        const long long g = (long long)tr.x + e0 + i;
-        const R m = mq[i];
-        const Acc mfix = fixp(m, s_m);
-        const R phi = phi_real(fix_to_real(M, s_m, sc_m, R()), ri[i], fix_to_real(Ttot - Pp, s_r, sc_r, R()), P);
-        const long long slot = H.offset + L.val_x[g];
-        const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
-        const long long dst = H.offset + C;
-        L.out.bound_idx[dst] = pi;
-        if (L.out.phi) ((R*)L.out.phi)[dst] = phi;
-        if (L.out.removed_iter) L.out.removed_iter[slot] = 0;
-        rc[H.gbase + C] = r;
-        mc[H.gbase + C] = M + mfix;
-        M += mfix;
-        Pp += fixp(m * ri[i], s_r);
-        C += 1;
-      }
+    if (alive) {
+      // M(<r) before the particle, and the outer sum from the particle out
+      const R phi = phi_real(fix_to_real(M + ia - a, s_m, sc_m, R()), ri,
+                             fix_to_real(Ttot - (Pp + ib - b), s_r, sc_r, R()), P);
+      const long long slot = H.offset + vq[i];
+      const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
+      const long long c = C + __popc(bal & below);
+      L.out.bound_idx[H.offset + c] = pi;
+      if (L.out.phi) ((R*)L.out.phi)[H.offset + c] = phi;
+      rc[H.gbase + c] = r;
+      mc[H.gbase + c] = M + ia;
     }
+    M += shfl_idx_x(ia, 31);
+    Pp += shfl_idx_x(ib, 31);
+    C += __popc(bal);
   }
 }
 
@@ -1743,7 +1803,7 @@ cudaError_t sort_t(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, un
     vo = y;
   }
   if (nd == 0) g_fill_identity<R><<<L.n_tiles, T, 0, s>>>(L);
-  g_sums<R><<<L.iter_grid, T, 0, s>>>(L);
+  g_sums<R><<<(int)(((long long)L.n_tiles * SPT + NWARP - 1) / NWARP), T, 0, s>>>(L);
   if (L.max_halo_tiles > 64) g_halo<R, true, HT_BIG><<<L.n_halos, HT_BIG, 0, s>>>(L, 0);
   else g_halo<R, true, HT_SMALL><<<L.n_halos, HT_SMALL, 0, s>>>(L, 0);
   return cudaGetLastError();
@@ -1775,8 +1835,9 @@ cudaError_t iterate_t(const GridLaunch& L, int pass, cudaStream_t s) {
 template <typename R>
 cudaError_t finish_t(const GridLaunch& L, cudaStream_t s) {
   if (L.n_tiles > 0) {
-    if (L.ms == nullptr) g_final<R, true><<<L.iter_grid, T, 0, s>>>(L);
-    else g_final<R, false><<<L.iter_grid, T, 0, s>>>(L);
+    const int nb = (int)(((long long)L.n_tiles * SPT + NWARP - 1) / NWARP);
+    if (L.ms == nullptr) g_final<R, true><<<nb, T, 0, s>>>(L);
+    else g_final<R, false><<<nb, T, 0, s>>>(L);
     g_virial<R><<<L.n_tiles, T, 0, s>>>(L);
   }
   g_result<R><<<blocks_for(L.n_halos, 128), 128, 0, s>>>(L);

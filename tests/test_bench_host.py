@@ -120,3 +120,44 @@ def test_trace_summary_of_a_synthetic_trace():
     tab = trace_report.table(s).splitlines()
     assert len(tab) == 2 + 2 and tab[2].startswith(f"| {ahf.PHASE_NAMES[0]} | 2 | 3.0 |")
     assert trace_report.summarize(np.zeros((4, 8), dtype=np.int64)) == {"haloes": 0}
+
+
+def test_issue_roofline_counts_issue_slots():
+    e = {"warp_instructions_per_launch": 4 * 152 * 2070e6 * 1e-3 * 0.25}   # a quarter of 1 ms of slots
+    r = bench.issue_roofline(e, 1.0, 2070.0, 152)
+    assert abs(r["frac"] - 0.25) < 1e-12
+    assert bench.issue_roofline({"warp_instructions_per_launch": None}, 1.0, 2070.0, 152) is None
+    assert bench.issue_roofline(None, 1.0, 2070.0, 152) is None
+
+
+def test_ncu_launch_list_to_phases(tmp_path):
+    from paper_0904_3662_gb300 import ncu_traffic as nt
+    assert nt.phase_of("void warp_kernel<1>(OnchipLaunch)") == 0
+    assert nt.phase_of("void unbind_kernel<512, 8192, 1, 16>(OnchipLaunch)") == 7
+    assert nt.phase_of("void unbind_kernel<256, 4096, 1, 1>(OnchipLaunch)") == 2
+    assert nt.phase_of("void unnamed>::g_halo<float, 1, 1024>(GridLaunch, int)") == 8
+    assert nt.phase_of("void unnamed>::g_halo<float, 0, 256>(GridLaunch, int)") == 9
+    assert nt.phase_of("unnamed>::g_pass_tma(GridLaunch, int)") == 9
+    assert nt.phase_of("void unnamed>::g_rows_mixed(GridLaunch)") == 10
+    assert nt.phase_of("void at::native::FillFunctor<float>") is None
+    head = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = []
+    launches = [("void unnamed>::g_scales<float>(GridLaunch)", 1000, 10, 5),
+                ("void unnamed>::g_scatter<unsigned int, float, 0, 1>(GridLaunch)", 2000, 100, 7),
+                ("unnamed>::g_pass_tma(GridLaunch, int)", 3000, 50, 11),
+                ("unnamed>::g_pass_tma(GridLaunch, int)", 3000, 50, 11),
+                ("void warp_kernel<1>(OnchipLaunch)", 500, 8, 3),
+                ("void warp_kernel<1>(OnchipLaunch)", 700, 12, 5)]
+    for i, (k, ns, mb, minst) in enumerate(launches):
+        rows.append(f'"{i}","{k}","gpu__time_duration.sum","usecond","{ns / 1e3}"')
+        rows.append(f'"{i}","{k}","dram__bytes_read.sum","Mbyte","{mb}"')
+        rows.append(f'"{i}","{k}","dram__bytes_write.sum","byte","0"')
+        rows.append(f'"{i}","{k}","smsp__inst_executed.sum","Minst","{minst}"')
+    p = tmp_path / "l.csv"
+    p.write_text("==PROF== x\n" + head + "\n".join(rows) + "\n")
+    s = nt.summarize(nt.read_launches(str(p)))
+    assert s[8]["calls"] == 1 and s[8]["launches"] == 2
+    assert abs(s[8]["dram_bytes_per_launch"] - 110e6) < 1 and abs(s[8]["us_per_launch"] - 3.0) < 1e-9
+    assert abs(s[9]["warp_instructions_per_launch"] - 22e6) < 1                 # both passes: one call
+    assert s[0]["launches"] == 2 and abs(s[0]["dram_bytes_per_launch"] - 10e6) < 1   # mean per launch
+    assert abs(s[0]["warp_instructions_per_launch"] - 4e6) < 1
