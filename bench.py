@@ -279,17 +279,42 @@ def measured_traffic(phase, workload):
     return e.get("dram_bytes_per_launch") if e else None
 
 
-def issue_roofline(entry, ms_per_launch, sm_mhz, n_sm):
+def issue_roofline(entry, ms_per_launch, sm_mhz, n_sm, sms_used=None):
     """Issue-slot roofline of a phase: its warp instructions (ncu) per launch
     over its live duration, against every SM sub-partition issuing one warp
-    instruction per clock (SMs x 4 x SM clock).  None without a count."""
+    instruction per clock (SMs x 4 x SM clock).  With sms_used (the SMs the
+    launch can occupy, e.g. 16 for one 16-CTA cluster) also the fraction of
+    those SMs' slots.  None without a count."""
     if not entry or not entry.get("warp_instructions_per_launch") or ms_per_launch <= 0:
         return None
     inst = float(entry["warp_instructions_per_launch"])
     achieved = inst / (ms_per_launch / 1e3) / 1e9
     peak = n_sm * 4 * sm_mhz * 1e6 / 1e9
-    return {"warp_instructions": inst, "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
-            "frac": achieved / peak, "peak_from": f"{n_sm} SMs x 4 issue slots x {sm_mhz:.0f} MHz"}
+    out = {"warp_instructions": inst, "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+           "frac": achieved / peak, "peak_from": f"{n_sm} SMs x 4 issue slots x {sm_mhz:.0f} MHz"}
+    if sms_used:
+        out["sms_used"] = int(sms_used)
+        out["frac_of_sms_used"] = achieved / (sms_used * 4 * sm_mhz * 1e6 / 1e9)
+    return out
+
+
+def sms_used_by_class(cls, n_sm):
+    """SMs each phase's launch can occupy: an on-chip class takes one CTA
+    (or one cluster of 2..16 CTAs, one per SM) per halo at most; the warp
+    class packs several haloes per CTA; the multi-CTA phases span the GPU."""
+    from paper_0904_3662_gb300 import ahf
+    nv = len(ahf.VARIANT_CAPS)
+    out = {}
+    for v in range(nv):
+        n = int(np.sum(cls == v))
+        if n == 0:
+            continue
+        cs = 1 << (v - 3) if v >= 4 else 1
+        per = 8 if v == 0 else 1
+        out[v] = min(n_sm, ((n + per - 1) // per) * cs)
+    for ph in range(nv, nv + 4):
+        out[ph] = n_sm
+    return out
 
 
 def peaks():
@@ -501,10 +526,13 @@ def run_ahf(args):
     import torch
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     sm_mhz = float(clocks["sm_mhz"]) if clocks else 2070.0
-    roofline["issue"] = issue_roofline(entry, float(avg[dom]), sm_mhz, n_sm)
+    used = sms_used_by_class(cls, n_sm)
+    roofline["issue"] = issue_roofline(entry, float(avg[dom]), sm_mhz, n_sm, used.get(dom))
     roofline["issue_by_phase"] = {
-        ahf.PHASE_NAMES[k]: round(r["frac"], 4) for k in range(ahf.N_PHASES) if phase_n[k] > 0
-        for r in [issue_roofline(measured_entry(k, args.workload), float(avg[k]), sm_mhz, n_sm)] if r}
+        ahf.PHASE_NAMES[k]: {"frac": round(r["frac"], 4), "sms_used": r.get("sms_used"),
+                             "frac_of_sms_used": round(r.get("frac_of_sms_used", r["frac"]), 4)}
+        for k in range(ahf.N_PHASES) if phase_n[k] > 0
+        for r in [issue_roofline(measured_entry(k, args.workload), float(avg[k]), sm_mhz, n_sm, used.get(k))] if r}
     if rank == 0 and args.properties:
         line["properties"] = time_properties(ctx, parts, hal, prm, pop, stream, flush)
         log(f"properties {line['properties']['properties_ms']:.3f} ms, matching {line['properties']['match_ms']:.3f} ms")
@@ -666,16 +694,21 @@ def time_e2e(ctx, pop, hal, prm, units, args):
             ctx.unbind_batch_host(hp, hal, prm, out=out, n_bins=N_BINS, r_min_frac=R_MIN_FRAC)
             ts.append(time.perf_counter() - t0)
         return float(np.mean(ts))
-    # default: inputs staged through device memory; then the kernels reading
-    # and writing the page-locked buffers in place, for comparison
-    ctx.set_option(ahf.OPT_HOST_DIRECT, 0)
-    s = timed()
-    ctx.set_option(ahf.OPT_HOST_DIRECT, 1)
-    s_direct = timed()
-    ctx.set_option(ahf.OPT_HOST_DIRECT, 0)
+    # the library's default route for page-locked buffers, then the others
+    # for comparison (0: staged copies, 1: in place, 2: per-class pulls)
+    default = ctx.get_option(ahf.OPT_HOST_DIRECT)
+    modes = {}
+    for mode in (default, *(m for m in (0, 1, 2) if m != default)):
+        ctx.set_option(ahf.OPT_HOST_DIRECT, mode)
+        modes[mode] = timed()
+    ctx.set_option(ahf.OPT_HOST_DIRECT, default)
+    s = modes[default]
+    names = {0: "staged copies", 1: "buffers used in place",
+             2: "inputs read in place, outputs pushed per size class"}
     return {"value": units / s, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": s * 1e3, "in_place_ms_per_step": s_direct * 1e3,
-            "api": "ahf_unbind_batch_host (unbinding + profile, page-locked host buffers, staged copies)"}
+            "ms_per_step": s * 1e3,
+            "ms_per_step_by_route": {names[m]: round(v * 1e3, 4) for m, v in sorted(modes.items())},
+            "api": f"ahf_unbind_batch_host (unbinding + profile, page-locked host buffers, {names[default]})"}
 
 
 def run_serve(args):

@@ -307,14 +307,24 @@ int ahf_unbind_profile_batch(ahf_ctx *ctx, const ahf_particles *p, const ahf_hal
  *                        the multi-CTA class.  Every routing gives the same
  *                        results bit for bit (exact sums); only the time
  *                        changes.  These are the autotuner's knobs.
- *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only: 1 = the kernels read host
- *                        arrays that are page-locked (cudaHostAlloc,
- *                        cudaHostRegister) and write page-locked outputs in
- *                        place through their mapped device addresses, with no
- *                        staging buffer in device memory (for inputs too large
- *                        to stage); 0 (default) = stage through device memory,
- *                        which is faster: the kernels re-read candidates in
- *                        radial order.  Pageable buffers are always staged.
+ *   AHF_OPT_HOST_DIRECT  ahf_unbind_batch_host only, for buffers that are
+ *                        page-locked (cudaHostAlloc, cudaHostRegister; pageable
+ *                        buffers are always staged): 0 = stage every input in
+ *                        device memory before the kernels and copy every
+ *                        output back after them; 1 = the kernels read
+ *                        the inputs and write the outputs in place through
+ *                        their mapped device addresses, with no staging of
+ *                        the inputs (for inputs too large to stage; slower:
+ *                        the kernels' scattered output writes cross the host
+ *                        link one by one); 2 = the kernels read the inputs in
+ *                        place (each candidate once, over the host link, while
+ *                        other haloes compute), and each size class copies its
+ *                        haloes' bound lists, phi and removal iterations to
+ *                        the caller's buffers as soon as its kernel is done,
+ *                        while the others still run (the records and profile
+ *                        rows follow at the end; outputs that are not
+ *                        page-locked, and the two-pass truncation variant,
+ *                        are copied back at the end as in 0).  Default 2.
  * Errors: AHF_ERR_INVALID (unknown option or value). */
 #define AHF_OPT_ONCHIP_MAX 1
 #define AHF_OPT_WAIT_LIMIT 2

@@ -150,7 +150,7 @@ struct ahf_ctx {
   size_t stage_bytes = 0;
   // per-call statistics and optional phase timing
   bool timing = false;
-  bool host_direct = false;          // host entry: use mapped page-locked buffers in place
+  int host_direct = 2;               // host entry: 0 staged, 1 in place, 2 inputs in place + pushed outputs
   bool graphs = false;               // on-chip launch sequence as a replayed CUDA graph
   void* hier = nullptr;              // hierarchy scratch (owners, compacted member lists)
   size_t hier_bytes = 0;
@@ -609,6 +609,55 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
                  int32_t n_bins, double r_min_frac, double* prof, cudaStream_t s,
                  const std::vector<char>* include = nullptr);
 
+// Outputs of the host-buffer entry point that each class pushes to the
+// caller's page-locked buffers as soon as its kernel is done
+// (AHF_OPT_HOST_DIRECT 2), while the other classes still run: the device
+// arrays the kernels wrote and the buffers' mapped device addresses.
+struct HostPush {
+  const ahf_result* res;     // device records (each halo's n_bound)
+  const long long* bi;       // device bound lists
+  long long* h_bi;
+  const char* phi;           // device phi (NULL: none)
+  char* h_phi;
+  int phi_es;                // 4 or 8
+  const int* ri;             // device removal iterations (NULL: none)
+  int* h_ri;
+};
+
+// Copy each halo's bound list and phi (its first n_bound slots) and its
+// removal iterations (all its slots) from device memory to the mapped host
+// buffers; CTA (k, j) takes the j-th of gridDim.y shares of halo k.
+// Consecutive threads write consecutive slots, so the host link carries
+// whole lines.
+__global__ void __launch_bounds__(256) push_slots(HostPush a, const HaloDev* __restrict__ hd) {
+  const HaloDev& H = hd[blockIdx.x];
+  const long long o = H.offset;
+  const long long nb = a.res[H.index].n_bound;
+  const long long per_b = ((nb + gridDim.y - 1) / gridDim.y + 255) & ~255ll;
+  const long long lo = (long long)blockIdx.y * per_b, hi = nb < lo + per_b ? nb : lo + per_b;
+  for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+    a.h_bi[o + i] = a.bi[o + i];
+    if (a.phi) {
+      if (a.phi_es == 8) ((double*)a.h_phi)[o + i] = ((const double*)a.phi)[o + i];
+      else ((float*)a.h_phi)[o + i] = ((const float*)a.phi)[o + i];
+    }
+  }
+  if (a.ri) {
+    const long long n = H.count;
+    const long long per = ((n + gridDim.y - 1) / gridDim.y + 255) & ~255ll;
+    const long long l2 = (long long)blockIdx.y * per, h2 = n < l2 + per ? n : l2 + per;
+    for (long long i = l2 + threadIdx.x; i < h2; i += 256) a.h_ri[o + i] = a.ri[o + i];
+  }
+}
+
+// The push of n haloes (largest count maxc) on stream s.
+cudaError_t launch_push(const HostPush& a, const HaloDev* hd, int n, long long maxc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int split = (int)std::min<long long>(256, std::max<long long>(1, (maxc + 8191) / 8192));
+  push_slots<<<dim3((unsigned)n, (unsigned)split), 256, 0, s>>>(a, hd);
+  return cudaGetLastError();
+}
+
 // Unbinding of a batch; with prof != NULL also the profile rows.  The warp
 // and single-CTA variants form the rows from the bound set they hold on chip;
 // haloes of the cluster and multi-CTA classes get theirs from the profile
@@ -616,7 +665,7 @@ int profile_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int6
 int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                 const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
                 int32_t* removed_iter, cudaStream_t s, int32_t n_bins = 0, double r_min_frac = 0.0,
-                double* prof = nullptr) {
+                double* prof = nullptr, const HostPush* push = nullptr) {
   int rc = validate(p, halos, n_halos, prm, out, bound_idx);
   if (rc) return rc;
   if (prof && (n_bins < 1 || n_bins > profile_max_bins()))
@@ -800,6 +849,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
         if ((prc = phase_begin(c, x.v, o, 0, 0))) return prc;
         AHF_CUDA(launch_variant(x.L, x.v, x.grid, o));
         if ((prc = phase_end(c, x.v, o))) return prc;
+        if (push) AHF_CUDA(launch_push(*push, x.L.halos, x.n, P.hd[(size_t)first_of[x.v]].count, o));
       }
       return AHF_OK;
     }
@@ -810,6 +860,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
       if ((prc = phase_begin(c, x.v, c->side[x.v], 0, 0))) return prc;
       AHF_CUDA(launch_variant(x.L, x.v, x.grid, c->side[x.v]));
       if ((prc = phase_end(c, x.v, c->side[x.v]))) return prc;
+      if (push) AHF_CUDA(launch_push(*push, x.L.halos, x.n, P.hd[(size_t)first_of[x.v]].count, c->side[x.v]));
       AHF_CUDA(cudaEventRecord(c->join[x.v], c->side[x.v]));
     }
     if (join)
@@ -817,7 +868,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     return AHF_OK;
   };
   for (const VLaunch& x : vl) {
-    c->stats.launches += 1;
+    c->stats.launches += push ? 2 : 1;
     c->phase_used[x.v] = true;
     c->stats.phase_halos[x.v] += x.n;
     c->stats.phase_candidates[x.v] += x.cands;
@@ -825,7 +876,7 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   // a batch of on-chip haloes only can run as a CUDA graph, replayed while
   // the launch parameters repeat (the descriptors staged above are inputs
   // of the graph's kernels, not part of it)
-  if (c->graphs && !c->timing && n_grid == 0 && !vl.empty()) {
+  if (c->graphs && !c->timing && n_grid == 0 && !vl.empty() && !push) {
     std::vector<unsigned char> key(vl.size() * sizeof(VLaunch));
     std::memcpy(key.data(), vl.data(), key.size());
     if (!c->graph_exec || key != c->graph_key) {
@@ -859,6 +910,10 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
     if ((rc = enqueue_onchip(s, false))) return rc;
     if (n_grid) {
       if ((rc = run_grid(c, G, prm, s, c->pass_chunk))) return rc;
+      if (push) {
+        AHF_CUDA(launch_push(*push, hd + n_onchip, n_grid, P.hd[(size_t)n_onchip].count, s));
+        c->stats.launches += 1;
+      }
     }
     if (!c->serial)
       for (const VLaunch& x : vl) AHF_CUDA(cudaStreamWaitEvent(s, c->join[x.v], 0));
@@ -1222,10 +1277,10 @@ int forest_depths(const int64_t* parent, int64_t n, std::vector<int>& depth) {
 int unbind_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos,
                 const int64_t* member_idx, const ahf_params* prm, ahf_result* out, int64_t* bound_idx, void* phi,
                 int32_t* removed_iter, cudaStream_t s, int32_t n_bins = 0, double r_min_frac = 0.0,
-                double* prof = nullptr) {
+                double* prof = nullptr, const HostPush* push = nullptr) {
   if (!prm || !(prm->variant & AHF_VAR_RETRUNCATE))
     return unbind_pass(c, p, halos, n_halos, member_idx, prm, out, bound_idx, phi, removed_iter, s, n_bins,
-                       r_min_frac, prof);
+                       r_min_frac, prof, push);
   ahf_params p1 = *prm;
   p1.variant &= ~AHF_VAR_RETRUNCATE;
   int rc = unbind_pass(c, p, halos, n_halos, member_idx, &p1, out, bound_idx, phi, removed_iter, s);
@@ -1415,9 +1470,13 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   AHF_CUDA(cudaSetDevice(c->device));
   if (c->last_valid) AHF_CUDA(cudaStreamWaitEvent(s, c->last, 0));
   Bump B{c->stage, 0, c->stage_bytes};
-  // each buffer is used in place when it is page-locked and mapped (and the
-  // option allows), else staged through the context's device buffer
+  // AHF_OPT_HOST_DIRECT 1: each buffer used in place when it is page-locked
+  // and mapped; 2: the inputs so (the kernels read each candidate once, over
+  // the host link, while other haloes compute), and the bound lists, phi and
+  // removal iterations pushed by each class as it finishes; otherwise staged
+  // through the context's device buffer
   auto direct = [&](const void* h) -> void* { return c->host_direct ? mapped_address(h) : nullptr; };
+  auto out_direct = [&](const void* h) -> void* { return c->host_direct == 1 ? mapped_address(h) : nullptr; };
   ahf_particles dp = *p;
   const void* src[8] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u_th};
   const void** dst[8] = {&dp.x, &dp.y, &dp.z, &dp.vx, &dp.vy, &dp.vz, &dp.m, &dp.u_th};
@@ -1437,12 +1496,13 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     if (void* m = direct(member_idx)) dmi = (int64_t*)m;
     else if (n_slots) AHF_CUDA(cudaMemcpyAsync(dmi, member_idx, (size_t)n_slots * 8, cudaMemcpyHostToDevice, s));
   }
-  // outputs: in place when mapped, else copied back after the kernels
-  void* m_out = n_halos ? direct(out) : nullptr;
-  void* m_bi = n_slots ? direct(bound_idx) : nullptr;
-  void* m_phi = (phi && n_slots) ? direct(phi) : nullptr;
-  void* m_ri = (removed_iter && n_slots) ? direct(removed_iter) : nullptr;
-  void* m_prof = (n_bins > 0 && n_halos) ? direct(prof) : nullptr;
+  // outputs: in place when mapped (mode 1), else copied back after the kernels
+  // or pushed by the classes (mode 2)
+  void* m_out = n_halos ? out_direct(out) : nullptr;
+  void* m_bi = n_slots ? out_direct(bound_idx) : nullptr;
+  void* m_phi = (phi && n_slots) ? out_direct(phi) : nullptr;
+  void* m_ri = (removed_iter && n_slots) ? out_direct(removed_iter) : nullptr;
+  void* m_prof = (n_bins > 0 && n_halos) ? out_direct(prof) : nullptr;
   ahf_result* dout = B.take<ahf_result>((size_t)n_halos);
   int64_t* dbi = B.take<int64_t>((size_t)std::max<int64_t>(n_slots, 1));
   void* dphi = phi ? (void*)B.take<char>((size_t)std::max<int64_t>(n_slots, 1) * ps) : nullptr;
@@ -1453,14 +1513,31 @@ int host_impl(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   if (m_phi) dphi = m_phi;
   if (m_ri) dri = (int32_t*)m_ri;
   if (m_prof) dprof = (double*)m_prof;
+  // mode 2: the slot outputs go out per class when every one of them is
+  // page-locked (not with the two-pass truncation variant, whose first pass
+  // is overwritten)
+  HostPush hp{};
+  bool pushing = c->host_direct == 2 && n_slots > 0 && !(prm->variant & AHF_VAR_RETRUNCATE) &&
+                 mapped_address(bound_idx) && (!phi || mapped_address(phi)) &&
+                 (!removed_iter || mapped_address(removed_iter));
+  if (pushing) {
+    hp.res = dout;
+    hp.bi = (const long long*)dbi;
+    hp.h_bi = (long long*)mapped_address(bound_idx);
+    hp.phi = (const char*)dphi;
+    hp.h_phi = phi ? (char*)mapped_address(phi) : nullptr;
+    hp.phi_es = (int)ps;
+    hp.ri = dri;
+    hp.h_ri = removed_iter ? (int*)mapped_address(removed_iter) : nullptr;
+  }
   if ((rc = unbind_impl(c, &dp, halos, n_halos, dmi, prm, dout, dbi, dphi, dri, s, n_bins, r_min_frac,
-                        n_bins > 0 ? dprof : nullptr)))
+                        n_bins > 0 ? dprof : nullptr, pushing ? &hp : nullptr)))
     return rc;
   if (n_halos && !m_out)
     AHF_CUDA(cudaMemcpyAsync(out, dout, sizeof(ahf_result) * (size_t)n_halos, cudaMemcpyDeviceToHost, s));
   if (n_bins > 0 && n_halos && !m_prof)
     AHF_CUDA(cudaMemcpyAsync(prof, dprof, sizeof(double) * (size_t)n_halos * n_bins * 4, cudaMemcpyDeviceToHost, s));
-  if (n_slots) {
+  if (n_slots && !pushing) {
     if (!m_bi) AHF_CUDA(cudaMemcpyAsync(bound_idx, dbi, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, s));
     if (phi && !m_phi) AHF_CUDA(cudaMemcpyAsync(phi, dphi, (size_t)n_slots * ps, cudaMemcpyDeviceToHost, s));
     if (removed_iter && !m_ri)
@@ -1641,8 +1718,8 @@ int ahf_set_option(ahf_ctx* c, int option, int64_t value) {
       c->timing = value == 1;
       return AHF_OK;
     case AHF_OPT_HOST_DIRECT:
-      if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "host_direct is 0 or 1");
-      c->host_direct = value == 1;
+      if (value < 0 || value > 2) return fail(AHF_ERR_INVALID, "host_direct is 0, 1 or 2");
+      c->host_direct = (int)value;
       return AHF_OK;
     case AHF_OPT_GRAPHS:
       if (value != 0 && value != 1) return fail(AHF_ERR_INVALID, "graphs is 0 or 1");
@@ -1686,7 +1763,7 @@ int ahf_get_option(ahf_ctx* c, int option, int64_t* value) {
     case AHF_OPT_ONCHIP_MAX: *value = c->onchip_max; return AHF_OK;
     case AHF_OPT_WAIT_LIMIT: *value = c->wait_limit; return AHF_OK;
     case AHF_OPT_TIMING: *value = c->timing ? 1 : 0; return AHF_OK;
-    case AHF_OPT_HOST_DIRECT: *value = c->host_direct ? 1 : 0; return AHF_OK;
+    case AHF_OPT_HOST_DIRECT: *value = c->host_direct; return AHF_OK;
     case AHF_OPT_GRAPHS: *value = c->graphs ? 1 : 0; return AHF_OK;
     case AHF_OPT_TRACE: *value = c->trace ? 1 : 0; return AHF_OK;
     case AHF_OPT_SERIAL: *value = c->serial ? 1 : 0; return AHF_OK;

@@ -161,3 +161,16 @@ def test_ncu_launch_list_to_phases(tmp_path):
     assert abs(s[9]["warp_instructions_per_launch"] - 22e6) < 1                 # both passes: one call
     assert s[0]["launches"] == 2 and abs(s[0]["dram_bytes_per_launch"] - 10e6) < 1   # mean per launch
     assert abs(s[0]["warp_instructions_per_launch"] - 4e6) < 1
+
+
+def test_sms_a_class_can_occupy():
+    cls = np.array([0] * 20 + [2] * 3 + [7] + [5] * 50 + [8] * 2)
+    used = bench.sms_used_by_class(cls, 152)
+    assert used[0] == 3                  # 20 warp-class haloes, 8 per CTA
+    assert used[2] == 3                  # one CTA per halo
+    assert used[7] == 16                 # one 16-CTA cluster
+    assert used[5] == 152                # 50 four-CTA clusters fill the GPU
+    assert used[8] == 152 and 1 not in used
+    e = {"warp_instructions_per_launch": 16 * 4 * 2070e6 * 1e-3 * 0.5}
+    r = bench.issue_roofline(e, 1.0, 2070.0, 152, 16)
+    assert abs(r["frac_of_sms_used"] - 0.5) < 1e-12 and abs(r["frac"] - 0.5 * 16 / 152) < 1e-12

@@ -187,13 +187,18 @@ def _pinned(torch, a):
     return t, t.numpy().view(a.dtype).reshape(a.shape)
 
 
-def test_host_entry_point_page_locked_in_place_and_staged():
-    # page-locked inputs and outputs used in place by the kernels, against the
-    # staged route and the device entry point: identical results
+@pytest.mark.parametrize("onchip_max", [131072, 8192])
+def test_host_entry_point_page_locked_in_place_and_staged(onchip_max):
+    # page-locked inputs and outputs used in place by the kernels (1), the
+    # inputs read in place with the outputs pushed by each class as it
+    # finishes (2), against the staged route (0) and the device entry point:
+    # identical results; with the on-chip classes capped at 8,192 candidates
+    # the larger haloes take the multi-CTA class (its push after its kernels)
     torch = require_gpu()
     from paper_0904_3662_gb300 import ahf
     pop = synth.halo_batch(seed=16, n_halos=40, n_lo=100, n_hi=40000, with_masses=True)
     ctx = ahf.Context(0)
+    ctx.set_option(ahf.OPT_ONCHIP_MAX, onchip_max)
     keep = []
 
     def pin(a):
@@ -206,7 +211,7 @@ def test_host_entry_point_page_locked_in_place_and_staged():
     hal = ahf.halos_from_population(pop)
     n = pop.n_particles
     outs = []
-    for direct in (1, 0):
+    for direct in (2, 1, 0):
         ctx.set_option(ahf.OPT_HOST_DIRECT, direct)
         assert ctx.get_option(ahf.OPT_HOST_DIRECT) == direct
         out = {"res": pin(np.zeros(pop.n_halos, dtype=ahf.RESULT_DTYPE)), "bound_idx": pin(np.zeros(n, np.int64)),
@@ -216,6 +221,9 @@ def test_host_entry_point_page_locked_in_place_and_staged():
         outs.append({k: v.copy() for k, v in out.items()})
     dev = ctx.unbind_profile_batch(ahf.particles_from_population(pop), hal, prm, n_bins=16, r_min_frac=0.02)
     torch.cuda.synchronize()
+    st = ctx.stats()
+    if onchip_max < 40000:
+        assert st["phase_halos"][ahf.PHASE_NAMES.index("grid_gather_sort")] > 0
     res_d = ahf.results_to_numpy(dev["res"])
     for o in outs:
         assert o["res"].tobytes() == res_d.tobytes()
