@@ -142,9 +142,22 @@ def main():
     ap.add_argument("--workload", required=True)
     ap.add_argument("--out", default=os.path.join(ROOT, "profiles", "traffic.json"))
     ap.add_argument("--command", default="")
+    ap.add_argument("--scale", default="",
+                    help="phase:factor,... : entries for a workload too large to capture under several ncu passes, "
+                         "scaled from a smaller case of the same kernels by the units each phase processes")
     args = ap.parse_args()
     launches = read_launches(args.csv)
     s = summarize(launches)
+    if args.scale:
+        factors = {int(k): float(v) for k, v in (kv.split(":") for kv in args.scale.split(","))}
+        s = {ph: e for ph, e in s.items() if ph in factors}
+        for ph, e in s.items():
+            f = factors[ph]
+            e["dram_bytes_per_launch"] *= f
+            if e["warp_instructions_per_launch"] is not None:
+                e["warp_instructions_per_launch"] *= f
+            e["us_per_launch"] *= f
+            e["scaled_from"] = f"{os.path.basename(args.csv)} x {f:g} (units processed)"
     t = {}
     if os.path.exists(args.out):
         with open(args.out) as f:
