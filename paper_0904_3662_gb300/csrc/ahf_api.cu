@@ -344,6 +344,27 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
   return AHF_OK;
 }
 
+// Ascending order of 64-bit keys whose low `low_bits` bits hold distinct
+// positions already in ascending order (h = 0, 1, ...): a stable LSD radix
+// sort on the higher bytes where the keys differ (the positions keep the
+// order of equal higher parts), 256 counters per pass.
+void sort_plan_keys(std::vector<uint64_t>& key, int low_bits) {
+  const size_t n = key.size();
+  if (n < 2) return;
+  uint64_t orb = 0, andb = ~0ull;
+  for (uint64_t k : key) { orb |= k; andb &= k; }
+  const uint64_t diff = orb ^ andb;
+  std::vector<uint64_t> tmp(n);
+  for (int b = low_bits / 8; b < 8; ++b) {
+    if (((diff >> (8 * b)) & 0xffull) == 0) continue;
+    size_t cnt[257] = {};
+    for (uint64_t k : key) ++cnt[((k >> (8 * b)) & 0xffull) + 1];
+    for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
+    for (uint64_t k : key) tmp[cnt[(k >> (8 * b)) & 0xffull]++] = k;
+    key.swap(tmp);
+  }
+}
+
 int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const ahf_params* prm,
               Plan& P) {
   P.frame.box = prm->box;
@@ -403,7 +424,7 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
     const uint64_t cnt = (uint64_t)std::min<int64_t>(halos[h].count, 0xffffffffll);
     key[(size_t)h] = ((uint64_t)cls[h] << 60) | ((0xffffffffull - cnt) << 27) | (uint64_t)h;
   }
-  std::sort(key.begin(), key.end());
+  sort_plan_keys(key, 27);
   std::vector<int> order((size_t)n_halos);
   for (int64_t k = 0; k < n_halos; ++k) order[(size_t)k] = (int)(key[(size_t)k] & ((1ull << 27) - 1));
   P.hd.resize((size_t)n_halos);
@@ -1587,7 +1608,7 @@ int apply_tuning(ahf_ctx* c) {
   if (!f) return AHF_OK;                     // no tuning yet
   char key[256];
   device_key(c->device, key, sizeof key);
-  char line[512], dev[256] = {}, build[128] = {};
+  char line[512], dev[256] = {}, build[256] = {};
   std::vector<std::pair<int, long long>> opts;
   int rc = AHF_OK;
   while (std::fgets(line, sizeof line, f)) {
@@ -1596,7 +1617,7 @@ int apply_tuning(ahf_ctx* c) {
     long long val = 0;
     char word[256];
     if (std::sscanf(line, "device %255s", word) == 1) std::snprintf(dev, sizeof dev, "%s", word);
-    else if (std::sscanf(line, "build %127s", word) == 1) std::snprintf(build, sizeof build, "%s", word);
+    else if (std::sscanf(line, "build %255s", word) == 1) std::snprintf(build, sizeof build, "%s", word);
     else if (std::sscanf(line, "option %d %lld", &opt, &val) == 2) opts.emplace_back(opt, val);
     else if (std::sscanf(line, "%255s", word) == 1 && word[0] != '#') {
       rc = fail(AHF_ERR_INVALID, "tuning file %s: cannot read '%s'", path, word);
