@@ -527,6 +527,7 @@ void grid_take(Bump& B, GridLaunch* G, const GridSizes& z) {
   int4* work = B.take<int4>(2 * n_sub);
   uint8_t* rmask = B.take<uint8_t>(32 * n_sub);
   AccSlot* tmv = B.take<AccSlot>(3 * (size_t)z.n_tiles);
+  SkipRec* skip = B.take<SkipRec>(n_sub);
   if (!G) return;
   G->state = st; G->ctl = ctl; G->rec = rec; G->key_a = ka; G->key_b = kb; G->val_a = va; G->val_b = vb;
   G->wr = wr; G->ms = z.masses ? ms : nullptr; G->uth = z.gas ? uth : nullptr; G->val_x = vx; G->mc = mc;
@@ -535,7 +536,7 @@ void grid_take(Bump& B, GridLaunch* G, const GridSizes& z) {
   G->agg_m = agm; G->agg_r = agr; G->agg_c = agc; G->pre_m = prm_; G->pre_r = prr; G->pre_c = prc;
   G->work = work;
   G->rem_mask = rmask;
-  G->tile_mv = tmv; G->max_halo_tiles = z.max_halo_tiles; G->n_halos = z.n_grid; G->n_flat = (long long)z.nf; G->n_tiles = z.n_tiles;
+  G->tile_mv = tmv; G->skip = skip; G->max_halo_tiles = z.max_halo_tiles; G->n_halos = z.n_grid; G->n_flat = (long long)z.nf; G->n_tiles = z.n_tiles;
   G->fp64 = z.fp64 ? 1 : 0;
 }
 

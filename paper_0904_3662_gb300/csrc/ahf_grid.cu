@@ -948,9 +948,12 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
   __shared__ long long wc_[NW];
   __shared__ Acc tm_[CH], tr_[CH];
   __shared__ long long tc_[CH];
-  __shared__ int s_nw, s_base;
+  __shared__ int s_nw;
   __shared__ Acc s_tm, s_tr;
   __shared__ long long s_tc;
+  __shared__ float s_vb[3];                // the skip test's halo input
+  __shared__ int s_wn[NW], s_wb[NW];       // kept sub-tiles per warp, their list positions
+  __shared__ int s_kept;                   // sub-tiles of the halo on the next list
   const int k = blockIdx.x;
   GridHaloState& S = L.state[k];
   if (!INIT && !S.active) return;
@@ -1103,17 +1106,80 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
     S.n_alive = C;
     if (active && (INIT || !L.prm.vbulk_initial)) set_vbulk<R>(S, M, mv);
     S.active = active;
+    // the mass lost so far (exact sums), for the skip records and test
+    if (INIT) A<Acc>(S.m_init) = M;
+    S.mrem = INIT ? 0.0 : dfix(Ald<Acc>(S.m_init) - M, S.s_m);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_vb[q] = sizeof(R) == 4 ? S.vbulk[q] : (float)S.vbulk_d[q];
     // the halo's sub-tiles holding members go on the next pass's list
     s_nw = active ? (int)((S.n_member + SUB - 1) / SUB) : 0;
-    s_base = s_nw ? atomicAdd(&L.ctl->work_n[(pass + 1) & 1], s_nw) : 0;
+    s_kept = 0;
   }
   __syncthreads();
   const int nw = s_nw;
   if (nw) {
     const long long nm = S.n_member, gb = L.halos[k].gbase;
-    int4* list = L.work + (size_t)((pass + 1) & 1) * n_sub + s_base;
-    for (int j = threadIdx.x; j < nw; j += HT)
-      list[j] = make_int4(t0 * SPT + j, k, (int)(gb + (long long)j * SUB), (int)min((long long)SUB, nm - (long long)j * SUB));
+    int* wn = &L.ctl->work_n[(pass + 1) & 1];
+    int4* list = L.work + (size_t)((pass + 1) & 1) * n_sub;
+    const double mrem = S.mrem;
+    const float vb0 = s_vb[0], vb1 = s_vb[1], vb2 = s_vb[2];
+    const float two_g = 2.0f * L.prm.Gf, rsoft = L.prm.r_soft_f;
+    for (int j0 = 0; j0 < nw; j0 += HT) {
+      const int j = j0 + threadIdx.x;
+      const int u = t0 * SPT + j;
+      bool keep = j < nw;
+      if (!INIT && keep) {
+        // a sub-tile tested in an earlier pass stays out while its members
+        // can neither be removed nor fall in the band: since that test each
+        // member's 2|phi| fell by at most 2 G dM / max(r, r_soft) (the
+        // halo lost mass dM, each removed particle's term at most m / r of
+        // the member's own radius), and its |u|^2 rose by at most
+        // 2 |u| dv + dv^2 (v_bulk moved by dv); the record's margin (slack
+        // 2^-16 of 2|phi| for the float rounding of both tests) must exceed
+        // that, with 2^-10 more on the bound for its own rounding
+        const SkipRec rc = L.skip[u];
+        const float dm = (float)(mrem - rc.mrem) * (1.0f + 0x1p-20f);
+        const float reff = fmaxf(rc.rin, rsoft);
+        const float ax = vb0 - rc.vb[0], ay = vb1 - rc.vb[1], az = vb2 - rc.vb[2];
+        const float vmag = fabsf(vb0) + fabsf(vb1) + fabsf(vb2) + fabsf(rc.vb[0]) + fabsf(rc.vb[1]) + fabsf(rc.vb[2]);
+        const float dv = sqrtf(fmaf(az, az, fmaf(ay, ay, ax * ax))) * (1.0f + 0x1p-20f) + vmag * 0x1p-20f;
+        const float bound = (two_g * dm / reff + dv * fmaf(2.0f, rc.umax, dv)) * (1.0f + 0x1p-10f);
+        if (reff > 0.0f && isfinite(bound) && rc.margin > bound) {
+          keep = false;
+          // its sums carry over to the copy the next pass would have written
+          const size_t a = (size_t)((pass + 1) & 1) * n_sub + u, b = (size_t)(pass & 1) * n_sub + u;
+          ((Acc*)L.agg_m)[b] = ((const Acc*)L.agg_m)[a];
+          ((Acc*)L.agg_r)[b] = ((const Acc*)L.agg_r)[a];
+          L.agg_c[b] = L.agg_c[a];
+        }
+      }
+      // list positions: one reservation per CTA and round
+      const unsigned bal = __ballot_sync(FULL_MASK, keep);
+      if (lane == 0) s_wn[warp] = __popc(bal);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < NW; ++w) {
+          s_wb[w] = tot;
+          tot += s_wn[w];
+        }
+        const int base = tot ? atomicAdd(wn, tot) : 0;
+        for (int w = 0; w < NW; ++w) s_wb[w] += base;
+        s_kept += tot;
+      }
+      __syncthreads();
+      if (keep)
+        list[s_wb[warp] + __popc(bal & lanemask_lt())] =
+            make_int4(u, k, (int)(gb + (long long)j * SUB), (int)min((long long)SUB, nm - (long long)j * SUB));
+      __syncthreads();                     // s_wn, s_wb are reused
+    }
+    // every sub-tile left out: the next pass would remove nothing, so the
+    // halo converges there (its particle-iterations counted, no band tests)
+    if (!INIT && threadIdx.x == 0 && s_kept == 0) {
+      S.part_iter += S.n_alive;
+      S.n_iter = pass + 1;
+      S.active = 0;
+    }
   }
 }
 
@@ -1139,6 +1205,34 @@ __device__ __forceinline__ void sub_prefix(const GridLaunch& L, int u, int t, in
   M = ((const Acc*)L.pre_m)[t] + wsum(m);
   P = ((const Acc*)L.pre_r)[t] + wsum(r);
   if (C) *C = L.pre_c[t] + __reduce_add_sync(FULL_MASK, c);
+}
+
+// The skip record of sub-tile u from the lanes' margins and |u|^2 maxima
+// (lane 0's first element is the sub-tile's first: its |r| bounds the
+// members' radii from below); conservative roundings to float.
+template <typename R>
+__device__ __forceinline__ void write_skip(const GridLaunch& L, int u, const GridHaloState& S, R mg, R uu, R r0,
+                                           const R vb[3]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mg = fmin(mg, __shfl_xor_sync(FULL_MASK, mg, o));
+    uu = fmax(uu, __shfl_xor_sync(FULL_MASK, uu, o));
+  }
+  if ((threadIdx.x & 31) != 0) return;
+  SkipRec rc;
+  if (sizeof(R) == 4) {
+    rc.margin = (float)mg;
+    rc.umax = __fsqrt_ru((float)uu);
+    rc.rin = fabsf((float)r0);
+  } else {
+    rc.margin = __double2float_rd((double)mg);
+    rc.umax = __double2float_ru(sqrt((double)uu));
+    rc.rin = __double2float_rd(fabs((double)r0));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) rc.vb[a] = (float)vb[a];
+  rc.mrem = S.mrem;
+  L.skip[u] = rc;
 }
 
 // Phi and the escape test over sub-tile w.x (halo w.y) in pass `pass`, by
@@ -1207,10 +1301,13 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
   const size_t jc = (size_t)cp * n_sub + u;
   const Acc n_m = ((const Acc*)L.agg_m)[jc], n_r = ((const Acc*)L.agg_r)[jc];
   const int n_c = L.agg_c[jc];
-  // phi and the escape test
+  // phi and the escape test; the skip record's margin and |u| over the
+  // members left alive
   unsigned rem = 0;
   int nband = 0;
   Acc rm = 0, rr = 0;
+  const R keep_frac = (R)1 - band - (R)0x1p-16;
+  R mg = (R)INFINITY, uu = (R)0;
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const R r = q[i].w;
@@ -1221,7 +1318,8 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
                                             : from_fix(Ttot - Pp, s_r, R());
       const R phi = phi_real(Mf, ri[i], Sf, P);
       const R ux = q[i].x - vb[0], uy = q[i].y - vb[1], uz = q[i].z - vb[2];
-      R u2 = fma_x(uz, uz, fma_x(uy, uy, ux * ux));
+      const R uk = fma_x(uz, uz, fma_x(uy, uy, ux * ux));
+      R u2 = uk;
       if (GAS) u2 += (R)2 * uq[i];                 // gas: |u|^2 + 2 u_th (Sect. 2.1)
       const R two_phi = (R)-2 * phi;
       if (fabs(u2 - two_phi) < band * two_phi) ++nband;
@@ -1229,11 +1327,15 @@ __device__ __forceinline__ void pass_sub(const GridLaunch& L, const int4 w, int 
         rem |= 1u << i;
         rm += mfix;
         rr += rf[i];
+      } else {
+        mg = fmin(mg, two_phi * keep_frac - u2);
+        uu = fmax(uu, uk);
       }
       M += mfix;
       Pp += rf[i];
     }
   }
+  write_skip<R>(L, u, S, mg, uu, q[0].w, vb);
   // the sub-tile's sums after the removals (next copy) and its removal flags
   const int nrem = __reduce_add_sync(FULL_MASK, __popc(rem));
   nband = __reduce_add_sync(FULL_MASK, nband);
@@ -1418,6 +1520,8 @@ __device__ __forceinline__ void pass_box(const GridLaunch& L, const int4 w, int 
   unsigned rem = 0;
   int nband = 0;
   Acc rr = 0;
+  const float keep_frac = 1.0f - band - 0x1p-16f;
+  float mg = INFINITY, uu = 0.0f;
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     if (alive & (1u << i)) {
@@ -1432,10 +1536,17 @@ __device__ __forceinline__ void pass_box(const GridLaunch& L, const int4 w, int 
       if (u2 > two_phi) {
         rem |= 1u << i;
         rr += rf[i];
+      } else {
+        mg = fminf(mg, fmaf(two_phi, keep_frac, -u2));
+        uu = fmaxf(uu, u2);
       }
       M += mfix0;
       Pp += rf[i];
     }
+  }
+  {
+    const float vbv[3] = {vb0, vb1, vb2};
+    write_skip<float>(L, u, S, mg, uu, box_at(box, lane, 0).w, vbv);
   }
   const int nrem = __reduce_add_sync(FULL_MASK, __popc(rem));
   nband = __reduce_add_sync(FULL_MASK, nband);

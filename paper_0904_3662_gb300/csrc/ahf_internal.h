@@ -102,6 +102,22 @@ struct GridHaloState {
   float vbulk[3];                    // v_bulk of the current set (mixed precision)
   float pad2;
   double vbulk_d[3];                 // v_bulk of the current set (all-FP64 mode)
+  AccSlot m_init;                    // exact sum of the members' masses (before any pass)
+  double mrem;                       // mass the halo lost before the current pass
+  double pad3;
+};
+
+// What the last pass that tested a sub-tile of the multi-CTA class saw, so
+// that a later pass can leave the sub-tile out while none of its members can
+// be removed or fall in the band (a bound on how far phi and |u| can have
+// moved since; the pass then re-tests nothing that could change).
+struct SkipRec {
+  float margin;  // min over the members it left alive of 2|phi| (1 - band - 2^-16) - |u|^2 (+ 2 u_th),
+                 // rounded down; +inf when none is left
+  float umax;    // max |u| over them, rounded up
+  float rin;     // |r| of the sub-tile's first element, rounded down (no member is closer)
+  float vb[3];   // v_bulk of that pass
+  double mrem;   // mass the halo had lost before that pass
 };
 
 // Device control words of one multi-CTA call.
@@ -213,6 +229,7 @@ struct GridLaunch {
   void *pre_m, *pre_r;
   long long* pre_c;
   AccSlot* tile_mv;        // [n_tiles][3]: sum m v of each tile's members (initial set)
+  SkipRec* skip;           // [n_tiles * GRID_TILE / GRID_SUB]: the last test of each sub-tile
   uint8_t* rem_mask;       // [n_tiles * GRID_TILE / GRID_SUB][32]: removal flags of the last
                            // pass, one byte per lane (bit i: the lane's element i)
   int4* work;              // [2][n_tiles * GRID_TILE / GRID_SUB]: the sub-tiles of the active
