@@ -1124,11 +1124,22 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
     const double mrem = S.mrem;
     const float vb0 = s_vb[0], vb1 = s_vb[1], vb2 = s_vb[2];
     const float two_g = 2.0f * L.prm.Gf, rsoft = L.prm.r_soft_f;
-    for (int j0 = 0; j0 < nw; j0 += HT) {
-      const int j = j0 + threadIdx.x;
-      const int u = t0 * SPT + j;
-      bool keep = j < nw;
-      if (!INIT && keep) {
+    // RB sub-tiles per thread and round, their records loaded together
+    constexpr int RB = 4;
+    for (int j0 = 0; j0 < nw; j0 += RB * HT) {
+      bool keep[RB];
+      SkipRec rc[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int j = j0 + r * HT + threadIdx.x;
+        keep[r] = j < nw;
+        if (!INIT && keep[r]) rc[r] = L.skip[t0 * SPT + j];
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int j = j0 + r * HT + threadIdx.x;
+        const int u = t0 * SPT + j;
+        if (INIT || !keep[r]) continue;
         // a sub-tile tested in an earlier pass stays out while its members
         // can neither be removed nor fall in the band: since that test each
         // member's 2|phi| fell by at most 2 G dM / max(r, r_soft) (the
@@ -1137,15 +1148,15 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
         // 2 |u| dv + dv^2 (v_bulk moved by dv); the record's margin (slack
         // 2^-16 of 2|phi| for the float rounding of both tests) must exceed
         // that, with 2^-10 more on the bound for its own rounding
-        const SkipRec rc = L.skip[u];
-        const float dm = (float)(mrem - rc.mrem) * (1.0f + 0x1p-20f);
-        const float reff = fmaxf(rc.rin, rsoft);
-        const float ax = vb0 - rc.vb[0], ay = vb1 - rc.vb[1], az = vb2 - rc.vb[2];
-        const float vmag = fabsf(vb0) + fabsf(vb1) + fabsf(vb2) + fabsf(rc.vb[0]) + fabsf(rc.vb[1]) + fabsf(rc.vb[2]);
+        const float dm = (float)(mrem - rc[r].mrem) * (1.0f + 0x1p-20f);
+        const float reff = fmaxf(rc[r].rin, rsoft);
+        const float ax = vb0 - rc[r].vb[0], ay = vb1 - rc[r].vb[1], az = vb2 - rc[r].vb[2];
+        const float vmag = fabsf(vb0) + fabsf(vb1) + fabsf(vb2) + fabsf(rc[r].vb[0]) + fabsf(rc[r].vb[1]) +
+                           fabsf(rc[r].vb[2]);
         const float dv = sqrtf(fmaf(az, az, fmaf(ay, ay, ax * ax))) * (1.0f + 0x1p-20f) + vmag * 0x1p-20f;
-        const float bound = (two_g * dm / reff + dv * fmaf(2.0f, rc.umax, dv)) * (1.0f + 0x1p-10f);
-        if (reff > 0.0f && isfinite(bound) && rc.margin > bound) {
-          keep = false;
+        const float bound = (two_g * dm / reff + dv * fmaf(2.0f, rc[r].umax, dv)) * (1.0f + 0x1p-10f);
+        if (reff > 0.0f && isfinite(bound) && rc[r].margin > bound) {
+          keep[r] = false;
           // its sums carry over to the copy the next pass would have written
           const size_t a = (size_t)((pass + 1) & 1) * n_sub + u, b = (size_t)(pass & 1) * n_sub + u;
           ((Acc*)L.agg_m)[b] = ((const Acc*)L.agg_m)[a];
@@ -1153,24 +1164,35 @@ __global__ void __launch_bounds__(HT) g_halo(GridLaunch L, int pass) {
           L.agg_c[b] = L.agg_c[a];
         }
       }
-      // list positions: one reservation per CTA and round
-      const unsigned bal = __ballot_sync(FULL_MASK, keep);
-      if (lane == 0) s_wn[warp] = __popc(bal);
+      // list positions: a warp scan of the warps' counts, one reservation per round
+      unsigned bal[RB];
+      int cnt = 0;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        bal[r] = __ballot_sync(FULL_MASK, keep[r]);
+        cnt += __popc(bal[r]);
+      }
+      if (lane == 0) s_wn[warp] = cnt;
       __syncthreads();
-      if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < NW; ++w) {
-          s_wb[w] = tot;
-          tot += s_wn[w];
-        }
-        const int base = tot ? atomicAdd(wn, tot) : 0;
-        for (int w = 0; w < NW; ++w) s_wb[w] += base;
-        s_kept += tot;
+      if (warp == 0) {
+        const int x = lane < NW ? s_wn[lane] : 0;
+        const int inc = (int)wscan((uint32_t)x, lane);
+        int base = 0;
+        if (lane == 31 && inc) base = atomicAdd(wn, inc);
+        base = __shfl_sync(FULL_MASK, base, 31);
+        if (lane < NW) s_wb[lane] = base + inc - x;
+        if (lane == 31) s_kept += inc;
       }
       __syncthreads();
-      if (keep)
-        list[s_wb[warp] + __popc(bal & lanemask_lt())] =
-            make_int4(u, k, (int)(gb + (long long)j * SUB), (int)min((long long)SUB, nm - (long long)j * SUB));
+      int off = s_wb[warp];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int j = j0 + r * HT + threadIdx.x;
+        if (keep[r])
+          list[off + __popc(bal[r] & lanemask_lt())] =
+              make_int4(t0 * SPT + j, k, (int)(gb + (long long)j * SUB), (int)min((long long)SUB, nm - (long long)j * SUB));
+        off += __popc(bal[r]);
+      }
       __syncthreads();                     // s_wn, s_wb are reused
     }
     // every sub-tile left out: the next pass would remove nothing, so the
@@ -1412,20 +1434,31 @@ __global__ void __launch_bounds__(T) g_removed(GridLaunch L, int pass) {
     const HaloDev& H = L.halos[w.y];
     const int s_v = S.s_mv;
     Acc mv0 = 0, mv1 = 0, mv2 = 0;
-    while (rem) {
-      const int e = __ffs(rem) - 1;
-      rem &= rem - 1;
-      const long long g = (long long)w.z + lane * EPL + e;
-      // removed: the sign bit of r, set without reading r
-      if (sizeof(R) == 4) atomicOr((unsigned*)&wr[g].w, 0x80000000u);
-      else atomicOr((unsigned long long*)&wr[g].w, 0x8000000000000000ull);
-      const uint32_t pos = L.val_x[g];
-      if (L.out.removed_iter) L.out.removed_iter[H.offset + pos] = pass;
-      const V4 vm = rec[2 * (H.gbase + pos) + 1];  // (v, m) of the candidate
-      const R m = UNIF ? m0 : ((const R*)L.ms)[g];
-      mv0 += fixr(mul_rn(m, vm.x), s_v);
-      mv1 += fixr(mul_rn(m, vm.y), s_v);
-      mv2 += fixr(mul_rn(m, vm.z), s_v);
+    if (rem) {
+      // the lane's removed elements: their candidate positions, then their
+      // records, each round's loads issued together
+      const long long g0 = (long long)w.z + lane * EPL;
+      uint32_t pos[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e)
+        if ((rem >> e) & 1u) pos[e] = L.val_x[g0 + e];
+      V4 vm[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e)
+        if ((rem >> e) & 1u) vm[e] = rec[2 * (H.gbase + pos[e]) + 1];  // (v, m) of the candidate
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        if (!((rem >> e) & 1u)) continue;
+        const long long g = g0 + e;
+        // removed: the sign bit of r, set without reading r
+        if (sizeof(R) == 4) atomicOr((unsigned*)&wr[g].w, 0x80000000u);
+        else atomicOr((unsigned long long*)&wr[g].w, 0x8000000000000000ull);
+        if (L.out.removed_iter) L.out.removed_iter[H.offset + pos[e]] = pass;
+        const R m = UNIF ? m0 : ((const R*)L.ms)[g];
+        mv0 += fixr(mul_rn(m, vm[e].x), s_v);
+        mv1 += fixr(mul_rn(m, vm[e].y), s_v);
+        mv2 += fixr(mul_rn(m, vm[e].z), s_v);
+      }
     }
     mv0 = wsum(mv0);
     mv1 = wsum(mv1);

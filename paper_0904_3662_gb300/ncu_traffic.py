@@ -22,7 +22,8 @@ Phases: each on-chip size class is one kernel launch per call (the figure is
 the mean over its launches); each multi-CTA phase is several kernels per call
 (prepare + radix passes; the passes of the iteration; the final pass, virial
 search, records and profile rows), whose figure is their sum per call, the
-calls counted by the one g_scales launch each call makes.
+calls counted by the one g_scales launch each call makes (a list that a launch
+count cut off inside a call is read up to its last complete call).
 """
 from __future__ import annotations
 
@@ -110,6 +111,14 @@ def summarize(launches):
     warp_instructions_per_launch, us_per_launch}}; per launch = per kernel
     launch for on-chip classes, per call for the multi-CTA phases."""
     tot = defaultdict(lambda: {"n": 0, "us": 0.0, "dram": 0.0, "inst": 0.0, "have_inst": True, "names": set()})
+    # a list cut off by the capture's launch count ends inside a call of the
+    # multi-CTA class: keep the complete calls (each ends with one g_result)
+    ends = [i for i, (_, name, _) in enumerate(launches) if "g_result" in name]
+    if ends:
+        last = ends[-1]
+        while last + 1 < len(launches) and phase_of(launches[last + 1][1]) == 10:
+            last += 1                      # the profile rows after the record
+        launches = launches[:last + 1]
     calls = 0
     for _, name, m in launches:
         if "g_scales" in name:
