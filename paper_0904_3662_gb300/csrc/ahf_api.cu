@@ -578,7 +578,7 @@ int run_grid(ahf_ctx* c, GridLaunch& G, const ahf_params* prm, cudaStream_t s, i
   std::memcpy(&orb, c->flag_host, 8);
   std::memcpy(&andb, c->flag_host + 2, 8);
   AHF_CUDA(grid_sort(G, s, orb, andb));
-  c->stats.launches += (4 + (G.n_big ? 1 : 0)) * G.sort_passes + (G.sort_passes ? 0 : 1) + 2;
+  c->stats.launches += G.sort_launches;
   if ((rc = phase_end(c, PH_GRID_SORT, s))) return rc;
   if ((rc = phase_begin(c, PH_GRID_ITER, s, G.n_halos, G.n_flat))) return rc;
   for (int pass = 1; pass <= prm->max_iter;) {

@@ -46,6 +46,7 @@ constexpr int T = GRID_THREADS;         // 256
 constexpr int TILE = GRID_TILE;         // 2048
 constexpr int IPT = TILE / T;           // 8 elements per thread
 constexpr int NWARP = T / 32;
+static_assert(T == 256, "one thread per byte digit in the histograms and scans");
 
 // Precision of the per-particle arithmetic.  float: the mixed mode (FP32
 // radius key, FP32 phi and escape test).  double: the all-FP64 mode (FP64
@@ -321,6 +322,14 @@ __device__ __forceinline__ double load_mass_f64(const ParticlesDev& p, long long
 
 // ---- prepare ---------------------------------------------------------------------
 
+// The tile's counts of the keys' low byte, in g_hist's layout: the first radix
+// pass sorts on that byte whenever it varies (it does for radii), and then
+// reads these counts instead of running its own histogram kernel.
+__device__ __forceinline__ void store_low_byte_hist(const GridLaunch& L, int t, int k, const uint32_t* h) {
+  const int t0 = L.halo_tile0[k], th = L.halo_tile0[k + 1] - t0;
+  L.tile_hist[(size_t)t0 * 256 + (size_t)threadIdx.x * th + (t - t0)] = h[threadIdx.x];
+}
+
 // The CTA's key range, per-halo maxima and member count merged into the call's
 // words.  Every thread passes its warp's reduced values; the CTA reduces them
 // once more and thread 0 issues an atomic only where it can change the word
@@ -374,6 +383,8 @@ __global__ void __launch_bounds__(T, 4) g_prepare_mixed(GridLaunch L) {
   const ParamsDev& P = L.prm;
   uint32_t* key_a = (uint32_t*)L.key_a;
   float4* rec = (float4*)L.rec;
+  __shared__ uint32_t h0[256];
+  h0[threadIdx.x] = 0u;
   Cand<CT> c[IPT];
   bool ok[IPT];
 #pragma unroll
@@ -396,6 +407,7 @@ __global__ void __launch_bounds__(T, 4) g_prepare_mixed(GridLaunch L) {
   uint32_t orb = 0, andb = 0xffffffffu;
   unsigned long long mxm = 0, mxr = 0, mxv = 0;
   int nmem = 0;
+  __syncthreads();                       // h0 zeroed
 #pragma unroll
   for (int q = 0; q < IPT; ++q) {
     const int e = q * T + threadIdx.x;
@@ -423,9 +435,12 @@ __global__ void __launch_bounds__(T, 4) g_prepare_mixed(GridLaunch L) {
     }
     if (L.out.removed_iter) L.out.removed_iter[H.offset + (g - H.gbase)] = key == KEY_NONMEMBER ? -1 : 0;
     key_a[g] = key;
+    atomicAdd(&h0[key & 0xffu], 1u);
     orb |= key;
     andb &= key;
   }
+  __syncthreads();
+  store_low_byte_hist(L, t, k, h0);
   for (int o = 16; o > 0; o >>= 1) {
     orb |= __shfl_xor_sync(FULL_MASK, orb, o);
     andb &= __shfl_xor_sync(FULL_MASK, andb, o);
@@ -449,6 +464,9 @@ __global__ void __launch_bounds__(T) g_prepare_f64(GridLaunch L) {
   D4* rec = (D4*)L.rec;
   unsigned long long orb = 0, andb = ~0ull, mxm = 0, mxr = 0, mxv = 0;
   int nmem = 0;
+  __shared__ uint32_t h0[256];
+  h0[threadIdx.x] = 0u;
+  __syncthreads();
   for (int e = threadIdx.x; e < tr.y; e += T) {
     const long long g = (long long)tr.x + e;
     const long long slot = H.offset + (g - H.gbase);
@@ -492,9 +510,12 @@ __global__ void __launch_bounds__(T) g_prepare_f64(GridLaunch L) {
     }
     if (L.out.removed_iter) L.out.removed_iter[slot] = key == ~0ull ? -1 : 0;
     key_a[g] = key;
+    atomicAdd(&h0[(uint32_t)key & 0xffu], 1u);
     orb |= key;
     andb &= key;
   }
+  __syncthreads();
+  store_low_byte_hist(L, t, k, h0);
   for (int o = 16; o > 0; o >>= 1) {
     orb |= __shfl_xor_sync(FULL_MASK, orb, o);
     andb &= __shfl_xor_sync(FULL_MASK, andb, o);
@@ -1925,12 +1946,18 @@ cudaError_t sort_t(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, un
     if ((diff >> (8 * d)) & 0xffull) digits[nd++] = d;
   if (L.n_tiles == 0) nd = 0;
   L.sort_passes = nd;
+  L.sort_launches = 0;
   if (L.n_tiles == 0) return cudaGetLastError();
   Key *ki = (Key*)L.key_a, *ko = (Key*)L.key_b;
   uint32_t *vi = L.val_a, *vo = L.val_b;
   for (int p = 0; p < nd; ++p) {
     const int shift = 8 * digits[p];
-    g_hist<Key><<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_halo, L.halo_tile0, L.tile_hist, shift);
+    // the prepare left the low byte's tile counts
+    if (p > 0 || shift != 0) {
+      g_hist<Key><<<L.n_tiles, T, 0, s>>>(ki, L.tile_range, L.tile_halo, L.halo_tile0, L.tile_hist, shift);
+      ++L.sort_launches;
+    }
+    L.sort_launches += 3 + (L.n_big ? 1 : 0);
     g_digit_scan_small<<<L.n_halos, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.digit_base);
     if (L.n_big) g_digit_scan_big<<<L.n_big * 256, 256, 0, s>>>(L.tile_hist, L.halo_tile0, L.big_halos, L.digit_base);
     g_digit_base<<<L.n_halos, 256, 0, s>>>(L.digit_base);
@@ -1947,6 +1974,7 @@ cudaError_t sort_t(GridLaunch& L, cudaStream_t s, unsigned long long or_bits, un
     vo = y;
   }
   if (nd == 0) g_fill_identity<R><<<L.n_tiles, T, 0, s>>>(L);
+  L.sort_launches += (nd == 0 ? 1 : 0) + 2;
   g_sums<R><<<(int)(((long long)L.n_tiles * SPT + NWARP - 1) / NWARP), T, 0, s>>>(L);
   if (L.max_halo_tiles > 64) g_halo<R, true, HT_BIG><<<L.n_halos, HT_BIG, 0, s>>>(L, 0);
   else g_halo<R, true, HT_SMALL><<<L.n_halos, HT_SMALL, 0, s>>>(L, 0);

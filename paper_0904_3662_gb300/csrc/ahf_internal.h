@@ -237,6 +237,7 @@ struct GridLaunch {
                            // flat element, members in it)
   int iter_grid;           // CTAs of the persistent iteration pass
   int sort_passes;         // radix passes the last grid_sort launched
+  int sort_launches;       // and its kernel launches
   ProfileRows rows;        // rows.prof != NULL: profile rows from the final pass
 };
 
