@@ -174,6 +174,7 @@ struct ahf_ctx {
   int variant_grid[NV] = {-1, -1, -1, -1, -1, -1, -1, -1};   // resident CTAs per variant (-1: not queried)
   int iter_grid[2] = {-1, -1};       // CTAs of the multi-CTA pass (mixed, FP64; -1: not queried)
   int tma_grid = -1;                 // CTAs of the pass with tensor copies (-1: not queried)
+  std::vector<HaloDev> plan_hd;      // host descriptor buffer reused by the calls' plans
 };
 
 namespace {
@@ -249,6 +250,29 @@ int phase_end(ahf_ctx* c, int ph, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// 2^e as a double, e in [-1022, 1023]: x * pow2(e) is ldexp(x, e), the one
+// rounding of the exact product (scaling by a power of two)
+inline double pow2(int e) {
+  const uint64_t b = (uint64_t)(e + 1023) << 52;
+  double x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
+}
+
+// llround for |v| < 2^63: nearest integer, halves away from zero (v minus
+// its truncation is exact)
+inline long long round_away(double v) {
+  long long i = (long long)v;
+  const double r = v - (double)i;
+  if (r >= 0.5) ++i;
+  else if (r <= -0.5) --i;
+  return i;
+}
+
+}  // namespace
+
 void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index, HaloDev& d) {
   d.c[0] = H.cx; d.c[1] = H.cy; d.c[2] = H.cz;
   // fixed-point frame of this halo alone (so a halo's result does not depend
@@ -257,9 +281,17 @@ void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index
   const double cm = std::max(std::fabs(H.cx), std::max(std::fabs(H.cy), std::fabs(H.cz)));
   double span = std::max(cm + std::fabs(H.radius), box);
   if (coord_type == AHF_COORD_F32_REL) span = std::max(span, 1.0);
-  // e: the smallest integer with 2^e > span + 1 (span + 1 >= 1 is finite)
+  // e: the smallest integer with 2^e > span + 1 (span + 1 >= 1: from the
+  // biased exponent while finite)
+  const double s1 = span + 1.0;
   int e = 0;
-  std::frexp(span + 1.0, &e);
+  if (std::isfinite(s1)) {
+    uint64_t b;
+    std::memcpy(&b, &s1, sizeof b);
+    e = (int)((b >> 52) & 0x7ff) - 1022;
+  } else {
+    std::frexp(s1, &e);
+  }
   e = std::min(e, 1100);
   const int frac = std::max(-200, std::min(200, 60 - e));
   d.frac = frac;
@@ -269,9 +301,11 @@ void ahf::fill_halo_dev(const ahf_halo& H, int coord_type, double box, int index
     exact = exact && (double)d.cf[a] == d.c[a];
   }
   d.fast = exact ? 1 : 0;
-  // the fixed-point frame (used only off the fast path)
-  d.boxfix = box > 0.0 ? (long long)std::llround(std::ldexp(box, frac)) : 0;
-  for (int a = 0; a < 3; ++a) d.cfix[a] = exact ? 0 : (long long)std::llround(std::ldexp(d.c[a], frac));
+  // the fixed-point frame (used only off the fast path); every value scaled
+  // here is below 2^60 in magnitude
+  const double sc = pow2(frac);
+  d.boxfix = box > 0.0 ? round_away(box * sc) : 0;
+  for (int a = 0; a < 3; ++a) d.cfix[a] = exact ? 0 : round_away(d.c[a] * sc);
   const double R = H.radius;
   d.R2 = R * R;
   d.R2lo = (float)(d.R2 * (1.0 - 4e-6));
@@ -290,6 +324,15 @@ struct Plan {
   long long grid_flat = 0;
   long long onchip_flat = 0;     // candidates of the on-chip classes (their records)
   FrameDev frame;
+  ahf_ctx* owner = nullptr;      // whose descriptor buffer hd holds
+  Plan() = default;
+  Plan(const Plan&) = delete;
+  Plan& operator=(const Plan&) = delete;
+  // the descriptor buffer goes back to the context for the next call (a
+  // fresh 120-byte-per-halo array each call cost its page faults and zeroing)
+  ~Plan() {
+    if (owner && owner->plan_hd.capacity() < hd.capacity()) owner->plan_hd.swap(hd);
+  }
 };
 
 int validate(const ahf_particles* p, const ahf_halo* halos, int64_t n_halos, const ahf_params* prm,
@@ -347,7 +390,12 @@ int validate_slots(const ahf_halo* halos, int64_t n_halos, int64_t n_slots, bool
 // Ascending order of 64-bit keys whose low `low_bits` bits hold distinct
 // positions already in ascending order (h = 0, 1, ...): a stable LSD radix
 // sort on the higher bytes where the keys differ (the positions keep the
-// order of equal higher parts), 256 counters per pass.
+// order of equal higher parts), 256 counters per pass.  The keys are taken
+// as four consecutive quarters, each with its own counters (the quarter's
+// runs of every digit placed in quarter order, so the sort stays stable):
+// the four counter updates of a step are independent, where one set of
+// counters made every key wait for the previous key's update of the same
+// digit.
 void sort_plan_keys(std::vector<uint64_t>& key, int low_bits) {
   const size_t n = key.size();
   if (n < 2) return;
@@ -355,12 +403,30 @@ void sort_plan_keys(std::vector<uint64_t>& key, int low_bits) {
   for (uint64_t k : key) { orb |= k; andb &= k; }
   const uint64_t diff = orb ^ andb;
   std::vector<uint64_t> tmp(n);
+  constexpr int Q = 4;
+  const size_t q = n / Q;                // keys [Q q, n) follow the last quarter's
   for (int b = low_bits / 8; b < 8; ++b) {
     if (((diff >> (8 * b)) & 0xffull) == 0) continue;
-    size_t cnt[257] = {};
-    for (uint64_t k : key) ++cnt[((k >> (8 * b)) & 0xffull) + 1];
-    for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
-    for (uint64_t k : key) tmp[cnt[(k >> (8 * b)) & 0xffull]++] = k;
+    const int sh = 8 * b;
+    uint32_t cnt[Q][256] = {};
+    const uint64_t* k = key.data();
+    for (size_t i = 0; i < q; ++i)
+      for (int s = 0; s < Q; ++s) ++cnt[s][(k[s * q + i] >> sh) & 0xffu];
+    for (size_t j = Q * q; j < n; ++j) ++cnt[Q - 1][(k[j] >> sh) & 0xffu];
+    uint32_t run = 0;
+    for (int d = 0; d < 256; ++d)
+      for (int s = 0; s < Q; ++s) {
+        const uint32_t c = cnt[s][d];
+        cnt[s][d] = run;
+        run += c;
+      }
+    uint64_t* t = tmp.data();
+    for (size_t i = 0; i < q; ++i)
+      for (int s = 0; s < Q; ++s) {
+        const uint64_t x = k[s * q + i];
+        t[cnt[s][(x >> sh) & 0xffu]++] = x;
+      }
+    for (size_t j = Q * q; j < n; ++j) t[cnt[Q - 1][(k[j] >> sh) & 0xffu]++] = k[j];
     key.swap(tmp);
   }
 }
@@ -427,6 +493,8 @@ int make_plan(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64_t
   sort_plan_keys(key, 27);
   std::vector<int> order((size_t)n_halos);
   for (int64_t k = 0; k < n_halos; ++k) order[(size_t)k] = (int)(key[(size_t)k] & ((1ull << 27) - 1));
+  P.owner = c;
+  P.hd.swap(c->plan_hd);                 // sized by an earlier call: no zeroing
   P.hd.resize((size_t)n_halos);
   long long gbase = 0, rbase = 0;
   for (int64_t k = 0; k < n_halos; ++k) {
@@ -897,10 +965,21 @@ int unbind_pass(ahf_ctx* c, const ahf_particles* p, const ahf_halo* halos, int64
   }
   // a batch of on-chip haloes only can run as a CUDA graph, replayed while
   // the launch parameters repeat (the descriptors staged above are inputs
-  // of the graph's kernels, not part of it)
-  if (c->graphs && !c->timing && n_grid == 0 && !vl.empty() && !push) {
+  // of the graph's kernels, not part of it); with outputs pushed to host
+  // buffers, their addresses and each class's push grid are parameters too
+  if (c->graphs && !c->timing && n_grid == 0 && !vl.empty()) {
     std::vector<unsigned char> key(vl.size() * sizeof(VLaunch));
     std::memcpy(key.data(), vl.data(), key.size());
+    if (push) {
+      auto put = [&](const void* v, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(v);
+        key.insert(key.end(), b, b + n);
+      };
+      const void* ptrs[7] = {push->res, push->bi, push->h_bi, push->phi, push->h_phi, push->ri, push->h_ri};
+      put(ptrs, sizeof ptrs);
+      put(&push->phi_es, sizeof push->phi_es);
+      for (const VLaunch& x : vl) put(&P.hd[(size_t)first_of[x.v]].count, sizeof(long long));
+    }
     if (!c->graph_exec || key != c->graph_key) {
       if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
       c->graph_exec = nullptr;

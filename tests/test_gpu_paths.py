@@ -187,6 +187,58 @@ def _pinned(torch, a):
     return t, t.numpy().view(a.dtype).reshape(a.shape)
 
 
+def test_host_entry_point_pushes_under_graph_replay():
+    # the host-buffer call with its outputs pushed per size class, as a
+    # replayed CUDA graph: a second call on the same buffers replays the
+    # captured graph (its outputs zeroed before, so a replay that pushed
+    # nothing would show), a call on other output buffers captures anew; every
+    # call's results equal the device entry point's
+    torch = require_gpu()
+    from paper_0904_3662_gb300 import ahf
+    pop = synth.halo_batch(seed=17, n_halos=60, n_lo=100, n_hi=20000)
+    ctx = ahf.Context(0)
+    ctx.set_option(ahf.OPT_GRAPHS, 1)
+    ctx.set_option(ahf.OPT_HOST_DIRECT, 2)
+    keep = []
+
+    def pin(a):
+        t, v = _pinned(torch, a)
+        keep.append(t)
+        return v
+    parts = ahf.Particles(pin(pop.x), pin(pop.y), pin(pop.z), pin(pop.vx), pin(pop.vy), pin(pop.vz), None,
+                          pop.m0, pop.coord_type)
+    prm = ahf.params_for(pop)
+    hal = ahf.halos_from_population(pop)
+    n = pop.n_particles
+
+    def buffers():
+        return {"res": pin(np.zeros(pop.n_halos, dtype=ahf.RESULT_DTYPE)), "bound_idx": pin(np.zeros(n, np.int64)),
+                "phi": pin(np.zeros(n, np.float32)), "removed_iter": pin(np.zeros(n, np.int32)),
+                "prof": pin(np.zeros((pop.n_halos, 16, 4)))}
+    a, b = buffers(), buffers()
+    got, graphs = [], []
+    for out in (a, a, b):
+        for v in out.values():
+            v[...] = 0
+        ctx.unbind_batch_host(parts, hal, prm, out=out, n_bins=16, r_min_frac=0.02)
+        st = ctx.stats()
+        graphs.append((st["graph_captures"], st["graph_launches"]))
+        got.append({k: v.copy() for k, v in out.items()})
+    assert graphs == [(1, 1), (0, 1), (1, 1)]
+    dev = ctx.unbind_profile_batch(ahf.particles_from_population(pop), hal, prm, n_bins=16, r_min_frac=0.02)
+    torch.cuda.synchronize()
+    res_d = ahf.results_to_numpy(dev["res"])
+    bi_d, phi_d = dev["bound_idx"].cpu().numpy(), dev["phi"].cpu().numpy()
+    for o in got:
+        assert o["res"].tobytes() == res_d.tobytes()
+        np.testing.assert_array_equal(o["removed_iter"], dev["removed_iter"].cpu().numpy())
+        np.testing.assert_array_equal(o["prof"], dev["prof"].cpu().numpy())
+        for h in range(pop.n_halos):
+            lo, nb = int(pop.offset[h]), int(res_d[h]["n_bound"])
+            np.testing.assert_array_equal(o["bound_idx"][lo:lo + nb], bi_d[lo:lo + nb])
+            np.testing.assert_array_equal(o["phi"][lo:lo + nb], phi_d[lo:lo + nb])
+
+
 @pytest.mark.parametrize("onchip_max", [131072, 8192])
 def test_host_entry_point_page_locked_in_place_and_staged(onchip_max):
     # page-locked inputs and outputs used in place by the kernels (1), the
