@@ -104,6 +104,22 @@ __device__ __forceinline__ float float_from_fix(long long v, int s) {
   return scale_pow2f(fmaf(hi, 4294967296.0f, lo), -s);
 }
 
+// float_from_fix when 2^-s is the normal float sc (no other route compiled in):
+// scale_pow2f multiplies by that same power of two.
+__device__ __forceinline__ float fix_to_float_sc(long long v, float sc) {
+  const float hi = (float)(int)(v >> 32);
+  const float lo = (float)(unsigned)(v & 0xffffffffll);
+  return fmaf(hi, 4294967296.0f, lo) * sc;
+}
+// 2^-s as a float when it is normal, else 0.
+__device__ __forceinline__ float pow2_neg(int s) {
+  return (s >= -127 && s <= 126) ? __int_as_float((127 - s) << 23) : 0.0f;
+}
+// float_from_fix(v, s) with sc = pow2_neg(s) computed once per halo.
+__device__ __forceinline__ float fix_to_float_fast(long long v, int s, float sc) {
+  return sc != 0.0f ? fix_to_float_sc(v, sc) : float_from_fix(v, s);
+}
+
 // v 2^-s as the nearest double (ties to even), assembled from the bits on the
 // integer pipes: the FP64 pipe of this part is narrow and its latency long, and
 // the per-halo record and profile rows would otherwise wait on it.  Results

@@ -889,15 +889,6 @@ __device__ __forceinline__ float fix_to_real(long long v, int s, float sc, float
   return fmaf(hi, 4294967296.0f, lo) * sc;
 }
 __device__ __forceinline__ double fix_to_real(__int128 v, int s, float, double) { return double_from_fix128(v, s); }
-// float_from_fix when 2^-s is the normal float sc (no other route compiled in)
-__device__ __forceinline__ float fix_to_float_sc(long long v, float sc) {
-  const float hi = (float)(int)(v >> 32);
-  const float lo = (float)(unsigned)(v & 0xffffffffll);
-  return fmaf(hi, 4294967296.0f, lo) * sc;
-}
-__device__ __forceinline__ float pow2_neg(int s) {
-  return (s >= -127 && s <= 126) ? __int_as_float((127 - s) << 23) : 0.0f;
-}
 
 // Sums of the initial set (all members alive) per sub-tile, one warp each,
 // into copy 1 (the first pass's).

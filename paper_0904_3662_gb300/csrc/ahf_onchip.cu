@@ -447,6 +447,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     const int s_v = fix_scale(float_exponent_of_bits(S.max_mv), n_mem);
     const bool unim = L.p.m == nullptr;                  // every particle has mass m0
     const long long m0fix = fix_from_float(L.p.m0f, s_m);
+    // 2^-s of the mass and m/r sums as floats (0 when not normal): each
+    // exact sum's float value is then one multiply, the bits of float_from_fix
+    const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
 
     if (tid == 0 && rank == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
@@ -493,7 +496,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           load_velocity<CT>(L.p, pi, v);
           m = load_mass<CT>(L.p, pi);
         }
-        mm[q] = m;
+        // with a uniform mass the slot holds 1 / max(r, r_soft) instead (the
+        // mass is m0): the reciprocal is formed once, not every iteration
+        mm[q] = unim ? rinv_of(rr[q], P.r_soft_f) : m;
         wx[q] = fmaf(P.Hf, dfl[0], v[0]);
         wy[q] = fmaf(P.Hf, dfl[1], v[1]);
         wz[q] = fmaf(P.Hf, dfl[2], v[2]);
@@ -527,9 +532,11 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       const int p = p0 + k;
       if (p < nmem_loc) {
         const int q = sw(p, mask);
-        const float m = mm[q];
+        const float mq = mm[q];
+        const float m = unim ? L.p.m0f : mq;
+        const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
         tm_own += (unim ? m0fix : fix_from_float(m, s_m));
-        tr_own += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
+        tr_own += fix_from_float(m * ri, s_r);
         tc_own += 1;
       }
     }
@@ -606,18 +613,20 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         const int p = p0 + k;
         if (p < nmem_loc) {
           const int q = sw(p, mask);
-          const float m = mm[q];
-          if (!signbit(m)) {
-            const float ri = rinv_of(rr[q], P.r_soft_f);
+          const float mq = mm[q];
+          if (!signbit(mq)) {
+            const float m = unim ? L.p.m0f : mq;
+            const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
             const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
             const long long rfix = fix_from_float(m * ri, s_r);
-            const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
+            const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
+                                     P.Gf);
             const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
             const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
             const float two_phi = -2.0f * phi;
             if (fabsf(u2 - two_phi) < P.band_f * two_phi) ++nband;
             if (u2 > two_phi) {
-              mm[q] = -m;
+              mm[q] = -mq;
               rmask |= 1u << k;
               rm += mfix;
               rq += rfix;
@@ -631,7 +640,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       for (uint32_t b = rmask; b; b &= b - 1) {
         const int k = __ffs(b) - 1;
         const int q = sw(p0 + k, mask);
-        const float m = -mm[q];
+        const float m = unim ? L.p.m0f : -mm[q];
         const int j = (int)jj[q];
         const long long slot = H.offset + j;
         float v[3];
@@ -735,12 +744,14 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         const int p = p0 + k;
         if (p < nmem_loc) {
           const int q = sw(p, mask);
-          const float m = mm[q];
-          if (!signbit(m)) {
+          const float mq = mm[q];
+          if (!signbit(mq)) {
             const float r = rr[q];
-            const float ri = rinv_of(r, P.r_soft_f);
+            const float m = unim ? L.p.m0f : mq;
+            const float ri = unim ? mq : rinv_of(r, P.r_soft_f);
             const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
-            const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
+            const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
+                                     P.Gf);
             const int j = (int)jj[q];
             const long long slot = H.offset + j;
             const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
@@ -779,7 +790,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           bool cross = true;
           if (!isinf(rn)) {
             const long long mk = mc[sw(kk, mask)];
-            const float lhs = float_from_fix(mk, s_m);
+            const float lhs = fix_to_float_fast(mk, s_m, sc_m);
             const float rhs = P.crit_f * rn * rn * rn;
             if (lhs < rhs * (1.0f - 1e-5f)) cross = true;
             else if (lhs > rhs * (1.0f + 1e-5f)) cross = false;

@@ -189,6 +189,9 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
     const int s_v = fix_scale(float_exponent_of_bits(mxv), n_mem);
     const bool unim = L.p.m == nullptr;                  // every particle has mass m0
     const long long m0fix = fix_from_float(L.p.m0f, s_m);
+    // 2^-s of the mass and m/r sums as floats (0 when not normal): each
+    // exact sum's float value is then one multiply, the bits of float_from_fix
+    const float sc_m = pow2_neg(s_m), sc_r = pow2_neg(s_r);
 
     if (lane == 0) trace_mark(L.trace, H.index, 1);
     // ---- radial sort (once) ----
@@ -217,7 +220,9 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
         load_velocity<CT>(L.p, pi, v);
         m = load_mass<CT>(L.p, pi);
       }
-      mm[q] = m;
+      // with a uniform mass the slot holds 1 / max(r, r_soft) instead (the
+      // mass is m0): the reciprocal is formed once, not every iteration
+      mm[q] = unim ? rinv_of(rr[q], P.r_soft_f) : m;
       wx[q] = fmaf(P.Hf, dfl[0], v[0]);
       wy[q] = fmaf(P.Hf, dfl[1], v[1]);
       wz[q] = fmaf(P.Hf, dfl[2], v[2]);
@@ -234,9 +239,11 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       const int p = p0 + k;
       if (p < n_mem) {
         const int q = sw(p, mask);
-        const float m = mm[q];
+        const float mq = mm[q];
+        const float m = unim ? L.p.m0f : mq;
+        const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
         tm_own += (unim ? m0fix : fix_from_float(m, s_m));
-        tr_own += fix_from_float(m * rinv_of(rr[q], P.r_soft_f), s_r);
+        tr_own += fix_from_float(m * ri, s_r);
         tc_own += 1;
       }
     }
@@ -263,38 +270,49 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       }
       long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
+      uint32_t rmask = 0;                 // this lane's removals (bit k: position p0 + k)
       for (int k = 0; k < ipt; ++k) {
         const int p = p0 + k;
         if (p < n_mem) {
           const int q = sw(p, mask);
-          const float m = mm[q];
-          if (!signbit(m)) {
-            const float ri = rinv_of(rr[q], P.r_soft_f);
+          const float mq = mm[q];
+          if (!signbit(mq)) {
+            const float m = unim ? L.p.m0f : mq;
+            const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
             const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
             const long long rfix = fix_from_float(m * ri, s_r);
-            const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
+            const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
+                                     P.Gf);
             const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
             const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
             const float two_phi = -2.0f * phi;
             if (fabsf(u2 - two_phi) < P.band_f * two_phi) ++nband;
             if (u2 > two_phi) {
-              mm[q] = -m;
-              ++nrem;
-              const long long slot = H.offset + (long long)jj[q];
-              float v[3];
-              if (L.rec) get_velocity_record(L.rec + 2 * (H.gbase + (long long)jj[q]), v);
-              else load_velocity<CT>(L.p, L.out.member_idx ? L.out.member_idx[slot] : slot, v);
+              mm[q] = -mq;
+              rmask |= 1u << k;
               rm += mfix;
               rq += rfix;
-              rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
-              rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
-              rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);
-              if (L.out.removed_iter) L.out.removed_iter[slot] = n_iter;
             }
             tm += mfix;
             tr += rfix;
           }
         }
+      }
+      // the removed, off the per-particle path: exact m v from the stored
+      // velocity, and their removal iteration
+      for (uint32_t b = rmask; b; b &= b - 1) {
+        const int k = __ffs(b) - 1;
+        const int q = sw(p0 + k, mask);
+        const float m = unim ? L.p.m0f : -mm[q];
+        const long long slot = H.offset + (long long)jj[q];
+        float v[3];
+        if (L.rec) get_velocity_record(L.rec + 2 * (H.gbase + (long long)jj[q]), v);
+        else load_velocity<CT>(L.p, L.out.member_idx ? L.out.member_idx[slot] : slot, v);
+        rv0 += fix_from_float(__fmul_rn(m, v[0]), s_v);
+        rv1 += fix_from_float(__fmul_rn(m, v[1]), s_v);
+        rv2 += fix_from_float(__fmul_rn(m, v[2]), s_v);
+        if (L.out.removed_iter) L.out.removed_iter[slot] = n_iter;
+        ++nrem;
       }
       tm_own -= rm;
       tr_own -= rq;
@@ -325,12 +343,14 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       const int p = p0 + k;
       if (p < n_mem) {
         const int q = sw(p, mask);
-        const float m = mm[q];
-        if (!signbit(m)) {
+        const float mq = mm[q];
+        if (!signbit(mq)) {
           const float r = rr[q];
-          const float ri = rinv_of(r, P.r_soft_f);
+          const float m = unim ? L.p.m0f : mq;
+          const float ri = unim ? mq : rinv_of(r, P.r_soft_f);
           const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
-          const float phi = phi_of(float_from_fix(tm, s_m), ri, float_from_fix(T_tot - tr, s_r), P.Gf);
+          const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
+                                   P.Gf);
           const long long slot = H.offset + (long long)jj[q];
           const long long pi = L.out.member_idx ? L.out.member_idx[slot] : slot;
           const long long dst = H.offset + tl;
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
         if (kk + 1 < nb) {
           const float rn = rc[sw(kk + 1, mask)];
           const long long mk = mc[sw(kk, mask)];
-          const float lhs = float_from_fix(mk, s_m);
+          const float lhs = fix_to_float_fast(mk, s_m, sc_m);
           const float rhs = P.crit_f * rn * rn * rn;
           if (lhs < rhs * (1.0f - 1e-5f)) cross = true;
           else if (lhs > rhs * (1.0f + 1e-5f)) cross = false;
