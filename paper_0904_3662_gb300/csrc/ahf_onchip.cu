@@ -71,9 +71,12 @@ struct Xchg {
   int g_nmem;
   uint32_t cnt[256];            // radix pass: digit counts of this CTA
   long long mv[3];              // fill: partial sum m v
-  long long tot[3];             // scan totals of this CTA (M, sum m/r, count)
-  long long rem[4];             // removed this iteration: m, m v (3)
-  int rem_n, rem_band;
+  // iteration exchange, two alternating copies: scan totals of this CTA
+  // (M, sum m/r, count) and its removals of the previous iteration (m,
+  // m v (3), count, band count)
+  long long xt[2][3];
+  long long xr[2][4];
+  int xn[2], xb[2];
   float first_r;                // emit: first compacted radius of this CTA
   int nb_loc;                   // emit: bound particles held by this CTA
   int kf;                       // emit: first local virial crossing (global index)
@@ -156,31 +159,50 @@ __device__ __forceinline__ void block_exclusive_scan2(long long& a, long long& b
   b = S.scan_base[warp][1] + ib - b;
 }
 
-// Publish this CTA's three scan totals and combine the cluster's: S.c_pre
-// gets the sum over lower ranks, S.c_tot the sum over all ranks.
+// One exchange of a cluster iteration: every CTA publishes its scan totals
+// of the current set and its removal sums of the previous iteration (zero
+// before the first) in copy `xs`, and combines the cluster's: S.c_pre gets
+// the totals over lower ranks, S.c_tot over all ranks; S.mv loses the m v
+// removed, S.c_removed and S.c_band count the removed and the band.  The
+// copies alternate between iterations: a CTA writes copy xs again only
+// after the next exchange's barrier, which every reader of this one has
+// passed after reading it.
 template <int NT, int CS>
-__device__ __forceinline__ void cluster_scan_totals(Smem<NT>& S, Xchg& X, int rank) {
-  if constexpr (CS == 1) {
-    if (threadIdx.x < 3) {
-      S.c_pre[threadIdx.x] = 0;
-      S.c_tot[threadIdx.x] = S.tot[threadIdx.x];
-    }
-    __syncthreads();
-  } else {
-    if (threadIdx.x == 0) { X.tot[0] = S.tot[0]; X.tot[1] = S.tot[1]; X.tot[2] = S.tot[2]; }
-    Cl<CS>::sync();
-    if (threadIdx.x < 3) {
-      long long pre = 0, tot = 0;
-      for (int r = 0; r < CS; ++r) {
-        const long long v = Cl<CS>::at(&X.tot[0], r)[threadIdx.x];
-        if (r < rank) pre += v;
-        tot += v;
-      }
-      S.c_pre[threadIdx.x] = pre;
-      S.c_tot[threadIdx.x] = tot;
-    }
-    __syncthreads();
+__device__ __forceinline__ void cluster_exchange(Smem<NT>& S, Xchg& X, int rank, int xs, bool first) {
+  if (threadIdx.x == 0) {
+    X.xt[xs][0] = S.tot[0]; X.xt[xs][1] = S.tot[1]; X.xt[xs][2] = S.tot[2];
+    X.xr[xs][0] = first ? 0 : S.acc[0];
+    X.xr[xs][1] = first ? 0 : S.acc[1];
+    X.xr[xs][2] = first ? 0 : S.acc[2];
+    X.xr[xs][3] = first ? 0 : S.acc[3];
+    X.xn[xs] = first ? 0 : S.acc_n;
+    X.xb[xs] = first ? 0 : S.acc_band;
   }
+  Cl<CS>::sync();
+  if (threadIdx.x < 3) {
+    long long pre = 0, tot = 0;
+#pragma unroll
+    for (int r = 0; r < CS; ++r) {
+      const long long v = Cl<CS>::at(&X.xt[xs][0], r)[threadIdx.x];
+      if (r < rank) pre += v;
+      tot += v;
+    }
+    S.c_pre[threadIdx.x] = pre;
+    S.c_tot[threadIdx.x] = tot;
+  } else if (threadIdx.x == 32) {
+    long long a1 = 0, a2 = 0, a3 = 0;
+    int nr = 0, nbd = 0;
+#pragma unroll
+    for (int r = 0; r < CS; ++r) {
+      const Xchg* Y = Cl<CS>::at(&X, r);
+      a1 += Y->xr[xs][1]; a2 += Y->xr[xs][2]; a3 += Y->xr[xs][3];
+      nr += Y->xn[xs]; nbd += Y->xb[xs];
+    }
+    S.mv[0] -= a1; S.mv[1] -= a2; S.mv[2] -= a3;
+    S.c_removed = nr;
+    S.c_band = nbd;
+  }
+  __syncthreads();
 }
 
 // Stable LSD radix sort of the halo's keys, 8-bit digits, skipping the digits
@@ -559,13 +581,20 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
           S.racc_band[bsel] = 0;
         }
     }
-    while (n_alive > 0 && n_iter < P.max_iter) {
-      ++n_iter;
-      part_iter += n_alive;
-      const int bsel = n_iter & 1;
+    // a cluster: one exchange per iteration (cluster_exchange) carries the
+    // scan totals of the current set and the previous iteration's removals;
+    // the last one, of the final set, also serves the emit
+    long long e_tm = 0, e_tr = 0, e_tc = 0;   // the emit's prefixes (cluster)
+    int xs = 0;
+    for (;;) {
       long long tm = tm_own, tr = tr_own;
       long long T_tot;
+      int bsel = 0;
       if constexpr (CS == 1) {
+        if (!(n_alive > 0 && n_iter < P.max_iter)) break;
+        ++n_iter;
+        part_iter += n_alive;
+        bsel = n_iter & 1;
         block_exclusive_scan2<NT>(tm, tr, S);
         T_tot = S.tot[1];
         // v_bulk = sum m v / sum m of the current set, from the exact sums
@@ -584,7 +613,26 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
       } else {
         long long tc = tc_own;
         block_exclusive_scan3<NT>(tm, tr, tc, S);
-        cluster_scan_totals<NT, CS>(S, X, rank);
+        cluster_exchange<NT, CS>(S, X, rank, xs, n_iter == 0);
+        xs ^= 1;
+        bool stop = false;
+        if (n_iter > 0) {                // the previous iteration's removals
+          const int removed = S.c_removed;
+          n_band += S.c_band;
+          n_alive -= removed;
+          if (removed == 0) {
+            converged = true;
+            stop = true;
+          }
+        }
+        if (stop || !(n_alive > 0 && n_iter < P.max_iter)) {
+          e_tm = tm;
+          e_tr = tr;
+          e_tc = tc;
+          break;
+        }
+        ++n_iter;
+        part_iter += n_alive;
         if (tid == 0) {
           if (n_iter == 1 || !P.vbulk_initial) {
             const float mt = float_from_fix(S.c_tot[0], s_m);
@@ -682,38 +730,8 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
         mvl[2] -= acc[3];
         n_alive -= removed;
         if (removed == 0) { converged = true; break; }
-        continue;
       }
-      if constexpr (CS > 1) {
-        if (tid == 0) {
-          X.rem[0] = S.acc[0]; X.rem[1] = S.acc[1]; X.rem[2] = S.acc[2]; X.rem[3] = S.acc[3];
-          X.rem_n = S.acc_n; X.rem_band = S.acc_band;
-        }
-        Cl<CS>::sync();
-        if (tid == 0) {
-          long long a1 = 0, a2 = 0, a3 = 0;
-          int nr = 0, nbd = 0;
-          for (int r = 0; r < CS; ++r) {
-            const Xchg* Y = Cl<CS>::at(&X, r);
-            a1 += Y->rem[1]; a2 += Y->rem[2]; a3 += Y->rem[3];
-            nr += Y->rem_n; nbd += Y->rem_band;
-          }
-          S.mv[0] -= a1; S.mv[1] -= a2; S.mv[2] -= a3;
-          S.c_removed = nr;
-          S.c_band = nbd;
-        }
-      } else {
-        if (tid == 0) {
-          S.mv[0] -= S.acc[1]; S.mv[1] -= S.acc[2]; S.mv[2] -= S.acc[3];
-          S.c_removed = S.acc_n;
-          S.c_band = S.acc_band;
-        }
-      }
-      __syncthreads();
-      const int removed = S.c_removed;
-      n_band += S.c_band;
-      n_alive -= removed;
-      if (removed == 0) { converged = true; break; }
+      // a cluster: this iteration's removal sums go out with the next exchange
     }
     if (n_alive == 0) status |= AHF_HALO_EMPTY;
     else if (!converged) status |= AHF_HALO_NOT_CONVERGED;
@@ -731,8 +749,18 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, CS>())) unbind_kernel(Onch
     long long* mc = (long long*)ex1;      // ex1 and ex2 are contiguous
     {
       long long tm = tm_own, tr = tr_own, tc = tc_own;
-      block_exclusive_scan3<NT>(tm, tr, tc, S);
-      cluster_scan_totals<NT, CS>(S, X, rank);
+      if constexpr (CS == 1) {
+        block_exclusive_scan3<NT>(tm, tr, tc, S);
+        if (tid < 3) {
+          S.c_pre[tid] = 0;
+          S.c_tot[tid] = S.tot[tid];
+        }
+        __syncthreads();
+      } else {                            // the last exchange was of the final set
+        tm = e_tm;
+        tr = e_tr;
+        tc = e_tc;
+      }
       const long long C_pre = S.c_pre[2];
       const long long C_loc = S.tot[2];
       const long long T_tot = S.c_tot[1];
