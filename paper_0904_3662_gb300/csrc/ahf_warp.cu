@@ -271,31 +271,34 @@ __global__ void __launch_bounds__(WPB * 32) warp_kernel(OnchipLaunch L) {
       long long rm = 0, rq = 0, rv0 = 0, rv1 = 0, rv2 = 0;
       int nrem = 0, nband = 0;
       uint32_t rmask = 0;                 // this lane's removals (bit k: position p0 + k)
-      for (int k = 0; k < ipt; ++k) {
-        const int p = p0 + k;
-        if (p < n_mem) {
+      // no branch per member: a slot past the members or removed earlier
+      // adds nothing and is not tested (every slot of the run is within the
+      // arrays), so the loop's members can overlap
+      if (p0 < n_mem) {
+#pragma unroll 4
+        for (int k = 0; k < ipt; ++k) {
+          const int p = p0 + k;
           const int q = sw(p, mask);
           const float mq = mm[q];
-          if (!signbit(mq)) {
-            const float m = unim ? L.p.m0f : mq;
-            const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
-            const long long mfix = (unim ? m0fix : fix_from_float(m, s_m));
-            const long long rfix = fix_from_float(m * ri, s_r);
-            const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
-                                     P.Gf);
-            const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
-            const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-            const float two_phi = -2.0f * phi;
-            if (fabsf(u2 - two_phi) < P.band_f * two_phi) ++nband;
-            if (u2 > two_phi) {
-              mm[q] = -mq;
-              rmask |= 1u << k;
-              rm += mfix;
-              rq += rfix;
-            }
-            tm += mfix;
-            tr += rfix;
+          const bool alive = p < n_mem && !signbit(mq);
+          const float m = unim ? L.p.m0f : mq;
+          const float ri = unim ? mq : rinv_of(rr[q], P.r_soft_f);
+          const long long mfix = alive ? (unim ? m0fix : fix_from_float(m, s_m)) : 0ll;
+          const long long rfix = alive ? fix_from_float(m * ri, s_r) : 0ll;
+          const float phi = phi_of(fix_to_float_fast(tm, s_m, sc_m), ri, fix_to_float_fast(T_tot - tr, s_r, sc_r),
+                                   P.Gf);
+          const float ux = wx[q] - vb0, uy = wy[q] - vb1, uz = wz[q] - vb2;
+          const float u2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+          const float two_phi = -2.0f * phi;
+          nband += (alive && fabsf(u2 - two_phi) < P.band_f * two_phi) ? 1 : 0;
+          if (alive && u2 > two_phi) {
+            mm[q] = -mq;
+            rmask |= 1u << k;
+            rm += mfix;
+            rq += rfix;
           }
+          tm += mfix;
+          tr += rfix;
         }
       }
       // the removed, off the per-particle path: exact m v from the stored
