@@ -145,6 +145,17 @@ def summarize(launches):
     return out
 
 
+def parse_scale(spec: str):
+    """{phase: factor} from "phase:factor,...", each phase given by its
+    number or its name (e.g. "8:18.7,grid_finish:18.7")."""
+    out = {}
+    for kv in filter(None, (x.strip() for x in spec.split(","))):
+        k, v = kv.rsplit(":", 1)
+        ph = int(k) if k.strip().lstrip("-").isdigit() else PHASE_NAMES.index(k.strip())
+        out[ph] = float(v)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
@@ -152,13 +163,14 @@ def main():
     ap.add_argument("--out", default=os.path.join(ROOT, "profiles", "traffic.json"))
     ap.add_argument("--command", default="")
     ap.add_argument("--scale", default="",
-                    help="phase:factor,... : entries for a workload too large to capture under several ncu passes, "
-                         "scaled from a smaller case of the same kernels by the units each phase processes")
+                    help="phase:factor,... (phase number or name): entries for a workload too large to capture "
+                         "under several ncu passes, scaled from a smaller case of the same kernels by the units "
+                         "each phase processes")
     args = ap.parse_args()
     launches = read_launches(args.csv)
     s = summarize(launches)
     if args.scale:
-        factors = {int(k): float(v) for k, v in (kv.split(":") for kv in args.scale.split(","))}
+        factors = parse_scale(args.scale)
         s = {ph: e for ph, e in s.items() if ph in factors}
         for ph, e in s.items():
             f = factors[ph]

@@ -7,6 +7,7 @@ import shutil
 import types
 
 import numpy as np
+import pytest
 
 import bench
 
@@ -161,6 +162,15 @@ def test_ncu_launch_list_to_phases(tmp_path):
     assert abs(s[9]["warp_instructions_per_launch"] - 22e6) < 1                 # both passes: one call
     assert s[0]["launches"] == 2 and abs(s[0]["dram_bytes_per_launch"] - 10e6) < 1   # mean per launch
     assert abs(s[0]["warp_instructions_per_launch"] - 4e6) < 1
+
+
+def test_ncu_scale_spec_by_number_or_name():
+    from paper_0904_3662_gb300 import ncu_traffic as nt
+    assert nt.parse_scale("8:18.715,10:18.715") == {8: 18.715, 10: 18.715}
+    assert nt.parse_scale("grid_gather_sort:2, grid_finish:0.5") == {8: 2.0, 10: 0.5}
+    assert nt.parse_scale("") == {}
+    with pytest.raises(ValueError):
+        nt.parse_scale("no_such_phase:2")
 
 
 def test_sms_a_class_can_occupy():
