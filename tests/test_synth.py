@@ -125,3 +125,27 @@ def test_generators_are_seeded():
     c = synth.halo_batch(seed=6, n_halos=20, n_lo=100, n_hi=2000)
     assert np.array_equal(a.x, b.x) and np.array_equal(a.vz, b.vz) and np.array_equal(a.count, b.count)
     assert not np.array_equal(a.count, c.count)
+
+
+def test_nfw_velocities_follow_the_jeans_dispersion():
+    # isotropic Jeans equation of the truncated profile with rho sigma^2 = 0
+    # at the truncation radius, by quadrature: rho(r) sigma^2(r) =
+    # int_r^{r_t} rho(r') G M(r') / r'^2 dr', M from the density by quadrature
+    rng = np.random.default_rng(synth.SEED_BASE + 62)
+    c, r200 = 10.0, synth.r200_of_mass(1e12)
+    rs, x_t = r200 / c, 2.0 * c
+    pos, vel = synth.sample_nfw(rng, 200_000, c, r200)
+    shape = lambda x: 1.0 / (x * (1.0 + x) ** 2)
+    i_c = integrate.quad(lambda t: t / (1.0 + t) ** 2, 0.0, c)[0]
+    rho_s = 1e12 / (4.0 * math.pi * rs ** 3 * i_c)              # M(<R_200) = 1e12
+    mass = lambda x: 4.0 * math.pi * rho_s * rs ** 3 * integrate.quad(lambda t: t / (1.0 + t) ** 2, 0.0, x)[0]
+    g = synth.G_GRAV
+    x = np.sqrt((pos * pos).sum(1)) / rs
+    for xc in (0.3, 1.0, 3.0, 8.0):
+        sel = np.abs(np.log(x / xc)) < 0.05
+        sig2 = integrate.quad(lambda t: shape(t) * g * mass(t) / (t * rs) ** 2 * rs, xc, x_t, limit=200)[0] / shape(xc)
+        got = float((vel[sel] ** 2).sum(1).mean() / 3.0)
+        n = int(sel.sum())
+        # sampling error of a variance from 3n Gaussian components, plus the
+        # variation of sigma^2 across the +-5 % shell
+        assert abs(got / sig2 - 1.0) < 4.0 * math.sqrt(2.0 / (3 * n)) + 0.01, (xc, got, sig2, n)
